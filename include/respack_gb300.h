@@ -1,0 +1,176 @@
+/*
+ * respack_gb300.h -- C ABI of the GB300 (sm_103a) polarization / screened-interaction library.
+ *
+ * The library computes, for one crystal and one k mesh, the plane-wave
+ * polarization function chi0_GG'(q, w) of the random-phase approximation and the
+ * screened interaction W_GG'(q, w) (Nakamura et al., RESPACK, Comput. Phys.
+ * Commun. 2021, arXiv 2001.02351, Sec. 2.3 "Response function with random phase
+ * approximation" and Sec. 2.4 "Direct-Coulomb and exchange integrals"):
+ *
+ *   pair densities   M^G_ab(k+q,k) = <psi_{a,k+q}| e^{i(q+G).r} |psi_{b,k}>      (Eq. ism)
+ *   frequency factor X = 1/(w - D + i d) - 1/(w + D - i d),  D = E_{a,k+q} - E_{b,k} (Eq. Xakqbk)
+ *                    integrated with generalized-tetrahedron weights x(k)          (Eq. tetrahedron)
+ *   polarization     chi_GG' = (2/N_k) sum_{k,a unocc,b occ} (1 - T T) M^G M^G'* x (Eq. chi)
+ *   dielectric       eps_GG' = delta_GG' - (4 pi/Omega) chi_GG' / (|q+G||q+G'|)    (Eq. epsGG)
+ *   screened         W_GG' = (4 pi/Omega) eps^-1_GG' / (|q+G||q+G'|), plus the bare
+ *                    diagonal 4 pi/(Omega |q+G|^2) between the two cut-offs         (Eq. Wq)
+ *
+ * Units: Hartree atomic units (energies in Ha, lengths in bohr).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex arrays are interleaved (re, im) double pairs ("c128"), row-major.
+ *  - Ownership: the caller owns every buffer it passes.  rp_load_bands copies the
+ *    band data into library-owned device memory; rp_destroy frees it.
+ *  - on_device = 1: every array argument marked "[io]" is a device pointer of the
+ *    current CUDA device, work is queued on `cuda_stream` (a cudaStream_t, NULL =
+ *    legacy default stream) and the call returns without synchronising.
+ *    on_device = 0: those arrays are host pointers and the call is synchronous.
+ *    Arrays not marked "[io]" are always host pointers.
+ *  - Errors: every entry point returns an rp_status.  No exception or abort crosses
+ *    the ABI.  rp_last_error(ctx) describes the last failure of that context.  A
+ *    context is not thread safe: one thread (one stream) per context at a time.
+ *  - k mesh: Gamma-centred, k = (i1/n1, i2/n2, i3/n3) in reciprocal-lattice
+ *    coordinates, index k = (i1*n2 + i2)*n3 + i3.  q must be a mesh vector.
+ *  - Band pairs: K = N_k * n_emp * n_occ pairs per q, column index
+ *    b = (k * n_emp + a) * n_occ + o, with a = alpha - n_occ the empty band at k+q
+ *    and o the occupied band at k (bands are 0-based, sorted by energy).
+ *  - G lists: the epsilon sphere of q is {G : 0 < 1/2|q+G|^2 <= E_cut^eps} (Sec. 2.3;
+ *    G = 0 at q = 0 is left out, the analytic head of Eq. eps00 is not computed),
+ *    the tail is {G : E_cut^eps < 1/2|q+G|^2 <= E_cut^psi} (Eq. Wq); both in
+ *    lexicographic (m1, m2, m3) Miller order.  NG and N_tail come from rp_sphere_size.
+ */
+#ifndef RESPACK_GB300_H
+#define RESPACK_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rp_ctx rp_ctx;
+
+typedef enum {
+    RP_OK = 0,
+    RP_ERR_ARG = -1,          /* an argument is out of range or inconsistent        */
+    RP_ERR_STATE = -2,        /* called out of order (e.g. no bands loaded)         */
+    RP_ERR_OOM = -3,          /* device or host allocation failed                   */
+    RP_ERR_CUDA = -4,         /* a CUDA runtime call failed                         */
+    RP_ERR_NUMERIC = -5,      /* zero or non-finite pivot in the Dyson solve        */
+    RP_ERR_TIMEOUT = -6,      /* a bounded device wait gave up                      */
+    RP_ERR_UNSUPPORTED = -7   /* valid request this build does not implement        */
+} rp_status;
+
+typedef enum {
+    RP_FP64_NATIVE = 0,       /* FP64 pair densities and FP64 tensor-core contraction */
+    RP_FP64_EMULATED = 1,     /* reserved                                             */
+    RP_TF32X3 = 2,            /* reserved                                             */
+    RP_BF16X3 = 3             /* FP32 pair densities, BF16x3 tcgen05 contraction with
+                                 FP32 accumulation flushed to FP64                    */
+} rp_precision;
+
+typedef enum { RP_AXIS_REAL = 0, RP_AXIS_IMAG = 1 } rp_axis;          /* w real, or w = i*nu */
+typedef enum { RP_TIME_ORDERED = 0, RP_RETARDED = 1 } rp_ordering;
+/* RP_TIME_ORDERED is Eq. Xakqbk as printed: X = 1/(w-D+id) - 1/(w+D-id), even in w.
+ * RP_RETARDED uses - 1/(w+D+id) for the second term, so that chi(-w) = chi(w)^*. */
+
+/* rp_setup_cell -- crystal, k mesh, FFT grid and cut-offs (Eq. pak; Sec. 2.3).
+ *   lat[9]      rows a1, a2, a3 of the direct lattice (bohr).
+ *   kmesh[3]    Gamma-centred mesh n1, n2, n3 (each >= 1).
+ *   fft[3]      real-space grid N1, N2, N3; each a product of 2s and 3s, 4..128.  It must
+ *               hold the wave-function sphere without overlap (checked in rp_load_bands).
+ *   ecut_psi_ha wave-function cut-off E_cut^psi (Ha), ecut_eps_ha polarization cut-off
+ *               E_cut^eps (Ha), 0 < E_cut^eps <= E_cut^psi.
+ *   out         receives a new context (library-owned; free with rp_destroy).
+ *   Selects the current CUDA device for the context.  RP_ERR_ARG on bad sizes. */
+int rp_setup_cell(const double lat[9], const int kmesh[3], const int fft[3],
+                  double ecut_psi_ha, double ecut_eps_ha, rp_ctx** out);
+
+/* rp_load_bands -- Bloch coefficients and energies (Eq. pak; dir-wfn data of Sec. 4).
+ *   nk          must equal n1*n2*n3.  nband = nocc + nemp bands per k, nocc >= 1, nemp >= 1.
+ *   npw[nk]     number of plane waves at each k;  npw_max >= max(npw) is the row stride.
+ *   miller      int [nk][npw_max][3] Miller indices (m1,m2,m3) of k+G, rows past npw ignored.
+ *   coef        c128 [nk][nband][npw_max] coefficients C_G,alpha(k), orthonormal per k.
+ *   energy_ha   double [nk][nband] band energies (Ha).
+ *   T           double [nk][nband] cRPA weights T_alpha,k of Eq. tak in [0,1], or NULL (RPA).
+ *   All host pointers; copied to device memory.  RP_ERR_ARG if a sphere does not fit the
+ *   FFT grid (two Miller indices congruent modulo the grid). */
+int rp_load_bands(rp_ctx* ctx, int nk, int nband, int nocc, const int* npw, int npw_max,
+                  const int* miller, const double* coef, const double* energy_ha, const double* T);
+
+/* rp_sphere_size -- epsilon sphere and tail of q.
+ *   q_frac[3]   q in reciprocal-lattice coordinates (a k-mesh vector).
+ *   ng, n_tail  receive NG and N_tail.  miller_out int [NG][3] or NULL; tail_out int
+ *   [N_tail][3] or NULL (host). */
+int rp_sphere_size(rp_ctx* ctx, const double q_frac[3], int* ng, int* n_tail,
+                   int* miller_out, int* tail_out);
+
+/* rp_pair_density -- M^G_ab(k+q,k) for the pairs of k in [k_begin, k_end) (Eq. ism),
+ *   computed as in the paper with Fourier transforms: gather of C onto the real-space
+ *   grid, inverse 3D transform, conjugate product, forward 3D transform read back on
+ *   the epsilon sphere, normalised by 1/(N1 N2 N3).
+ *   M_out [io] c128 [NG][(k_end-k_begin)*nemp*nocc]  (pair columns as above).
+ *   FP64 throughout. */
+int rp_pair_density(rp_ctx* ctx, const double q_frac[3], int k_begin, int k_end,
+                    double* M_out, int on_device, void* cuda_stream);
+
+/* rp_tetra_weights -- pair weights w_b(w) = (2/N_k)(1 - T_{a,k+q} T_{b,k}) x(k; a, b, q, w)
+ *   (Eq. chi prefactor times Eq. tetrahedron).
+ *   freq_ha[nfreq]  real frequencies (RP_AXIS_REAL) or nu of w = i nu (RP_AXIS_IMAG), Ha.
+ *   delta_ha        broadening d of Eq. Xakqbk (>= 0); both poles must stay off the real axis.
+ *   delta_a (Ha), delta_r  degeneracy thresholds of Eq. tetrahedron: sorted nodes closer than
+ *                   delta_a + delta_r*max(|x|) to their group's first node are merged.
+ *   w_out [io]      c128 [nfreq][K].   FP64 throughout. */
+int rp_tetra_weights(rp_ctx* ctx, const double q_frac[3], int axis, int ordering,
+                     int nfreq, const double* freq_ha, double delta_ha, double delta_a,
+                     double delta_r, double* w_out, int on_device, void* cuda_stream);
+
+/* rp_contract_chi0 -- chi[f] = M diag(w[f]) M^H (Eq. chi as a weighted contraction).
+ *   ng, K        sizes;  M [io] c128 [ng][K];  w [io] c128 [nfreq][K];
+ *   chi_out [io] c128 [nfreq][ng][ng] (overwritten).  precision: RP_FP64_NATIVE or
+ *   RP_BF16X3. */
+int rp_contract_chi0(rp_ctx* ctx, int ng, long long K, int nfreq, const double* M,
+                     const double* w, int precision, double* chi_out, int on_device,
+                     void* cuda_stream);
+
+/* rp_build_chi0 -- the whole chi0 path for one q: pair densities, tetrahedron weights and
+ *   the contraction, streamed over blocks of k so that M is never held whole.
+ *   chi0_out [io] c128 [nfreq][NG][NG].  Other arguments as above. */
+int rp_build_chi0(rp_ctx* ctx, const double q_frac[3], int axis, int ordering, int nfreq,
+                  const double* freq_ha, double delta_ha, double delta_a, double delta_r,
+                  int precision, double* chi0_out, int on_device, void* cuda_stream);
+
+/* rp_solve_w -- Dyson step (Eq. epsGG, Eq. Wq) in FP64:
+ *   eps = 1 - v^1/2 chi0 v^1/2,  W = v^1/2 eps^-1 v^1/2,  v^1/2_G = sqrt(4 pi/Omega)/|q+G|,
+ *   eps^-1 by Gauss-Jordan elimination with partial pivoting, one matrix per frequency.
+ *   chi0 [io] c128 [nfreq][NG][NG];  W_out [io] c128 [nfreq][NG][NG];
+ *   tail_out [io] double [N_tail] (4 pi/(Omega |q+G|^2) on the tail list) or NULL.
+ *   RP_ERR_NUMERIC if a pivot is zero or not finite (W_out is then unspecified); with
+ *   on_device = 1 that status is only known after the stream is synchronised and is
+ *   returned by the next call of rp_solve_w or by rp_check_numeric. */
+int rp_solve_w(rp_ctx* ctx, const double q_frac[3], int nfreq, const double* chi0,
+               double* W_out, double* tail_out, int on_device, void* cuda_stream);
+
+/* rp_check_numeric -- synchronises the context's last stream and returns RP_ERR_NUMERIC
+ *   if an asynchronous rp_solve_w met a bad pivot since the previous check, else RP_OK. */
+int rp_check_numeric(rp_ctx* ctx);
+
+/* rp_profile_enable -- measurement aid (no counterpart in the paper).  enable = 1 starts
+ *   recording a CUDA event pair on the launching stream around every stage of the path and
+ *   counting kernel launches per stage; enable = 0 stops.  Either call resets the totals.
+ * rp_profile_read -- synchronises the context's last stream and returns, per stage,
+ *   the summed device time (ms) and the number of kernels launched since the last reset.
+ *   Stages: 0 gather + inverse transform, 1 pair product + forward transform + read-back,
+ *   2 tetrahedron weights, 3 chi0 contraction, 4 Dyson solve.  ms[5], launches[5] (host). */
+int rp_profile_enable(rp_ctx* ctx, int enable);
+int rp_profile_read(rp_ctx* ctx, double* ms, long long* launches);
+
+/* rp_last_error -- text of the last failure of ctx (valid until the next call on ctx). */
+const char* rp_last_error(const rp_ctx* ctx);
+
+/* rp_destroy -- frees the context and all library-owned device memory. */
+void rp_destroy(rp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

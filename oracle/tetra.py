@@ -178,12 +178,14 @@ def vertex_weights(e_occ, e_emp_kq, tets, z1, z2, delta_a, delta_r, k_list=None,
         d = e_emp_kq[tt][:, :, :, None] - e_occ[tt][:, :, None, :]   # [T, 4, nemp, nocc]
         d = d[..., None]                                          # [T, 4, nemp, nocc, 1]
         for j in range(4):
-            nodes = np.stack([d[:, 0], d[:, 1], d[:, 2], d[:, 3], d[:, j]], axis=-1)  # [T,nemp,nocc,1,5]
-            val = sum(divided_difference(nodes, z, delta_a, delta_r) for z in zz)  # [T,nemp,nocc,nf]
-            for t in range(len(tt)):
-                k = tt[t, j]
-                if want[k]:
-                    x[k] += val[t] / 6.0
+            rows = np.nonzero(want[tt[:, j]])[0]
+            if len(rows) == 0:
+                continue
+            dj = d[rows]
+            nodes = np.stack([dj[:, 0], dj[:, 1], dj[:, 2], dj[:, 3], dj[:, j]], axis=-1)  # [T',nemp,nocc,1,5]
+            val = sum(divided_difference(nodes, z, delta_a, delta_r) for z in zz)        # [T',nemp,nocc,nf]
+            for r, t in enumerate(rows):
+                x[tt[t, j]] += val[r] / 6.0
     return x[ks]
 
 

@@ -1,0 +1,246 @@
+"""ctypes binding of librespack_gb300.so: argument marshalling only.
+
+Every function of the C ABI (include/respack_gb300.h) has a method of the same name on
+`Context`.  Arrays are either numpy arrays (host, synchronous call) or CUDA torch
+tensors (device, queued on torch's current stream).  Nothing here computes any step
+of the method; a missing library raises instead of falling back to anything.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librespack_gb300.so")
+
+RP_OK, RP_ERR_ARG, RP_ERR_STATE, RP_ERR_OOM, RP_ERR_CUDA, RP_ERR_NUMERIC, RP_ERR_TIMEOUT, RP_ERR_UNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+RP_FP64_NATIVE, RP_FP64_EMULATED, RP_TF32X3, RP_BF16X3 = 0, 1, 2, 3
+RP_AXIS_REAL, RP_AXIS_IMAG = 0, 1
+RP_TIME_ORDERED, RP_RETARDED = 0, 1
+
+_STATUS = {0: "RP_OK", -1: "RP_ERR_ARG", -2: "RP_ERR_STATE", -3: "RP_ERR_OOM", -4: "RP_ERR_CUDA",
+           -5: "RP_ERR_NUMERIC", -6: "RP_ERR_TIMEOUT", -7: "RP_ERR_UNSUPPORTED"}
+
+# every symbol the header declares
+EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density", "rp_tetra_weights",
+           "rp_contract_chi0", "rp_build_chi0", "rp_solve_w", "rp_check_numeric", "rp_profile_enable",
+           "rp_profile_read", "rp_last_error", "rp_destroy"]
+
+
+class RPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: run paper_2001_02351_gb300.build.build() first")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "rp_setup_cell": (I, [P, P, P, D, D, ctypes.POINTER(P)]),
+        "rp_load_bands": (I, [P, I, I, I, P, I, P, P, P, P]),
+        "rp_sphere_size": (I, [P, P, ctypes.POINTER(I), ctypes.POINTER(I), P, P]),
+        "rp_pair_density": (I, [P, P, I, I, P, I, P]),
+        "rp_tetra_weights": (I, [P, P, I, I, I, P, D, D, D, P, I, P]),
+        "rp_contract_chi0": (I, [P, I, LL, I, P, P, I, P, I, P]),
+        "rp_build_chi0": (I, [P, P, I, I, I, P, D, D, D, I, P, I, P]),
+        "rp_solve_w": (I, [P, P, I, P, P, P, I, P]),
+        "rp_check_numeric": (I, [P]),
+        "rp_profile_enable": (I, [P, I]),
+        "rp_profile_read": (I, [P, P, P]),
+        "rp_last_error": (ctypes.c_char_p, [P]),
+        "rp_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _dev_ptr(t):
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("device arrays must be contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """One crystal + k mesh + band set (rp_ctx)."""
+
+    def __init__(self, lat, kmesh, fft, ecut_psi, ecut_eps):
+        self._lib = library()
+        self._h = ctypes.c_void_p()
+        lat_, plat = _host(np.asarray(lat, dtype=np.float64).reshape(9), np.float64)
+        km_, pkm = _host(kmesh, np.int32)
+        ff_, pff = _host(fft, np.int32)
+        code = self._lib.rp_setup_cell(plat, pkm, pff, float(ecut_psi), float(ecut_eps), ctypes.byref(self._h))
+        if code != RP_OK:
+            raise RPError(code, "rp_setup_cell rejected its arguments")
+        self._keep = (lat_, km_, ff_)
+
+    # -- helpers -------------------------------------------------------------------------
+    def _check(self, code):
+        if code != RP_OK:
+            raise RPError(code, self._lib.rp_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            self._lib.rp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI ---------------------------------------------------------------------------
+    def rp_load_bands(self, nocc, npw, miller, coef, energy, T=None):
+        coef = np.ascontiguousarray(coef, dtype=np.complex128)
+        nk, nband, npw_max = coef.shape
+        npw_, pnpw = _host(npw, np.int32)
+        mil_, pmil = _host(np.asarray(miller).reshape(nk, npw_max, 3), np.int32)
+        en_, pen = _host(energy, np.float64)
+        pT = None
+        if T is not None:
+            T_, pT = _host(T, np.float64)
+        self._check(self._lib.rp_load_bands(self._h, nk, nband, int(nocc), pnpw, npw_max, pmil,
+                                            coef.ctypes.data_as(ctypes.c_void_p), pen, pT))
+        self.nk, self.nband, self.nocc, self.nemp = nk, nband, int(nocc), nband - int(nocc)
+
+    load_bands = rp_load_bands
+
+    def rp_sphere_size(self, q):
+        q_, pq = _host(q, np.float64)
+        ng, nt = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.rp_sphere_size(self._h, pq, ctypes.byref(ng), ctypes.byref(nt), None, None))
+        g = np.zeros((ng.value, 3), dtype=np.int32)
+        t = np.zeros((max(nt.value, 1), 3), dtype=np.int32)
+        self._check(self._lib.rp_sphere_size(self._h, pq, ctypes.byref(ng), ctypes.byref(nt),
+                                             g.ctypes.data_as(ctypes.c_void_p), t.ctypes.data_as(ctypes.c_void_p)))
+        return g, t[:nt.value]
+
+    def _out(self, out, shape, dtype=np.complex128):
+        if out is None:
+            return np.zeros(shape, dtype=dtype), 0
+        return out, (1 if _is_torch(out) else 0)
+
+    def _ptr(self, a, on_device):
+        return _dev_ptr(a) if on_device else a.ctypes.data_as(ctypes.c_void_p)
+
+    def rp_pair_density(self, q, k_begin, k_end, out=None):
+        g, _ = self.rp_sphere_size(q)
+        K = (k_end - k_begin) * self.nemp * self.nocc
+        out, dev = self._out(out, (len(g), K))
+        q_, pq = _host(q, np.float64)
+        self._check(self._lib.rp_pair_density(self._h, pq, int(k_begin), int(k_end), self._ptr(out, dev), dev,
+                                              _stream() if dev else None))
+        return out
+
+    def rp_tetra_weights(self, q, axis, ordering, freq, delta, delta_a=1e-8, delta_r=1e-8, out=None):
+        fr, pf = _host(freq, np.float64)
+        K = self.nk * self.nemp * self.nocc
+        out, dev = self._out(out, (len(fr), K))
+        q_, pq = _host(q, np.float64)
+        self._check(self._lib.rp_tetra_weights(self._h, pq, int(axis), int(ordering), len(fr), pf, float(delta),
+                                               float(delta_a), float(delta_r), self._ptr(out, dev), dev,
+                                               _stream() if dev else None))
+        return out
+
+    def rp_contract_chi0(self, M, w, precision=RP_FP64_NATIVE, out=None):
+        dev = 1 if _is_torch(M) else 0
+        if dev:
+            ng, K = M.shape
+            nf = w.shape[0]
+            if out is None:
+                import torch
+                out = torch.empty((nf, ng, ng), dtype=torch.complex128, device=M.device)
+            pm, pw = _dev_ptr(M), _dev_ptr(w)
+        else:
+            M = np.ascontiguousarray(M, dtype=np.complex128)
+            w = np.ascontiguousarray(w, dtype=np.complex128)
+            ng, K = M.shape
+            nf = w.shape[0]
+            out = np.zeros((nf, ng, ng), dtype=np.complex128) if out is None else out
+            pm, pw = M.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)
+        self._check(self._lib.rp_contract_chi0(self._h, int(ng), int(K), int(nf), pm, pw, int(precision),
+                                               self._ptr(out, dev), dev, _stream() if dev else None))
+        return out
+
+    def rp_build_chi0(self, q, axis, ordering, freq, delta, precision=RP_FP64_NATIVE, delta_a=1e-8,
+                      delta_r=1e-8, out=None):
+        g, _ = self.rp_sphere_size(q)
+        fr, pf = _host(freq, np.float64)
+        out, dev = self._out(out, (len(fr), len(g), len(g)))
+        q_, pq = _host(q, np.float64)
+        self._check(self._lib.rp_build_chi0(self._h, pq, int(axis), int(ordering), len(fr), pf, float(delta),
+                                            float(delta_a), float(delta_r), int(precision), self._ptr(out, dev),
+                                            dev, _stream() if dev else None))
+        return out
+
+    def rp_solve_w(self, q, chi0, out=None, tail=None):
+        g, t = self.rp_sphere_size(q)
+        dev = 1 if _is_torch(chi0) else 0
+        nf = chi0.shape[0]
+        if dev:
+            import torch
+            out = torch.empty_like(chi0) if out is None else out
+            tail = torch.zeros(max(len(t), 1), dtype=torch.float64, device=chi0.device) if tail is None else tail
+            pc = _dev_ptr(chi0)
+        else:
+            chi0 = np.ascontiguousarray(chi0, dtype=np.complex128)
+            out = np.zeros_like(chi0) if out is None else out
+            tail = np.zeros(max(len(t), 1)) if tail is None else tail
+            pc = chi0.ctypes.data_as(ctypes.c_void_p)
+        q_, pq = _host(q, np.float64)
+        self._check(self._lib.rp_solve_w(self._h, pq, int(nf), pc, self._ptr(out, dev), self._ptr(tail, dev), dev,
+                                         _stream() if dev else None))
+        return out, tail[:len(t)]
+
+    def rp_check_numeric(self):
+        self._check(self._lib.rp_check_numeric(self._h))
+
+    def rp_profile_enable(self, enable=True):
+        self._check(self._lib.rp_profile_enable(self._h, 1 if enable else 0))
+
+    def rp_profile_read(self):
+        """(ms[5], launches[5]) per stage: gather+inverse, pair forward, weights, contraction, Dyson."""
+        ms = np.zeros(5)
+        nl = np.zeros(5, dtype=np.int64)
+        self._check(self._lib.rp_profile_read(self._h, ms.ctypes.data_as(ctypes.c_void_p),
+                                              nl.ctypes.data_as(ctypes.c_void_p)))
+        return ms, nl
+
+
+def context_for(wl, q_index=0):
+    """Context with the bands of a synthetic workload loaded (helper for tests and bench)."""
+    b = wl.bands
+    ctx = Context(b.cell.lat, b.kmesh, wl.fft, b.ecut_psi, float(wl.ecut_eps[q_index]))
+    nb = wl.nocc + wl.nemp
+    ctx.load_bands(wl.nocc, b.npw, b.miller, b.coef[:, :nb], b.energy[:, :nb],
+                   None if wl.T is None else wl.T[:, :nb])
+    return ctx

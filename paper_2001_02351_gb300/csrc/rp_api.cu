@@ -1,0 +1,622 @@
+// Host side of the C ABI: validation, the per-q plan, scratch management and the
+// order of kernel launches for each entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "rp_internal.h"
+
+namespace rp {
+
+int fail(rp_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(rp_ctx* c, cudaError_t e, const char* where) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    return fail(c, e == cudaErrorMemoryAllocation ? RP_ERR_OOM : RP_ERR_CUDA, buf);
+}
+
+void prof_begin(rp_ctx* c, int stage, cudaStream_t st) {
+    if (!c->prof) return;
+    std::vector<cudaEvent_t>& v = c->prof_ev[stage];
+    const int i = 2 * c->prof_used[stage];
+    while ((int)v.size() < i + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        v.push_back(e);
+    }
+    cudaEventRecord(v[i], st);
+}
+
+void prof_end(rp_ctx* c, int stage, cudaStream_t st, int launches) {
+    c->prof_launches[stage] += launches;
+    if (!c->prof) return;
+    std::vector<cudaEvent_t>& v = c->prof_ev[stage];
+    const int i = 2 * c->prof_used[stage];
+    if ((int)v.size() < i + 2) return;
+    cudaEventRecord(v[i + 1], st);
+    c->prof_used[stage]++;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int ensure(rp_ctx* c, DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return RP_OK;
+    release(b);
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        char buf[128];
+        snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed", bytes);
+        return fail(c, RP_ERR_OOM, buf);
+    }
+    b.bytes = bytes;
+    return RP_OK;
+}
+
+static int upload(rp_ctx* c, DevBuf& b, const void* src, size_t bytes) {
+    int s = ensure(c, b, bytes);
+    if (s) return s;
+    cudaError_t e = cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "upload");
+}
+
+static bool good_fft(int n) {
+    if (n < 4 || n > 128) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+static void cart(const rp_ctx* c, const double f[3], double out[3]) {
+    for (int x = 0; x < 3; ++x) out[x] = f[0] * c->recip[0 * 3 + x] + f[1] * c->recip[1 * 3 + x] + f[2] * c->recip[2 * 3 + x];
+}
+
+static double half_norm2(const rp_ctx* c, const double q[3], int m1, int m2, int m3) {
+    double f[3] = {q[0] + m1, q[1] + m2, q[2] + m3}, v[3];
+    cart(c, f, v);
+    return 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+}
+
+static void search_box(const rp_ctx* c, double ecut, const double q[3], int nmax[3]) {
+    for (int i = 0; i < 3; ++i) {
+        double alen = std::sqrt(c->lat[i * 3] * c->lat[i * 3] + c->lat[i * 3 + 1] * c->lat[i * 3 + 1] + c->lat[i * 3 + 2] * c->lat[i * 3 + 2]);
+        nmax[i] = (int)std::floor(std::sqrt(2.0 * ecut) * alen / (2.0 * M_PI) + std::fabs(q[i])) + 1;
+    }
+}
+
+int plan_q(rp_ctx* c, const double q[3]) {
+    QPlan& P = c->plan;
+    if (P.valid && P.q[0] == q[0] && P.q[1] == q[1] && P.q[2] == q[2]) return RP_OK;
+    P.valid = false;
+    for (int i = 0; i < 3; ++i) {
+        if (!std::isfinite(q[i]) || !(std::fabs(q[i]) < 1.0)) return fail(c, RP_ERR_ARG, "q must be finite with |q_i| < 1");
+        double v = q[i] * c->kmesh[i];
+        long long r = llround(v);
+        if (std::fabs(v - (double)r) > 1e-9) return fail(c, RP_ERR_ARG, "q is not a vector of the k mesh");
+        P.qi[i] = (int)r;
+    }
+    // epsilon sphere and tail, lexicographic Miller order
+    P.gm.clear(); P.tail.clear(); P.vs.clear(); P.tailv.clear();
+    int nmax[3];
+    search_box(c, c->ecut_psi, q, nmax);
+    const double fourpi_om = 4.0 * M_PI / c->omega;
+    for (int m1 = -nmax[0]; m1 <= nmax[0]; ++m1)
+        for (int m2 = -nmax[1]; m2 <= nmax[1]; ++m2)
+            for (int m3 = -nmax[2]; m3 <= nmax[2]; ++m3) {
+                double e = half_norm2(c, q, m1, m2, m3);
+                if (e <= c->ecut_eps && e > 1e-14) {
+                    P.gm.push_back(m1); P.gm.push_back(m2); P.gm.push_back(m3);
+                    P.vs.push_back(std::sqrt(fourpi_om / (2.0 * e)));
+                } else if (e > c->ecut_eps && e <= c->ecut_psi) {
+                    P.tail.push_back(m1); P.tail.push_back(m2); P.tail.push_back(m3);
+                    P.tailv.push_back(fourpi_om / (2.0 * e));
+                }
+            }
+    P.ng = (int)P.vs.size();
+    P.ntail = (int)P.tailv.size();
+    if (P.ng == 0) return fail(c, RP_ERR_ARG, "empty epsilon sphere");
+    // umklapp map
+    const int n2 = c->kmesh[1], n3 = c->kmesh[2];
+    P.kp.assign(c->nk, 0);
+    P.g0.assign(3 * c->nk, 0);
+    for (int k = 0; k < c->nk; ++k) {
+        int i[3] = {k / (n2 * n3), (k / n3) % n2, k % n3};
+        int j[3], kk[3];
+        for (int a = 0; a < 3; ++a) {
+            j[a] = i[a] + P.qi[a];
+            int n = c->kmesh[a];
+            int g = (j[a] >= 0) ? j[a] / n : -((-j[a] + n - 1) / n);
+            P.g0[3 * k + a] = g;
+            kk[a] = j[a] - g * n;
+        }
+        P.kp[k] = (kk[0] * n2 + kk[1]) * n3 + kk[2];
+    }
+    // index sets of the pruned forward transforms
+    P.gpos.assign(3 * P.ng, 0);
+    for (int a = 0; a < 3; ++a) {
+        std::set<int> s;
+        for (int g = 0; g < P.ng; ++g) s.insert(P.gm[3 * g + a]);
+        P.setv[a].assign(s.begin(), s.end());
+        P.nset[a] = (int)P.setv[a].size();
+        for (int g = 0; g < P.ng; ++g)
+            P.gpos[3 * g + a] = (int)(std::lower_bound(P.setv[a].begin(), P.setv[a].end(), P.gm[3 * g + a]) - P.setv[a].begin());
+        // forward phases exp(+2 pi i g x / N): the matrix element of Eq. ism carries e^{+iG.r}
+        const int N = c->fft[a];
+        std::vector<double> e(2 * P.nset[a] * N);
+        std::vector<float> e32(2 * P.nset[a] * N);
+        for (int s_ = 0; s_ < P.nset[a]; ++s_)
+            for (int x = 0; x < N; ++x) {
+                long long ph = ((long long)P.setv[a][s_] * x) % N;
+                if (ph < 0) ph += N;
+                double ang = 2.0 * M_PI * (double)ph / (double)N;
+                e[2 * (s_ * N + x)] = std::cos(ang);
+                e[2 * (s_ * N + x) + 1] = std::sin(ang);
+                e32[2 * (s_ * N + x)] = (float)std::cos(ang);
+                e32[2 * (s_ * N + x) + 1] = (float)std::sin(ang);
+            }
+        int st = upload(c, P.d_efwd[a], e.data(), e.size() * sizeof(double));
+        if (st) return st;
+        st = upload(c, P.d_efwd32[a], e32.data(), e32.size() * sizeof(float));
+        if (st) return st;
+    }
+    int st;
+    if ((st = upload(c, P.d_gpos, P.gpos.data(), P.gpos.size() * sizeof(int)))) return st;
+    if ((st = upload(c, P.d_kp, P.kp.data(), P.kp.size() * sizeof(int)))) return st;
+    if ((st = upload(c, P.d_g0, P.g0.data(), P.g0.size() * sizeof(int)))) return st;
+    if ((st = upload(c, P.d_vs, P.vs.data(), P.vs.size() * sizeof(double)))) return st;
+    for (int i = 0; i < 3; ++i) P.q[i] = q[i];
+    P.valid = true;
+    return RP_OK;
+}
+
+// Six tetrahedra per sub-cell sharing the shortest main diagonal (Eq. tetrahedron reading).
+static void build_tetrahedra(rp_ctx* c) {
+    const int n[3] = {c->kmesh[0], c->kmesh[1], c->kmesh[2]};
+    const int starts[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    int best = 0;
+    double best_len = 1e300;
+    for (int s = 0; s < 4; ++s) {
+        double f[3], v[3];
+        for (int a = 0; a < 3; ++a) f[a] = (1.0 - 2.0 * starts[s][a]) / n[a];
+        cart(c, f, v);
+        double len = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (len < best_len * (1.0 - 1e-12)) { best_len = len; best = s; }
+    }
+    // paths 0 -> e_i -> e_i + e_j -> (1,1,1) over the 6 axis orders, reflected onto the diagonal
+    const int order[6][2] = {{0, 1}, {0, 2}, {1, 0}, {1, 2}, {2, 0}, {2, 1}};
+    int off[6][4][3];
+    for (int t = 0; t < 6; ++t) {
+        int v[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {1, 1, 1}};
+        v[1][order[t][0]] = 1;
+        v[2][order[t][0]] = 1;
+        v[2][order[t][1]] = 1;
+        for (int p = 0; p < 4; ++p)
+            for (int a = 0; a < 3; ++a) off[t][p][a] = starts[best][a] ? 1 - v[p][a] : v[p][a];
+    }
+    c->tets.assign(24 * c->nk, 0);
+    c->tetk.assign(24 * c->nk, -1);
+    std::vector<int> fill(c->nk, 0);
+    int t_index = 0;
+    for (int i1 = 0; i1 < n[0]; ++i1)
+        for (int i2 = 0; i2 < n[1]; ++i2)
+            for (int i3 = 0; i3 < n[2]; ++i3)
+                for (int t = 0; t < 6; ++t, ++t_index)
+                    for (int p = 0; p < 4; ++p) {
+                        int j1 = (i1 + off[t][p][0]) % n[0], j2 = (i2 + off[t][p][1]) % n[1], j3 = (i3 + off[t][p][2]) % n[2];
+                        int k = (j1 * n[1] + j2) * n[2] + j3;
+                        c->tets[4 * t_index + p] = k;
+                        c->tetk[24 * k + fill[k]++] = 4 * t_index + p;
+                    }
+}
+
+}  // namespace rp
+
+using namespace rp;
+
+extern "C" {
+
+int rp_setup_cell(const double lat[9], const int kmesh[3], const int fft[3], double ecut_psi_ha,
+                  double ecut_eps_ha, rp_ctx** out) {
+    if (!out || !lat || !kmesh || !fft) return RP_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(lat[i])) return RP_ERR_ARG;
+    for (int i = 0; i < 3; ++i) {
+        if (kmesh[i] < 1 || kmesh[i] > 64) return RP_ERR_ARG;
+        if (!good_fft(fft[i])) return RP_ERR_ARG;
+    }
+    if (!(ecut_eps_ha > 0) || !(ecut_psi_ha >= ecut_eps_ha) || !std::isfinite(ecut_psi_ha)) return RP_ERR_ARG;
+    rp_ctx* c = new (std::nothrow) rp_ctx();
+    if (!c) return RP_ERR_OOM;
+    std::memcpy(c->lat, lat, sizeof(c->lat));
+    const double* a = lat;
+    double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
+    if (!(std::fabs(det) > 1e-12)) { delete c; return RP_ERR_ARG; }
+    c->omega = std::fabs(det);
+    // b_i = 2 pi (a_j x a_k) / det  (rows), so that a_i . b_j = 2 pi delta_ij
+    const double* a1 = a; const double* a2 = a + 3; const double* a3 = a + 6;
+    double* b = c->recip;
+    auto crossv = [](const double* u, const double* v, double* w) {
+        w[0] = u[1] * v[2] - u[2] * v[1]; w[1] = u[2] * v[0] - u[0] * v[2]; w[2] = u[0] * v[1] - u[1] * v[0]; };
+    crossv(a2, a3, b); crossv(a3, a1, b + 3); crossv(a1, a2, b + 6);
+    for (int i = 0; i < 9; ++i) b[i] *= 2.0 * M_PI / det;
+    for (int i = 0; i < 3; ++i) { c->kmesh[i] = kmesh[i]; c->fft[i] = fft[i]; }
+    c->nk = kmesh[0] * kmesh[1] * kmesh[2];
+    c->nr = (long long)fft[0] * fft[1] * fft[2];
+    c->ecut_psi = ecut_psi_ha;
+    c->ecut_eps = ecut_eps_ha;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) { delete c; return RP_ERR_CUDA; }
+    if (ensure(c, c->d_err, 16 * sizeof(int)) || cudaMemset(c->d_err.p, 0, 16 * sizeof(int)) != cudaSuccess) {
+        delete c;
+        return RP_ERR_OOM;
+    }
+    *out = c;
+    return RP_OK;
+}
+
+int rp_load_bands(rp_ctx* c, int nk, int nband, int nocc, const int* npw, int npw_max, const int* miller,
+                  const double* coef, const double* energy_ha, const double* T) {
+    if (!c) return RP_ERR_ARG;
+    if (nk != c->nk) return fail(c, RP_ERR_ARG, "nk does not match the k mesh");
+    if (nocc < 1 || nband <= nocc) return fail(c, RP_ERR_ARG, "need 1 <= nocc < nband");
+    if (!npw || !miller || !coef || !energy_ha || npw_max < nband) return fail(c, RP_ERR_ARG, "bad band arrays");
+    int maxm = 0;
+    std::vector<unsigned char> mark((size_t)c->nr);
+    for (int k = 0; k < nk; ++k) {
+        if (npw[k] < nband || npw[k] > npw_max) return fail(c, RP_ERR_ARG, "npw out of range");
+        std::fill(mark.begin(), mark.end(), 0);
+        for (int p = 0; p < npw[k]; ++p) {
+            long long idx = 0;
+            for (int a = 0; a < 3; ++a) {
+                int m = miller[((size_t)k * npw_max + p) * 3 + a];
+                maxm = std::max(maxm, std::abs(m));
+                int w = ((m % c->fft[a]) + c->fft[a]) % c->fft[a];
+                idx = idx * c->fft[a] + w;
+            }
+            if (mark[idx]) return fail(c, RP_ERR_ARG, "wave-function sphere does not fit the FFT grid");
+            mark[idx] = 1;
+        }
+    }
+    for (long long i = 0; i < (long long)nk * nband; ++i) {
+        if (!std::isfinite(energy_ha[i])) return fail(c, RP_ERR_ARG, "energy not finite");
+        if (T && !(T[i] >= 0.0 && T[i] <= 1.0)) return fail(c, RP_ERR_ARG, "T outside [0,1]");
+    }
+    c->loaded = false;
+    c->plan.valid = false;
+    c->nband = nband; c->nocc = nocc; c->nemp = nband - nocc; c->npw_max = npw_max;
+    c->lb = maxm + 1;
+    if (2 * c->lb + 1 > 4 * std::max(c->fft[0], std::max(c->fft[1], c->fft[2])))
+        return fail(c, RP_ERR_ARG, "Miller indices too large for the grid");
+    c->npw.assign(npw, npw + nk);
+    c->miller.assign(miller, miller + (size_t)nk * npw_max * 3);
+    c->energy.assign(energy_ha, energy_ha + (size_t)nk * nband);
+    if (T) c->T.assign(T, T + (size_t)nk * nband); else c->T.clear();
+    int st;
+    if ((st = upload(c, c->d_coef, coef, (size_t)nk * nband * npw_max * 2 * sizeof(double)))) return st;
+    if ((st = upload(c, c->d_miller, miller, (size_t)nk * npw_max * 3 * sizeof(int)))) return st;
+    if ((st = upload(c, c->d_npw, npw, (size_t)nk * sizeof(int)))) return st;
+    if ((st = upload(c, c->d_energy, energy_ha, (size_t)nk * nband * sizeof(double)))) return st;
+    if (T) { if ((st = upload(c, c->d_T, T, (size_t)nk * nband * sizeof(double)))) return st; }
+    build_tetrahedra(c);
+    if ((st = upload(c, c->d_tets, c->tets.data(), c->tets.size() * sizeof(int)))) return st;
+    if ((st = upload(c, c->d_tetk, c->tetk.data(), c->tetk.size() * sizeof(int)))) return st;
+    // inverse-transform phases exp(+2 pi i m x / N) for m = -lb..lb (Eq. pak on the grid)
+    const int B = 2 * c->lb + 1;
+    for (int a = 0; a < 3; ++a) {
+        const int N = c->fft[a];
+        std::vector<double> e(2 * (size_t)N * B);
+        for (int x = 0; x < N; ++x)
+            for (int mi = 0; mi < B; ++mi) {
+                long long ph = ((long long)(mi - c->lb) * x) % N;
+                if (ph < 0) ph += N;
+                double ang = 2.0 * M_PI * (double)ph / (double)N;
+                e[2 * ((size_t)x * B + mi)] = std::cos(ang);
+                e[2 * ((size_t)x * B + mi) + 1] = std::sin(ang);
+            }
+        if ((st = upload(c, c->d_einv[a], e.data(), e.size() * sizeof(double)))) return st;
+    }
+    c->loaded = true;
+    return RP_OK;
+}
+
+int rp_sphere_size(rp_ctx* c, const double q[3], int* ng, int* n_tail, int* miller_out, int* tail_out) {
+    if (!c || !q) return RP_ERR_ARG;
+    int st = plan_q(c, q);
+    if (st) return st;
+    if (ng) *ng = c->plan.ng;
+    if (n_tail) *n_tail = c->plan.ntail;
+    if (miller_out) std::memcpy(miller_out, c->plan.gm.data(), c->plan.gm.size() * sizeof(int));
+    if (tail_out) std::memcpy(tail_out, c->plan.tail.data(), c->plan.tail.size() * sizeof(int));
+    return RP_OK;
+}
+
+static int check_ready(rp_ctx* c, const double q[3]) {
+    if (!c) return RP_ERR_ARG;
+    if (!c->loaded) return fail(c, RP_ERR_STATE, "bands not loaded");
+    if (!q) return fail(c, RP_ERR_ARG, "q is NULL");
+    return plan_q(c, q);
+}
+
+static int finish(rp_ctx* c, cudaStream_t st, int on_device) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    c->last_stream = st;
+    if (!on_device) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    }
+    return RP_OK;
+}
+
+// pair densities of k in [k0, k1) into M (device) with leading dimension ldm, column col0
+static int pair_density_device(rp_ctx* c, int k0, int k1, double2* M, long long ldm, long long col0, cudaStream_t st) {
+    for (int k = k0; k < k1; ++k) {
+        prof_begin(c, 0, st);
+        cudaError_t e = launch_gather_inverse(c, k, 1, st);
+        prof_end(c, 0, st, 5);
+        if (e != cudaSuccess) return cuda_fail(c, e, "gather/inverse transform");
+        prof_begin(c, 1, st);
+        int nl = 0;
+        e = launch_pair_forward(c, 1, M, ldm, col0 + (long long)(k - k0) * c->nemp * c->nocc, st, &nl);
+        prof_end(c, 1, st, nl);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pair transform");
+    }
+    return RP_OK;
+}
+
+int rp_pair_density(rp_ctx* c, const double q[3], int k_begin, int k_end, double* M_out, int on_device, void* stream) {
+    int s = check_ready(c, q);
+    if (s) return s;
+    if (k_begin < 0 || k_end > c->nk || k_begin >= k_end || !M_out) return fail(c, RP_ERR_ARG, "bad k range or output");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long kcols = (long long)(k_end - k_begin) * c->nemp * c->nocc;
+    const size_t bytes = (size_t)c->plan.ng * kcols * sizeof(double2);
+    double2* M = (double2*)M_out;
+    if (!on_device) {
+        if ((s = ensure(c, c->s_io1, bytes))) return s;
+        M = (double2*)c->s_io1.p;
+    }
+    if ((s = pair_density_device(c, k_begin, k_end, M, kcols, 0, st))) return s;
+    if (!on_device) {
+        cudaError_t e = cudaMemcpyAsync(M_out, M, bytes, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy M");
+    }
+    return finish(c, st, on_device);
+}
+
+static int check_freq(rp_ctx* c, int axis, int ordering, int nfreq, const double* freq, double delta,
+                      double da, double dr) {
+    if (axis != RP_AXIS_REAL && axis != RP_AXIS_IMAG) return fail(c, RP_ERR_ARG, "bad axis");
+    if (ordering != RP_TIME_ORDERED && ordering != RP_RETARDED) return fail(c, RP_ERR_ARG, "bad ordering");
+    if (nfreq < 1 || !freq) return fail(c, RP_ERR_ARG, "no frequencies");
+    if (!(delta >= 0) || !(da >= 0) || !(dr >= 0) || !std::isfinite(delta)) return fail(c, RP_ERR_ARG, "bad broadening/thresholds");
+    for (int f = 0; f < nfreq; ++f) {
+        if (!std::isfinite(freq[f])) return fail(c, RP_ERR_ARG, "frequency not finite");
+        double im1 = (axis == RP_AXIS_REAL) ? delta : freq[f] + delta;
+        double im2 = (axis == RP_AXIS_REAL) ? (ordering == RP_TIME_ORDERED ? delta : -delta)
+                                            : (ordering == RP_TIME_ORDERED ? -freq[f] + delta : -freq[f] - delta);
+        if (im1 == 0.0 || im2 == 0.0) return fail(c, RP_ERR_ARG, "a pole of X lies on the real axis");
+    }
+    return RP_OK;
+}
+
+static int weights_device(rp_ctx* c, int axis, int ordering, int nfreq, const double* freq, double delta,
+                          double da, double dr, double2* w, cudaStream_t st) {
+    int s = ensure(c, c->s_io3, nfreq * sizeof(double));
+    if (s) return s;
+    cudaError_t e = cudaMemcpyAsync(c->s_io3.p, freq, nfreq * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy frequencies");
+    prof_begin(c, 2, st);
+    e = launch_tetra(c, axis, ordering, nfreq, (const double*)c->s_io3.p, delta, da, dr, w, st);
+    prof_end(c, 2, st, 1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tetrahedron weights");
+    // the frequency copy is from pageable host memory; keep it valid until it has landed
+    e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "synchronize");
+}
+
+int rp_tetra_weights(rp_ctx* c, const double q[3], int axis, int ordering, int nfreq, const double* freq,
+                     double delta, double da, double dr, double* w_out, int on_device, void* stream) {
+    int s = check_ready(c, q);
+    if (s) return s;
+    if ((s = check_freq(c, axis, ordering, nfreq, freq, delta, da, dr))) return s;
+    if (!w_out) return fail(c, RP_ERR_ARG, "w_out is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long K = (long long)c->nk * c->nemp * c->nocc;
+    const size_t bytes = (size_t)nfreq * K * sizeof(double2);
+    double2* w = (double2*)w_out;
+    if (!on_device) {
+        if ((s = ensure(c, c->s_io1, bytes))) return s;
+        w = (double2*)c->s_io1.p;
+    }
+    if ((s = weights_device(c, axis, ordering, nfreq, freq, delta, da, dr, w, st))) return s;
+    if (!on_device) {
+        cudaError_t e = cudaMemcpyAsync(w_out, w, bytes, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy w");
+    }
+    return finish(c, st, on_device);
+}
+
+int rp_contract_chi0(rp_ctx* c, int ng, long long K, int nfreq, const double* M, const double* w, int precision,
+                     double* chi_out, int on_device, void* stream) {
+    if (!c) return RP_ERR_ARG;
+    if (ng < 1 || K < 1 || nfreq < 1 || !M || !w || !chi_out) return fail(c, RP_ERR_ARG, "bad contraction arguments");
+    if (precision != RP_FP64_NATIVE) return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double2 *dM = (const double2*)M, *dw = (const double2*)w;
+    double2* dchi = (double2*)chi_out;
+    int s;
+    const size_t bm = (size_t)ng * K * sizeof(double2), bw = (size_t)nfreq * K * sizeof(double2);
+    const size_t bc = (size_t)nfreq * ng * ng * sizeof(double2);
+    if (!on_device) {
+        if ((s = ensure(c, c->s_io1, bm)) || (s = ensure(c, c->s_io2, bw)) || (s = ensure(c, c->s_chi, bc))) return s;
+        cudaMemcpyAsync(c->s_io1.p, M, bm, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(c->s_io2.p, w, bw, cudaMemcpyHostToDevice, st);
+        dM = (const double2*)c->s_io1.p; dw = (const double2*)c->s_io2.p; dchi = (double2*)c->s_chi.p;
+    }
+    prof_begin(c, 3, st);
+    cudaError_t e = launch_contract_f64(dM, K, K, dw, K, 0, nfreq, ng, dchi, 0, st);
+    prof_end(c, 3, st, 1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+    if (!on_device) {
+        e = cudaMemcpyAsync(chi_out, dchi, bc, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy chi");
+    }
+    return finish(c, st, on_device);
+}
+
+int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfreq, const double* freq,
+                  double delta, double da, double dr, int precision, double* chi0_out, int on_device, void* stream) {
+    int s = check_ready(c, q);
+    if (s) return s;
+    if ((s = check_freq(c, axis, ordering, nfreq, freq, delta, da, dr))) return s;
+    if (!chi0_out) return fail(c, RP_ERR_ARG, "chi0_out is NULL");
+    if (precision != RP_FP64_NATIVE) return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ng = c->plan.ng;
+    const long long K = (long long)c->nk * c->nemp * c->nocc;
+    const long long kcols = (long long)c->nemp * c->nocc;
+    if ((s = ensure(c, c->s_w, (size_t)nfreq * K * sizeof(double2)))) return s;
+    if ((s = ensure(c, c->s_m, (size_t)ng * kcols * sizeof(double2)))) return s;
+    const size_t bc = (size_t)nfreq * ng * ng * sizeof(double2);
+    double2* chi = (double2*)chi0_out;
+    if (!on_device) {
+        if ((s = ensure(c, c->s_chi, bc))) return s;
+        chi = (double2*)c->s_chi.p;
+    }
+    double2* w = (double2*)c->s_w.p;
+    if ((s = weights_device(c, axis, ordering, nfreq, freq, delta, da, dr, w, st))) return s;
+    double2* M = (double2*)c->s_m.p;
+    for (int k = 0; k < c->nk; ++k) {
+        if ((s = pair_density_device(c, k, k + 1, M, kcols, 0, st))) return s;
+        prof_begin(c, 3, st);
+        cudaError_t e = launch_contract_f64(M, kcols, kcols, w, K, (long long)k * kcols, nfreq, ng, chi, k > 0, st);
+        prof_end(c, 3, st, 1);
+        if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+    }
+    if (!on_device) {
+        cudaError_t e = cudaMemcpyAsync(chi0_out, chi, bc, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy chi0");
+    }
+    return finish(c, st, on_device);
+}
+
+int rp_check_numeric(rp_ctx* c) {
+    if (!c) return RP_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read error flag");
+    if (flag) {
+        cudaMemset(c->d_err.p, 0, sizeof(int));
+        return fail(c, RP_ERR_NUMERIC, "zero or non-finite pivot in the Dyson solve");
+    }
+    return RP_OK;
+}
+
+int rp_solve_w(rp_ctx* c, const double q[3], int nfreq, const double* chi0, double* W_out, double* tail_out,
+               int on_device, void* stream) {
+    int s = check_ready(c, q);
+    if (s) return s;
+    if (nfreq < 1 || !chi0 || !W_out) return fail(c, RP_ERR_ARG, "bad Dyson arguments");
+    const int ng = c->plan.ng;
+    if (ng > 4096) return fail(c, RP_ERR_UNSUPPORTED, "NG above 4096");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (on_device && c->last_stream) {
+        // a bad pivot of an earlier asynchronous call is reported here
+        int flag = 0;
+        if (cudaMemcpy(&flag, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && flag) {
+            cudaMemset(c->d_err.p, 0, sizeof(int));
+            return fail(c, RP_ERR_NUMERIC, "zero or non-finite pivot in an earlier Dyson solve");
+        }
+    }
+    const size_t bc = (size_t)nfreq * ng * ng * sizeof(double2);
+    const double2* dchi = (const double2*)chi0;
+    double2* dW = (double2*)W_out;
+    if (!on_device) {
+        if ((s = ensure(c, c->s_io1, bc)) || (s = ensure(c, c->s_io2, bc)) ||
+            (s = ensure(c, c->s_io3, (size_t)std::max(1, c->plan.ntail) * sizeof(double)))) return s;
+        cudaError_t e = cudaMemcpyAsync(c->s_io1.p, chi0, bc, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy chi0");
+        dchi = (const double2*)c->s_io1.p;
+        dW = (double2*)c->s_io2.p;
+    }
+    prof_begin(c, 4, st);
+    cudaError_t e = launch_dyson(dchi, (const double*)c->plan.d_vs.p, ng, nfreq, dW, (int*)c->d_err.p, st);
+    prof_end(c, 4, st, 1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Dyson solve");
+    if (tail_out && c->plan.ntail > 0) {
+        e = cudaMemcpyAsync(tail_out, c->plan.tailv.data(), c->plan.ntail * sizeof(double),
+                            on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "tail");
+        if (on_device) cudaStreamSynchronize(st);   // the source is host memory owned by the plan
+    }
+    if (!on_device) {
+        e = cudaMemcpyAsync(W_out, dW, bc, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy W");
+        if ((s = finish(c, st, 0))) return s;
+        return rp_check_numeric(c);
+    }
+    return finish(c, st, 1);
+}
+
+int rp_profile_enable(rp_ctx* c, int enable) {
+    if (!c) return RP_ERR_ARG;
+    c->prof = enable != 0;
+    for (int i = 0; i < RP_NSTAGE; ++i) { c->prof_used[i] = 0; c->prof_launches[i] = 0; }
+    return RP_OK;
+}
+
+int rp_profile_read(rp_ctx* c, double* ms, long long* launches) {
+    if (!c || !ms || !launches) return RP_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    for (int i = 0; i < RP_NSTAGE; ++i) {
+        double tot = 0.0;
+        for (int j = 0; j < c->prof_used[i]; ++j) {
+            float t = 0.0f;
+            e = cudaEventElapsedTime(&t, c->prof_ev[i][2 * j], c->prof_ev[i][2 * j + 1]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "event time");
+            tot += t;
+        }
+        ms[i] = tot;
+        launches[i] = c->prof_launches[i];
+    }
+    return RP_OK;
+}
+
+const char* rp_last_error(const rp_ctx* c) {
+    return c ? c->err.c_str() : "null context";
+}
+
+void rp_destroy(rp_ctx* c) {
+    if (!c) return;
+    DevBuf* bufs[] = {&c->d_coef, &c->d_miller, &c->d_npw, &c->d_energy, &c->d_T, &c->d_tets, &c->d_tetk,
+                      &c->d_einv[0], &c->d_einv[1], &c->d_einv[2], &c->d_err, &c->s_box, &c->s_u1, &c->s_u2,
+                      &c->s_u, &c->s_p, &c->s_t1, &c->s_t2, &c->s_m, &c->s_w, &c->s_chi, &c->s_io1, &c->s_io2,
+                      &c->s_io3, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
+                      &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
+                      &c->plan.d_efwd32[1], &c->plan.d_efwd32[2]};
+    for (DevBuf* b : bufs) release(*b);
+    for (int i = 0; i < RP_NSTAGE; ++i)
+        for (cudaEvent_t e : c->prof_ev[i]) cudaEventDestroy(e);
+    delete c;
+}
+
+}  // extern "C"

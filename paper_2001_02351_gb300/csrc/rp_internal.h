@@ -1,0 +1,102 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "respack_gb300.h"
+
+#define RP_NSTAGE 5
+
+namespace rp {
+
+// Grow-only device allocation owned by a context.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Everything that depends on q: the epsilon sphere and its tail, the umklapp map
+// k + q = k' + G0, and the phase tables of the pruned transforms.
+struct QPlan {
+    bool valid = false;
+    double q[3] = {0, 0, 0};
+    int qi[3] = {0, 0, 0};           // q * kmesh (integers)
+    int ng = 0, ntail = 0;
+    std::vector<int> gm;             // [ng][3]
+    std::vector<int> tail;           // [ntail][3]
+    std::vector<double> vs;          // [ng] sqrt(4 pi / Omega) / |q+G|
+    std::vector<double> tailv;       // [ntail] 4 pi / (Omega |q+G|^2)
+    std::vector<int> kp, g0;         // [nk], [nk][3]
+    int nset[3] = {0, 0, 0};         // distinct Miller values per axis in the sphere
+    std::vector<int> setv[3];        // the values
+    std::vector<int> gpos;           // [ng][3] position of each G's components in the sets
+    DevBuf d_gpos, d_efwd[3], d_efwd32[3], d_kp, d_g0, d_vs;
+};
+
+}  // namespace rp
+
+struct rp_ctx {
+    int device = 0;
+    double lat[9], recip[9], omega = 0;
+    int kmesh[3] = {1, 1, 1}, nk = 1, fft[3] = {0, 0, 0};
+    long long nr = 0;
+    double ecut_psi = 0, ecut_eps = 0;
+
+    bool loaded = false;
+    int nband = 0, nocc = 0, nemp = 0, npw_max = 0;
+    int lb = 0;                       // half width of the Miller box used by the gather
+    std::vector<int> npw;             // [nk]
+    std::vector<int> miller;          // [nk][npw_max][3]
+    std::vector<double> energy;       // [nk][nband]
+    std::vector<double> T;            // [nk][nband] or empty
+    std::vector<int> tets;            // [6 nk][4]
+    std::vector<int> tetk;            // [nk][24]: 4 * tetra + vertex position
+
+    rp::DevBuf d_coef, d_miller, d_npw, d_energy, d_T, d_tets, d_tetk;
+    rp::DevBuf d_einv[3];             // inverse-transform phases [N_axis][2 lb + 1]
+    rp::DevBuf d_err;                 // int error flags written by kernels
+    // scratch (grow-only)
+    rp::DevBuf s_box, s_u1, s_u2, s_u, s_p, s_t1, s_t2, s_m, s_w, s_chi, s_io1, s_io2, s_io3;
+
+    rp::QPlan plan;
+    // per-stage timing (CUDA events on the launching stream) and launch counts
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev[RP_NSTAGE];
+    int prof_used[RP_NSTAGE] = {0};
+    long long prof_launches[RP_NSTAGE] = {0};
+    std::string err;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace rp {
+
+int fail(rp_ctx* c, int code, const std::string& msg);
+void prof_begin(rp_ctx* c, int stage, cudaStream_t st);
+void prof_end(rp_ctx* c, int stage, cudaStream_t st, int launches);
+int cuda_fail(rp_ctx* c, cudaError_t e, const char* where);
+int ensure(rp_ctx* c, DevBuf& b, size_t bytes);
+void release(DevBuf& b);
+int plan_q(rp_ctx* c, const double q[3]);
+
+// ---- kernel launchers (each returns cudaError_t of the launch) ----
+// gather + inverse transform of nb bands into u[nb][N1][N2][N3] (complex double)
+cudaError_t launch_gather_inverse(rp_ctx* c, int k0, int nkb, cudaStream_t st);
+// pair densities of the bands prepared by launch_gather_inverse into M[ng][ld] at column col0
+cudaError_t launch_pair_forward(rp_ctx* c, int nkb, double2* M, long long ldm, long long col0,
+                                cudaStream_t st, int* nlaunch);
+// tetrahedron weights for all pairs: w[nf][K]
+cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double* d_freq,
+                         double delta, double delta_a, double delta_r, double2* w,
+                         cudaStream_t st);
+// chi[f] (+)= M diag(w[f][col0..]) M^H, FP64 tensor cores
+cudaError_t launch_contract_f64(const double2* M, long long ldm, long long K, const double2* w,
+                                long long ldw, long long col0, int nf, int ng, double2* chi,
+                                int accumulate, cudaStream_t st);
+// Dyson step
+cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W,
+                         int* err_flag, cudaStream_t st);
+
+}  // namespace rp

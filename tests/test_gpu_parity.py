@@ -1,0 +1,170 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (FP64 path): pair densities and weights agree to rounding of a few hundred
+operations (1e-12 relative to the largest element); chi0 and W per frequency to a
+relative Frobenius error of 1e-11, the bound the summation of ~1e4..1e6 FP64 terms and
+the Gauss-Jordan inverse of a well-conditioned NG x NG matrix leave.
+"""
+import numpy as np
+import pytest
+
+from conftest import workload
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import paper_2001_02351_gb300 as rp  # noqa: E402
+from oracle import chi0 as OC, dyson as OD, lattice as OL, pair_density as OP  # noqa: E402
+
+
+def _ctx(wl):
+    return rp.context_for(wl)
+
+
+def _axis(wl):
+    return rp.RP_AXIS_IMAG if wl.axis == "imag" else rp.RP_AXIS_REAL
+
+
+def _ordering(wl):
+    return rp.RP_TIME_ORDERED if wl.ordering == "time" else rp.RP_RETARDED
+
+
+def _rel_fro(a, b):
+    a = np.asarray(a).reshape(a.shape[0], -1)
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return workload("tiny")
+
+
+def test_sphere_matches_oracle(tiny):
+    ctx = _ctx(tiny)
+    q = tiny.q[0]
+    g, t = ctx.rp_sphere_size(q)
+    assert np.array_equal(g, OL.eps_sphere(tiny.cell.lat, q, tiny.ecut_eps[0]))
+    assert np.array_equal(t, OL.tail_sphere(tiny.cell.lat, q, tiny.ecut_eps[0], tiny.bands.ecut_psi))
+
+
+@pytest.mark.parametrize("name,krange", [("micro", (0, 8)), ("tiny", (5, 13)), ("small", (0, 27))])
+def test_pair_density(name, krange):
+    wl = workload(name)
+    ctx = _ctx(wl)
+    q = wl.q[0]
+    G = OL.eps_sphere(wl.cell.lat, q, wl.ecut_eps[0])
+    ref = OP.pair_density(wl.bands, wl.nocc, wl.nemp, q, G, fft=wl.fft, k_list=range(*krange))
+    got = ctx.rp_pair_density(q, *krange)
+    assert got.shape == ref.shape
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", ["micro", "small"])
+def test_tetra_weights(name):
+    wl = workload(name)
+    ctx = _ctx(wl)
+    q = wl.q[0]
+    ref = OC.pair_weights(wl, q)
+    got = ctx.rp_tetra_weights(q, _axis(wl), _ordering(wl), wl.freq, wl.delta, wl.delta_a, wl.delta_r)
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(got - ref) <= 1e-11 * scale)
+
+
+def test_tetra_weights_tiny_retarded_crpa():
+    from dataclasses import replace
+    wl = workload("tiny", crpa=True)
+    wl = replace(wl, axis="real", ordering="retarded", delta=0.01, freq=np.array([-0.3, 0.0, 0.2, 0.6]))
+    ctx = _ctx(wl)
+    q = wl.q[0]
+    ref = OC.pair_weights(wl, q, k_list=[0, 7, 21, 63])
+    got = ctx.rp_tetra_weights(q, rp.RP_AXIS_REAL, rp.RP_RETARDED, wl.freq, wl.delta)
+    cols = np.concatenate([np.arange(k * wl.nemp * wl.nocc, (k + 1) * wl.nemp * wl.nocc) for k in [0, 7, 21, 63]])
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(got[:, cols] - ref) <= 1e-11 * scale)
+
+
+@pytest.mark.parametrize("ng,K,nf", [(77, 1000, 3), (128, 64, 1), (5, 37, 2)])
+def test_contract_fp64(ng, K, nf):
+    rng = np.random.default_rng(ng * 1000 + K)
+    M = rng.standard_normal((ng, K)) + 1j * rng.standard_normal((ng, K))
+    w = rng.standard_normal((nf, K)) + 1j * rng.standard_normal((nf, K))
+    ctx = _ctx(workload("micro"))
+    got = ctx.rp_contract_chi0(M, w)
+    ref = OC.chi0(M, w)
+    assert np.all(_rel_fro(got, ref) < 1e-13)
+    # device pointers give the same result
+    Md = torch.from_numpy(M).cuda()
+    wd = torch.from_numpy(w).cuda()
+    gd = ctx.rp_contract_chi0(Md, wd)
+    torch.cuda.synchronize()
+    assert np.array_equal(gd.cpu().numpy(), got)
+
+
+@pytest.fixture(scope="module")
+def tiny_ref(tiny):
+    q = tiny.q[0]
+    G = OL.eps_sphere(tiny.cell.lat, q, tiny.ecut_eps[0])
+    M = OP.pair_density(tiny.bands, tiny.nocc, tiny.nemp, q, G, fft=tiny.fft)
+    w = OC.pair_weights(tiny, q)
+    chi = OC.chi0(M, w)
+    vs = OD.coulomb_sqrt(tiny.cell.lat, q, G)
+    return chi, OD.screened(chi, vs)
+
+
+def test_build_chi0_and_w_tiny(tiny, tiny_ref):
+    chi_ref, W_ref = tiny_ref
+    ctx = _ctx(tiny)
+    q = tiny.q[0]
+    chi = ctx.rp_build_chi0(q, _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, rp.RP_FP64_NATIVE)
+    assert np.all(_rel_fro(chi, chi_ref) < 1e-11)
+    W, tail = ctx.rp_solve_w(q, chi)
+    assert np.all(_rel_fro(W, W_ref) < 1e-11)
+    T = OL.tail_sphere(tiny.cell.lat, q, tiny.ecut_eps[0], tiny.bands.ecut_psi)
+    assert np.allclose(tail, OD.tail(tiny.cell.lat, q, T), rtol=1e-14, atol=0)
+    # the same through device pointers on torch's stream
+    chi_d = torch.empty((len(tiny.freq),) + chi.shape[1:], dtype=torch.complex128, device="cuda")
+    ctx.rp_build_chi0(q, _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, rp.RP_FP64_NATIVE, out=chi_d)
+    W_d, _ = ctx.rp_solve_w(q, chi_d)
+    torch.cuda.synchronize()
+    assert np.all(_rel_fro(chi_d.cpu().numpy(), chi_ref) < 1e-11)
+    assert np.all(_rel_fro(W_d.cpu().numpy(), W_ref) < 1e-11)
+
+
+def test_retarded_symmetry_on_gpu():
+    wl = workload("micro")
+    ctx = _ctx(wl)
+    q = wl.q[0]
+    freq = np.array([0.1, 0.3, -0.1, -0.3])
+    chi = ctx.rp_build_chi0(q, rp.RP_AXIS_REAL, rp.RP_RETARDED, freq, 0.02, rp.RP_FP64_NATIVE)
+    assert np.abs(chi[2:] - np.conj(chi[:2])).max() < 1e-13 * np.abs(chi).max()
+
+
+def test_errors_are_reported():
+    wl = workload("micro")
+    b = wl.bands
+    ctx = rp.Context(b.cell.lat, b.kmesh, wl.fft, b.ecut_psi, float(wl.ecut_eps[0]))
+    with pytest.raises(rp.RPError) as e:
+        ctx.nk, ctx.nemp, ctx.nocc = 8, 4, 4
+        ctx.rp_tetra_weights(wl.q[0], rp.RP_AXIS_IMAG, rp.RP_TIME_ORDERED, wl.freq, 0.0)
+    assert e.value.code == rp.RP_ERR_STATE
+    ctx = _ctx(wl)
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_sphere_size([0.3, 0.0, 0.0])           # not a mesh vector
+    assert e.value.code == rp.RP_ERR_ARG
+    with pytest.raises(rp.RPError) as e:              # pole on the real axis
+        ctx.rp_tetra_weights(wl.q[0], rp.RP_AXIS_REAL, rp.RP_TIME_ORDERED, wl.freq, 0.0)
+    assert e.value.code == rp.RP_ERR_ARG
+    # a non-finite chi0 makes the pivot search fail: reported, not faulted
+    q = wl.q[0]
+    G = OL.eps_sphere(wl.cell.lat, q, wl.ecut_eps[0])
+    vs = OD.coulomb_sqrt(wl.cell.lat, q, G)
+    chi = np.zeros((1, len(G), len(G)), dtype=np.complex128)
+    chi[0, :, 0] = np.nan
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_solve_w(q, chi)
+    assert e.value.code == rp.RP_ERR_NUMERIC
+    # the context stays usable afterwards
+    W, _ = ctx.rp_solve_w(q, np.zeros((1, len(G), len(G)), dtype=np.complex128))
+    assert np.allclose(W[0], np.diag(vs * vs), rtol=1e-14, atol=0)
