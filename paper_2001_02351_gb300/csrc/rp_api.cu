@@ -173,6 +173,30 @@ int plan_q(rp_ctx* c, const double q[3]) {
         st = upload(c, P.d_efwd32[a], e32.data(), e32.size() * sizeof(float));
         if (st) return st;
     }
+    // twiddle tables and residue maps of the fused line transforms
+    P.fused = true;
+    for (int a = 0; a < 3; ++a) {
+        const int N = c->fft[a];
+        std::vector<double> t(2 * N);
+        std::vector<float> t32(2 * N);
+        for (int e = 0; e < N; ++e) {
+            double ang = 2.0 * M_PI * (double)e / (double)N;
+            t[2 * e] = std::cos(ang); t[2 * e + 1] = std::sin(ang);
+            t32[2 * e] = (float)t[2 * e]; t32[2 * e + 1] = (float)t[2 * e + 1];
+        }
+        int st_ = upload(c, P.d_tw[a], t.data(), t.size() * sizeof(double));
+        if (st_) return st_;
+        if ((st_ = upload(c, P.d_tw32[a], t32.data(), t32.size() * sizeof(float)))) return st_;
+        if (a > 0) {
+            std::vector<int> map(N, -1);
+            for (int s_ = 0; s_ < P.nset[a]; ++s_) {
+                int r = ((P.setv[a][s_] % N) + N) % N;
+                if (map[r] >= 0) P.fused = false;     // two sphere values on one residue (aliasing)
+                map[r] = s_;
+            }
+            if ((st_ = upload(c, a == 2 ? P.d_zmap : P.d_ymap, map.data(), N * sizeof(int)))) return st_;
+        }
+    }
     int st;
     if ((st = upload(c, P.d_gpos, P.gpos.data(), P.gpos.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_kp, P.kp.data(), P.kp.size() * sizeof(int)))) return st;
@@ -261,6 +285,10 @@ int rp_setup_cell(const double lat[9], const int kmesh[3], const int fft[3], dou
     c->ecut_eps = ecut_eps_ha;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) { delete c; return RP_ERR_CUDA; }
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        delete c;
+        return RP_ERR_CUDA;
+    }
     if (ensure(c, c->d_err, 16 * sizeof(int)) || cudaMemset(c->d_err.p, 0, 16 * sizeof(int)) != cudaSuccess) {
         delete c;
         return RP_ERR_OOM;
@@ -320,6 +348,7 @@ int rp_load_bands(rp_ctx* c, int nk, int nband, int nocc, const int* npw, int np
     for (int a = 0; a < 3; ++a) {
         const int N = c->fft[a];
         std::vector<double> e(2 * (size_t)N * B);
+        std::vector<float> e32(2 * (size_t)N * B);
         for (int x = 0; x < N; ++x)
             for (int mi = 0; mi < B; ++mi) {
                 long long ph = ((long long)(mi - c->lb) * x) % N;
@@ -327,8 +356,11 @@ int rp_load_bands(rp_ctx* c, int nk, int nband, int nocc, const int* npw, int np
                 double ang = 2.0 * M_PI * (double)ph / (double)N;
                 e[2 * ((size_t)x * B + mi)] = std::cos(ang);
                 e[2 * ((size_t)x * B + mi) + 1] = std::sin(ang);
+                e32[2 * ((size_t)x * B + mi)] = (float)std::cos(ang);
+                e32[2 * ((size_t)x * B + mi) + 1] = (float)std::sin(ang);
             }
         if ((st = upload(c, c->d_einv[a], e.data(), e.size() * sizeof(double)))) return st;
+        if ((st = upload(c, c->d_einv32[a], e32.data(), e32.size() * sizeof(float)))) return st;
     }
     c->loaded = true;
     return RP_OK;
@@ -364,15 +396,23 @@ static int finish(rp_ctx* c, cudaStream_t st, int on_device) {
 }
 
 // pair densities of k in [k0, k1) into M (device) with leading dimension ldm, column col0
-static int pair_density_device(rp_ctx* c, int k0, int k1, double2* M, long long ldm, long long col0, cudaStream_t st) {
-    for (int k = k0; k < k1; ++k) {
+// M is complex double, or complex float when fp32 (split-precision tiers).  The k points are
+// taken in sub-blocks whose real-space grids stay within a scratch budget.
+static int pair_density_device(rp_ctx* c, int k0, int k1, void* M, bool fp32, long long ldm, long long col0,
+                               cudaStream_t st) {
+    const size_t per_k = (size_t)c->nband * c->nr * (fp32 ? sizeof(float2) : sizeof(double2));
+    const int kb = (int)std::max<size_t>(1, std::min<size_t>((size_t)(k1 - k0), ((size_t)2 << 30) / (3 * per_k)));
+    for (int k = k0; k < k1; k += kb) {
+        const int nkb = std::min(kb, k1 - k);
         prof_begin(c, 0, st);
-        cudaError_t e = launch_gather_inverse(c, k, 1, st);
+        cudaError_t e = launch_gather_inverse(c, k, nkb, fp32, st);
         prof_end(c, 0, st, 5);
         if (e != cudaSuccess) return cuda_fail(c, e, "gather/inverse transform");
         prof_begin(c, 1, st);
         int nl = 0;
-        e = launch_pair_forward(c, 1, M, ldm, col0 + (long long)(k - k0) * c->nemp * c->nocc, st, &nl);
+        const long long col = col0 + (long long)(k - k0) * c->nemp * c->nocc;
+        e = fp32 ? launch_pair_forward32(c, nkb, (float2*)M, ldm, col, st, &nl)
+                 : launch_pair_forward(c, nkb, (double2*)M, ldm, col, st, &nl);
         prof_end(c, 1, st, nl);
         if (e != cudaSuccess) return cuda_fail(c, e, "pair transform");
     }
@@ -391,7 +431,7 @@ int rp_pair_density(rp_ctx* c, const double q[3], int k_begin, int k_end, double
         if ((s = ensure(c, c->s_io1, bytes))) return s;
         M = (double2*)c->s_io1.p;
     }
-    if ((s = pair_density_device(c, k_begin, k_end, M, kcols, 0, st))) return s;
+    if ((s = pair_density_device(c, k_begin, k_end, M, false, kcols, 0, st))) return s;
     if (!on_device) {
         cudaError_t e = cudaMemcpyAsync(M_out, M, bytes, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "copy M");
@@ -452,11 +492,48 @@ int rp_tetra_weights(rp_ctx* c, const double q[3], int axis, int ordering, int n
     return finish(c, st, on_device);
 }
 
+// chi (+)= M[:, col0m .. col0m+K) diag(w[f][col0w ..]) M^H with the selected precision.
+// For RP_BF16X3 the caller zeroes chi before the first block.
+static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, long long ldm, long long col0m,
+                          long long K, const double2* w, long long ldw, long long col0w, int nfreq, int ng,
+                          double2* chi, int accumulate, cudaStream_t st) {
+    cudaError_t e;
+    if (precision == RP_FP64_NATIVE) {
+        prof_begin(c, 3, st);
+        e = launch_contract_f64((const double2*)M + col0m, ldm, K, w, ldw, col0w, nfreq, ng, chi, accumulate, st);
+        prof_end(c, 3, st, 1);
+        return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "contraction");
+    }
+    const size_t sb = (size_t)ng * tc_kp2(K) * 2;
+    int s;
+    if ((s = ensure(c, c->s_hi, sb)) || (s = ensure(c, c->s_lo, sb))) return s;
+    prof_begin(c, 3, st);
+    e = launch_split_bf16(M, m32, ldm, col0m, K, ng, c->s_hi.p, c->s_lo.p, st);
+    if (e == cudaSuccess)
+        e = launch_contract_bf16x3(c->s_hi.p, c->s_lo.p, K, ng, w, ldw, col0w, nfreq, chi, (int*)c->d_err.p + 1,
+                                   c->num_sms, st);
+    prof_end(c, 3, st, 2);
+    return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "bf16x3 contraction");
+}
+
+static int check_timeout(rp_ctx* c) {
+    int flag = 0;
+    if (cudaMemcpy(&flag, (int*)c->d_err.p + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "read timeout flag");
+    if (flag) {
+        cudaMemset((int*)c->d_err.p + 1, 0, sizeof(int));
+        char buf[96];
+        snprintf(buf, sizeof(buf), "a bounded device wait gave up (site %d)", flag);
+        return fail(c, RP_ERR_TIMEOUT, buf);
+    }
+    return RP_OK;
+}
+
 int rp_contract_chi0(rp_ctx* c, int ng, long long K, int nfreq, const double* M, const double* w, int precision,
                      double* chi_out, int on_device, void* stream) {
     if (!c) return RP_ERR_ARG;
     if (ng < 1 || K < 1 || nfreq < 1 || !M || !w || !chi_out) return fail(c, RP_ERR_ARG, "bad contraction arguments");
-    if (precision != RP_FP64_NATIVE) return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
+    if (precision != RP_FP64_NATIVE && precision != RP_BF16X3) return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
     cudaStream_t st = (cudaStream_t)stream;
     const double2 *dM = (const double2*)M, *dw = (const double2*)w;
     double2* dchi = (double2*)chi_out;
@@ -469,15 +546,17 @@ int rp_contract_chi0(rp_ctx* c, int ng, long long K, int nfreq, const double* M,
         cudaMemcpyAsync(c->s_io2.p, w, bw, cudaMemcpyHostToDevice, st);
         dM = (const double2*)c->s_io1.p; dw = (const double2*)c->s_io2.p; dchi = (double2*)c->s_chi.p;
     }
-    prof_begin(c, 3, st);
-    cudaError_t e = launch_contract_f64(dM, K, K, dw, K, 0, nfreq, ng, dchi, 0, st);
-    prof_end(c, 3, st, 1);
-    if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+    if (precision == RP_BF16X3) {
+        cudaError_t e = cudaMemsetAsync(dchi, 0, bc, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "zero chi");
+    }
+    if ((s = contract_block(c, precision, dM, false, K, 0, K, dw, K, 0, nfreq, ng, dchi, 0, st))) return s;
     if (!on_device) {
-        e = cudaMemcpyAsync(chi_out, dchi, bc, cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaMemcpyAsync(chi_out, dchi, bc, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "copy chi");
     }
-    return finish(c, st, on_device);
+    if ((s = finish(c, st, on_device))) return s;
+    return on_device ? RP_OK : check_timeout(c);
 }
 
 int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfreq, const double* freq,
@@ -486,13 +565,16 @@ int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfre
     if (s) return s;
     if ((s = check_freq(c, axis, ordering, nfreq, freq, delta, da, dr))) return s;
     if (!chi0_out) return fail(c, RP_ERR_ARG, "chi0_out is NULL");
-    if (precision != RP_FP64_NATIVE) return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
+    if (precision != RP_FP64_NATIVE && precision != RP_BF16X3) return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
     cudaStream_t st = (cudaStream_t)stream;
     const int ng = c->plan.ng;
     const long long K = (long long)c->nk * c->nemp * c->nocc;
     const long long kcols = (long long)c->nemp * c->nocc;
+    // k points per contraction launch: about 64k pair columns
+    const int kb = (int)std::max(1LL, std::min((long long)c->nk, 65536LL / kcols));
     if ((s = ensure(c, c->s_w, (size_t)nfreq * K * sizeof(double2)))) return s;
-    if ((s = ensure(c, c->s_m, (size_t)ng * kcols * sizeof(double2)))) return s;
+    const bool m32 = precision != RP_FP64_NATIVE;
+    if ((s = ensure(c, c->s_m, (size_t)ng * kcols * kb * (m32 ? sizeof(float2) : sizeof(double2))))) return s;
     const size_t bc = (size_t)nfreq * ng * ng * sizeof(double2);
     double2* chi = (double2*)chi0_out;
     if (!on_device) {
@@ -501,19 +583,25 @@ int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfre
     }
     double2* w = (double2*)c->s_w.p;
     if ((s = weights_device(c, axis, ordering, nfreq, freq, delta, da, dr, w, st))) return s;
-    double2* M = (double2*)c->s_m.p;
-    for (int k = 0; k < c->nk; ++k) {
-        if ((s = pair_density_device(c, k, k + 1, M, kcols, 0, st))) return s;
-        prof_begin(c, 3, st);
-        cudaError_t e = launch_contract_f64(M, kcols, kcols, w, K, (long long)k * kcols, nfreq, ng, chi, k > 0, st);
-        prof_end(c, 3, st, 1);
-        if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+    if (precision == RP_BF16X3) {
+        cudaError_t e = cudaMemsetAsync(chi, 0, bc, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "zero chi");
+    }
+    void* M = c->s_m.p;
+    for (int k0 = 0; k0 < c->nk; k0 += kb) {
+        const int k1 = std::min(c->nk, k0 + kb);
+        const long long cols = (long long)(k1 - k0) * kcols;
+        if ((s = pair_density_device(c, k0, k1, M, m32, cols, 0, st))) return s;
+        if ((s = contract_block(c, precision, M, m32, cols, 0, cols, w, K, (long long)k0 * kcols, nfreq, ng, chi,
+                                k0 > 0, st)))
+            return s;
     }
     if (!on_device) {
         cudaError_t e = cudaMemcpyAsync(chi0_out, chi, bc, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "copy chi0");
     }
-    return finish(c, st, on_device);
+    if ((s = finish(c, st, on_device))) return s;
+    return on_device ? RP_OK : check_timeout(c);
 }
 
 int rp_check_numeric(rp_ctx* c) {
@@ -608,11 +696,14 @@ const char* rp_last_error(const rp_ctx* c) {
 void rp_destroy(rp_ctx* c) {
     if (!c) return;
     DevBuf* bufs[] = {&c->d_coef, &c->d_miller, &c->d_npw, &c->d_energy, &c->d_T, &c->d_tets, &c->d_tetk,
-                      &c->d_einv[0], &c->d_einv[1], &c->d_einv[2], &c->d_err, &c->s_box, &c->s_u1, &c->s_u2,
+                      &c->d_einv[0], &c->d_einv[1], &c->d_einv[2], &c->d_einv32[0], &c->d_einv32[1],
+                      &c->d_einv32[2], &c->d_err, &c->s_box, &c->s_u1, &c->s_u2,
                       &c->s_u, &c->s_p, &c->s_t1, &c->s_t2, &c->s_m, &c->s_w, &c->s_chi, &c->s_io1, &c->s_io2,
-                      &c->s_io3, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
+                      &c->s_io3, &c->s_hi, &c->s_lo, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
-                      &c->plan.d_efwd32[1], &c->plan.d_efwd32[2]};
+                      &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_tw[0], &c->plan.d_tw[1],
+                      &c->plan.d_tw[2], &c->plan.d_tw32[0], &c->plan.d_tw32[1], &c->plan.d_tw32[2],
+                      &c->plan.d_zmap, &c->plan.d_ymap};
     for (DevBuf* b : bufs) release(*b);
     for (int i = 0; i < RP_NSTAGE; ++i)
         for (cudaEvent_t e : c->prof_ev[i]) cudaEventDestroy(e);

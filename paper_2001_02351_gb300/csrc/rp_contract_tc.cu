@@ -1,0 +1,454 @@
+// chi[f][G][G'] = sum_b w[f][b] M[G][b] conj(M[G'][b])   (Eq. chi)  --  BF16x3 on tcgen05.
+//
+// Real form of the complex product: with b running over pairs and the real index
+// k' = 2b + {0,1} interleaving (re, im), the G row of A is exactly the interleaved storage of
+// M[G][.], and for each G' the weighted operand B = w conj(M) contributes two rows:
+//   re-row (P, Q), im-row (-Q, P)  with  P = wr mr + wi mi,  Q = wr mi - wi mr,
+// so that  D[G][re-row G'] = Re chi[G][G'],  D[G][im-row G'] = Im chi[G][G'].
+// Each real operand x is split x = hi + lo into two bf16 and the product is
+// a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs), accumulated in FP32 in tensor memory and
+// flushed into FP64 every FLUSH_STAGES stages (double-buffered accumulators).
+//
+// CTA: 10 warps.  warp 0 = TMA producer (A_hi, A_lo rows of the G tile; the same arrays'
+// rows of the G' tile as raw B), warp 1 = MMA issuer, warps 2-5 = B builders (scale by w,
+// split, write the 128B-swizzled K-major tile), warps 6-9 = epilogue (tcgen05.ld -> FP64).
+// Tile: 128 G rows x (64 G' re-rows + 64 G' im-rows), K step 64 reals per stage.
+// Every wait is bounded; a wait that gives up records where in err_flag[1] and the CTA
+// leaves through the common teardown (its copies in flight are waited for, TMEM is freed).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "rp_internal.h"
+
+namespace rp {
+
+#define TC_NS 3                 // load stages
+#define TC_BM 128               // G rows per tile
+#define TC_BN 64                // G' per tile (128 real columns)
+#define TC_BK 64                // reals per stage
+#define TC_FLUSH_STAGES 128     // stages per FP32 accumulation window (8192 reals)
+#define TC_THREADS 320
+
+#define TC_A_BYTES (TC_BM * TC_BK * 2)            // 16 KB
+#define TC_R_BYTES (TC_BN * TC_BK * 2)            // 8 KB
+#define TC_STAGE_BYTES (2 * TC_A_BYTES + 2 * TC_R_BYTES)   // 48 KB
+#define TC_B_BYTES (2 * TC_BN * TC_BK * 2)        // 16 KB (128 rows)
+#define TC_SMEM_B0 (TC_NS * TC_STAGE_BYTES)
+#define TC_SMEM_BAR (TC_SMEM_B0 + 2 * 2 * TC_B_BYTES)
+#define TC_SMEM_TOTAL (TC_SMEM_BAR + 256 + 1024)
+
+#define TC_WAIT_NS 2000000000ULL   // a wait gives up after 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: false (and err_flag set to `code`) if the phase does not complete within TC_WAIT_NS
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try(bar, parity)) return true;
+        if (gtimer() - t0 > TC_WAIT_NS) break;
+    }
+    atomicExch(err, code);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// kind::f16 instruction descriptor: D f32, A bf16, B bf16, both K-major, M = 128, N = 128
+__host__ __device__ constexpr uint32_t tc_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(tc_idesc()), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t sw128_off(int row, int chunk) {
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void split2(float x, float& hi, float& lo) {
+    hi = __bfloat162float(__float2bfloat16_rn(x));
+    lo = x - hi;
+}
+
+struct TcArgs {
+    const double2* w;
+    long long ldw, col0, K;
+    int ng, nf, mt, nt, nst;
+    double2* chi;
+    int* err;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_contract_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+                      TcArgs args) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = sbase + TC_SMEM_BAR;
+    // barriers: full[NS], empty[NS], bready[2], bfree[2], accf[2], acce[2], done
+    auto full = [&](int s) { return bar0 + 8 * s; };
+    auto empty = [&](int s) { return bar0 + 8 * (TC_NS + s); };
+    auto bready = [&](int b) { return bar0 + 8 * (2 * TC_NS + b); };
+    auto bfree = [&](int b) { return bar0 + 8 * (2 * TC_NS + 2 + b); };
+    auto accf = [&](int b) { return bar0 + 8 * (2 * TC_NS + 4 + b); };
+    auto acce = [&](int b) { return bar0 + 8 * (2 * TC_NS + 6 + b); };
+    const uint32_t done_bar = bar0 + 8 * (2 * TC_NS + 8);
+    uint32_t* taddr_slot = (uint32_t*)(smem + TC_SMEM_BAR + 8 * (2 * TC_NS + 9));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_NS; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 128 + 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bready(b), 128);
+            mbar_init(bfree(b), 1);
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), 128);
+        }
+        mbar_init(done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(taddr_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *taddr_slot;
+
+    const int njobs = args.nf * args.mt * args.nt;
+    const int nst = args.nst;
+    const int nchunk = (nst + TC_FLUSH_STAGES - 1) / TC_FLUSH_STAGES;
+    int* err = args.err;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            long long sg = 0;
+            bool ok = true;
+            for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
+                const int rem = job % (args.mt * args.nt);
+                const int m0 = (rem / args.nt) * TC_BM, n0 = (rem % args.nt) * TC_BN;
+                for (int st = 0; st < nst; ++st, ++sg) {
+                    const int s = (int)(sg % TC_NS);
+                    const uint32_t ph = (uint32_t)((sg / TC_NS) & 1);
+                    if (!(ok = mbar_wait(empty(s), ph ^ 1, err, 101))) break;
+                    const uint32_t base = sbase + s * TC_STAGE_BYTES;
+                    mbar_expect_tx(full(s), TC_STAGE_BYTES);
+                    const int x = st * TC_BK;
+                    tma_load_2d(base, &map_hi, x, m0, full(s));
+                    tma_load_2d(base + TC_A_BYTES / 2, &map_hi, x, m0 + 64, full(s));
+                    tma_load_2d(base + TC_A_BYTES, &map_lo, x, m0, full(s));
+                    tma_load_2d(base + TC_A_BYTES + TC_A_BYTES / 2, &map_lo, x, m0 + 64, full(s));
+                    tma_load_2d(base + 2 * TC_A_BYTES, &map_hi, x, n0, full(s));
+                    tma_load_2d(base + 2 * TC_A_BYTES + TC_R_BYTES, &map_lo, x, n0, full(s));
+                }
+            }
+            // copies still in flight land before the CTA leaves
+            for (long long k = (sg > TC_NS ? sg - TC_NS : 0); k < sg; ++k)
+                mbar_wait(full((int)(k % TC_NS)), (uint32_t)((k / TC_NS) & 1), err, 102);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            long long sg = 0, cg = 0;
+            bool ok = true;
+            for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
+                for (int ch = 0; ch < nchunk && ok; ++ch, ++cg) {
+                    const int ab = (int)(cg & 1);
+                    if (!(ok = mbar_wait(acce(ab), (uint32_t)(((cg >> 1) & 1) ^ 1), err, 111))) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t d = tmem + (uint32_t)(ab * 128);
+                    const int st1 = min(nst, (ch + 1) * TC_FLUSH_STAGES);
+                    for (int st = ch * TC_FLUSH_STAGES; st < st1; ++st, ++sg) {
+                        const int s = (int)(sg % TC_NS);
+                        const int bb = (int)(sg & 1);
+                        if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 112))) break;
+                        if (!(ok = mbar_wait(bready(bb), (uint32_t)((sg >> 1) & 1), err, 113))) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a_hi = sbase + s * TC_STAGE_BYTES, a_lo = a_hi + TC_A_BYTES;
+                        const uint32_t b_hi = sbase + TC_SMEM_B0 + bb * 2 * TC_B_BYTES, b_lo = b_hi + TC_B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                            const uint32_t off = kk * 32;
+                            const uint32_t first = (st == ch * TC_FLUSH_STAGES && kk == 0) ? 0u : 1u;
+                            mma_bf16(d, sw128_desc(a_hi + off), sw128_desc(b_hi + off), first);
+                            mma_bf16(d, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
+                            mma_bf16(d, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+                        }
+                        mma_commit(empty(s));
+                        mma_commit(bfree(bb));
+                    }
+                    if (ok) mma_commit(accf(ab));
+                }
+            }
+            // all issued MMAs complete before teardown
+            mma_commit(done_bar);
+            mbar_wait(done_bar, 0, err, 114);
+        }
+    } else if (warp < 6) {
+        // ---------------- B builders (128 threads) ----------------
+        const int t = threadIdx.x - 64;
+        long long sg = 0;
+        bool ok = true;
+        for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
+            const int f = job / (args.mt * args.nt);
+            const double2* wf = args.w + (size_t)f * args.ldw + args.col0;
+            for (int st = 0; st < nst; ++st, ++sg) {
+                const int s = (int)(sg % TC_NS);
+                const int bb = (int)(sg & 1);
+                if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 121))) break;
+                if (!(ok = mbar_wait(bfree(bb), (uint32_t)(((sg >> 1) & 1) ^ 1), err, 122))) break;
+                const unsigned char* rhi = smem + s * TC_STAGE_BYTES + 2 * TC_A_BYTES;
+                const unsigned char* rlo = rhi + TC_R_BYTES;
+                unsigned char* bhi = smem + TC_SMEM_B0 + bb * 2 * TC_B_BYTES;
+                unsigned char* blo = bhi + TC_B_BYTES;
+#pragma unroll
+                for (int it = 0; it < (TC_BN * 8) / 128; ++it) {
+                    const int task = t + it * 128;
+                    const int r = task >> 3, c = task & 7;
+                    const uint32_t o = sw128_off(r, c);
+                    const uint4 vh = *reinterpret_cast<const uint4*>(rhi + o);
+                    const uint4 vl = *reinterpret_cast<const uint4*>(rlo + o);
+                    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&vh);
+                    const __nv_bfloat162* l2 = reinterpret_cast<const __nv_bfloat162*>(&vl);
+                    uint32_t reh[4], rel[4], imh[4], iml[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 hh = __bfloat1622float2(h2[i]);
+                        const float2 ll = __bfloat1622float2(l2[i]);
+                        const float mr = hh.x + ll.x, mi = hh.y + ll.y;
+                        const long long b = (long long)st * (TC_BK / 2) + 4 * c + i;
+                        float wr = 0.f, wi = 0.f;
+                        if (b < args.K) {
+                            const double2 wv = wf[b];
+                            wr = (float)wv.x;
+                            wi = (float)wv.y;
+                        }
+                        const float P = wr * mr + wi * mi;
+                        const float Q = wr * mi - wi * mr;
+                        float ph, pl, qh, ql;
+                        split2(P, ph, pl);
+                        split2(Q, qh, ql);
+                        reh[i] = pack_bf16(ph, qh);
+                        rel[i] = pack_bf16(pl, ql);
+                        imh[i] = pack_bf16(-qh, ph);
+                        iml[i] = pack_bf16(-ql, pl);
+                    }
+                    *reinterpret_cast<uint4*>(bhi + sw128_off(r, c)) = make_uint4(reh[0], reh[1], reh[2], reh[3]);
+                    *reinterpret_cast<uint4*>(blo + sw128_off(r, c)) = make_uint4(rel[0], rel[1], rel[2], rel[3]);
+                    *reinterpret_cast<uint4*>(bhi + sw128_off(r + TC_BN, c)) = make_uint4(imh[0], imh[1], imh[2], imh[3]);
+                    *reinterpret_cast<uint4*>(blo + sw128_off(r + TC_BN, c)) = make_uint4(iml[0], iml[1], iml[2], iml[3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(empty(s));
+                mbar_arrive(bready(bb));
+            }
+        }
+    } else {
+        // ---------------- epilogue (128 threads, TMEM lanes by warp % 4) ----------------
+        const int q4 = warp & 3;
+        const int row_in_tile = q4 * 32 + lane;
+        long long cg = 0;
+        bool ok = true;
+        for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
+            const int f = job / (args.mt * args.nt);
+            const int rem = job % (args.mt * args.nt);
+            const int m0 = (rem / args.nt) * TC_BM, n0 = (rem % args.nt) * TC_BN;
+            const int g = m0 + row_in_tile;
+            double2* out = args.chi + (size_t)f * args.ng * args.ng + (size_t)g * args.ng;
+            for (int ch = 0; ch < nchunk; ++ch, ++cg) {
+                const int ab = (int)(cg & 1);
+                if (!(ok = mbar_wait(accf(ab), (uint32_t)((cg >> 1) & 1), err, 131))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * 128);
+                float v[2][64];
+#pragma unroll
+                for (int part = 0; part < 4; ++part) {
+                    uint32_t r[32];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                        : "r"(src + (uint32_t)(part * 32)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[part >> 1][(part & 1) * 32 + i] = __uint_as_float(r[i]);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(acce(ab));
+                if (g < args.ng) {
+#pragma unroll
+                    for (int j = 0; j < TC_BN; ++j) {
+                        const int gp = n0 + j;
+                        if (gp < args.ng) {
+                            double2 o = out[gp];
+                            o.x += (double)v[0][j];
+                            o.y += (double)v[1][j];
+                            out[gp] = o;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+}
+
+// hi/lo bf16 split of M (complex double [ng][ldm] from column col0, K columns) into
+// real arrays [ng][kp2] (kp2 = 2 * K rounded up to 64), zero padded
+template <typename CI>
+__global__ void k_split_bf16(const CI* __restrict__ M, long long ldm, long long col0, long long K, int ng,
+                             long long kp2, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long half = kp2 / 2;
+    if (t >= (long long)ng * half) return;
+    const int g = (int)(t / half);
+    const long long b = t % half;
+    float x = 0.f, y = 0.f;
+    if (b < K) {
+        const CI v = M[(size_t)g * ldm + col0 + b];
+        x = (float)v.x;
+        y = (float)v.y;
+    }
+    const __nv_bfloat16 hx = __float2bfloat16_rn(x), hy = __float2bfloat16_rn(y);
+    const __nv_bfloat16 lx = __float2bfloat16_rn(x - __bfloat162float(hx));
+    const __nv_bfloat16 ly = __float2bfloat16_rn(y - __bfloat162float(hy));
+    __nv_bfloat162 h2, l2;
+    h2.x = hx; h2.y = hy;
+    l2.x = lx; l2.y = ly;
+    reinterpret_cast<__nv_bfloat162*>(hi)[t] = h2;
+    reinterpret_cast<__nv_bfloat162*>(lo)[t] = l2;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+static bool make_map(CUtensorMap* map, void* base, int ng, long long kp2) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)kp2, (cuuint64_t)ng};
+    cuuint64_t strides[1] = {(cuuint64_t)kp2 * 2};
+    cuuint32_t box[2] = {TC_BK, 64};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+long long tc_kp2(long long K) { return ((2 * K + TC_BK - 1) / TC_BK) * TC_BK; }
+
+cudaError_t launch_split_bf16(const void* M, bool m32, long long ldm, long long col0, long long K, int ng, void* hi,
+                              void* lo, cudaStream_t st) {
+    const long long kp2 = tc_kp2(K);
+    const long long n = (long long)ng * (kp2 / 2);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (m32)
+        k_split_bf16<float2><<<grid, 256, 0, st>>>((const float2*)M, ldm, col0, K, ng, kp2, (__nv_bfloat16*)hi,
+                                                   (__nv_bfloat16*)lo);
+    else
+        k_split_bf16<double2><<<grid, 256, 0, st>>>((const double2*)M, ldm, col0, K, ng, kp2, (__nv_bfloat16*)hi,
+                                                    (__nv_bfloat16*)lo);
+    return cudaGetLastError();
+}
+
+// chi (+)= ... over the K pairs whose bf16 split is in hi/lo ([ng][kp2]); chi must be zeroed by
+// the caller before the first accumulation
+cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, int ng, const double2* w,
+                                   long long ldw, long long col0, int nf, double2* chi, int* err, int num_sms,
+                                   cudaStream_t st) {
+    const long long kp2 = tc_kp2(K);
+    CUtensorMap mhi, mlo;
+    if (!make_map(&mhi, const_cast<void*>(hi), ng, kp2) || !make_map(&mlo, const_cast<void*>(lo), ng, kp2))
+        return cudaErrorInvalidValue;
+    TcArgs a;
+    a.w = w; a.ldw = ldw; a.col0 = col0; a.K = K;
+    a.ng = ng; a.nf = nf;
+    a.mt = (ng + TC_BM - 1) / TC_BM;
+    a.nt = (ng + TC_BN - 1) / TC_BN;
+    a.nst = (int)(kp2 / TC_BK);
+    a.chi = chi; a.err = err;
+    const int njobs = nf * a.mt * a.nt;
+    cudaError_t e = cudaFuncSetAttribute(k_contract_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_TOTAL);
+    if (e != cudaSuccess) return e;
+    const int grid = njobs < num_sms ? njobs : num_sms;
+    k_contract_bf16x3<<<grid, TC_THREADS, TC_SMEM_TOTAL, st>>>(mhi, mlo, a);
+    return cudaGetLastError();
+}
+
+}  // namespace rp

@@ -34,6 +34,10 @@ struct QPlan {
     std::vector<int> setv[3];        // the values
     std::vector<int> gpos;           // [ng][3] position of each G's components in the sets
     DevBuf d_gpos, d_efwd[3], d_efwd32[3], d_kp, d_g0, d_vs;
+    // line-transform twiddles exp(2 pi i e / N_axis), e = 0..N_axis-1, and residue maps
+    // (grid index -> position in the axis set, -1 if absent) for the fused pair kernels
+    bool fused = false;
+    DevBuf d_tw[3], d_tw32[3], d_zmap, d_ymap;
 };
 
 }  // namespace rp
@@ -57,9 +61,12 @@ struct rp_ctx {
 
     rp::DevBuf d_coef, d_miller, d_npw, d_energy, d_T, d_tets, d_tetk;
     rp::DevBuf d_einv[3];             // inverse-transform phases [N_axis][2 lb + 1]
+    rp::DevBuf d_einv32[3];           // the same in FP32
     rp::DevBuf d_err;                 // int error flags written by kernels
     // scratch (grow-only)
     rp::DevBuf s_box, s_u1, s_u2, s_u, s_p, s_t1, s_t2, s_m, s_w, s_chi, s_io1, s_io2, s_io3;
+    rp::DevBuf s_hi, s_lo;            // bf16 hi/lo split of a block of pair densities
+    int num_sms = 0;
 
     rp::QPlan plan;
     // per-stage timing (CUDA events on the launching stream) and launch counts
@@ -83,10 +90,13 @@ int plan_q(rp_ctx* c, const double q[3]);
 
 // ---- kernel launchers (each returns cudaError_t of the launch) ----
 // gather + inverse transform of nb bands into u[nb][N1][N2][N3] (complex double)
-cudaError_t launch_gather_inverse(rp_ctx* c, int k0, int nkb, cudaStream_t st);
+cudaError_t launch_gather_inverse(rp_ctx* c, int k0, int nkb, bool fp32, cudaStream_t st);
 // pair densities of the bands prepared by launch_gather_inverse into M[ng][ld] at column col0
 cudaError_t launch_pair_forward(rp_ctx* c, int nkb, double2* M, long long ldm, long long col0,
                                 cudaStream_t st, int* nlaunch);
+// the same in FP32 (for the split-precision tiers), M as complex float
+cudaError_t launch_pair_forward32(rp_ctx* c, int nkb, float2* M, long long ldm, long long col0,
+                                  cudaStream_t st, int* nlaunch);
 // tetrahedron weights for all pairs: w[nf][K]
 cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double* d_freq,
                          double delta, double delta_a, double delta_r, double2* w,
@@ -95,6 +105,13 @@ cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double
 cudaError_t launch_contract_f64(const double2* M, long long ldm, long long K, const double2* w,
                                 long long ldw, long long col0, int nf, int ng, double2* chi,
                                 int accumulate, cudaStream_t st);
+// BF16x3 tcgen05 contraction: split, then chi (+)= over the split block (chi zeroed by the caller)
+long long tc_kp2(long long K);
+cudaError_t launch_split_bf16(const void* M, bool m32, long long ldm, long long col0, long long K, int ng,
+                              void* hi, void* lo, cudaStream_t st);
+cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, int ng, const double2* w,
+                                   long long ldw, long long col0, int nf, double2* chi, int* err, int num_sms,
+                                   cudaStream_t st);
 // Dyson step
 cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W,
                          int* err_flag, cudaStream_t st);

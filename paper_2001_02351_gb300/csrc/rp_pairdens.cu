@@ -10,6 +10,7 @@
 // Every transform stage is a pruned discrete Fourier sum along one axis written as a
 // batched product with a small phase matrix E[out][in].
 #include "rp_internal.h"
+#include "rp_fft.cuh"
 
 namespace rp {
 
@@ -29,10 +30,11 @@ struct CT<float2> {
 // Scatter the plane-wave coefficients of the bands of k into boxes [band][B][B][B].
 // Slot s < nocc: occupied band s at k.  Slot s >= nocc: empty band s at k' = kp[k],
 // placed at Miller index m - G0(k), so that its transform is u~_a(r) = sum C e^{i(G-G0).r}.
+template <typename C>
 __global__ void k_scatter_box(const double2* __restrict__ coef, const int* __restrict__ miller,
                               const int* __restrict__ npw, int npw_max, int nband, int nocc,
                               const int* __restrict__ kp, const int* __restrict__ g0, int k0, int nkb,
-                              int lb, double2* __restrict__ box) {
+                              int lb, C* __restrict__ box) {
     const int B = 2 * lb + 1;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long total = (long long)nkb * nband * npw_max;
@@ -48,7 +50,8 @@ __global__ void k_scatter_box(const double2* __restrict__ coef, const int* __res
     if (s >= nocc) { sh0 = g0[3 * k]; sh1 = g0[3 * k + 1]; sh2 = g0[3 * k + 2]; }
     int i0 = m[0] - sh0 + lb, i1 = m[1] - sh1 + lb, i2 = m[2] - sh2 + lb;
     size_t dst = (((size_t)(kl * nband + s) * B + i0) * B + i1) * B + i2;
-    box[dst] = coef[((size_t)ks * nband + s) * npw_max + p];
+    const double2 v = coef[((size_t)ks * nband + s) * npw_max + p];
+    box[dst] = CT<C>::make((typename CT<C>::R)v.x, (typename CT<C>::R)v.y);
 }
 
 // Y[b][j][c] = sum_i E[j][i] X[b][i][c]   (one output per thread, c fastest)
@@ -91,10 +94,10 @@ __global__ void k_pair_product(const C* __restrict__ u, long long nr, int nocc, 
 }
 
 // M[g][col0 + pair] = (1/Nr) sum_x Ex[gx(g)][x] T2[pair][x][gy(g)][gz(g)]
-template <typename C>
+template <typename C, typename CO>
 __global__ void k_sphere_readout(const C* __restrict__ T2, const C* __restrict__ Ex,
                                  const int* __restrict__ gpos, int ng, int npair, int n1, int ny,
-                                 int nz, typename CT<C>::R scale, double2* __restrict__ M,
+                                 int nz, typename CT<C>::R scale, CO* __restrict__ M,
                                  long long ldm, long long col0) {
     using R = typename CT<C>::R;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -112,91 +115,267 @@ __global__ void k_sphere_readout(const C* __restrict__ T2, const C* __restrict__
         re += w.x * v.x - w.y * v.y;
         im += w.x * v.y + w.y * v.x;
     }
-    M[(size_t)g * ldm + col0 + pr] = make_double2((double)(re * scale), (double)(im * scale));
+    M[(size_t)g * ldm + col0 + pr] = CT<CO>::make((typename CT<CO>::R)(re * scale), (typename CT<CO>::R)(im * scale));
 }
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-cudaError_t launch_gather_inverse(rp_ctx* c, int k0, int nkb, cudaStream_t st) {
+// ---- fused pair kernels (line transforms in registers) ----
+
+// product and z transform: one (pair, x, y) line per thread, pruned to the z values of the sphere
+// u holds the bands of nkb k points ([kl][band][line][z]); grid.z runs over (kl, pa), pa < nab;
+// T1 pair index (kl * nab + pa) * nocc + o
+template <typename C, int N3>
+__global__ void __launch_bounds__(128) k_pair_z(const C* __restrict__ u, int nband, int nocc, int a0, int nab,
+                                                int nlines, const int* __restrict__ zmap, int nz,
+                                                const C* __restrict__ tw, C* __restrict__ T1) {
+    const int line = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int o = blockIdx.y * 4 + (threadIdx.x >> 5);
+    const int kl = blockIdx.z / nab, pa = blockIdx.z % nab;
+    if (line >= nlines || o >= nocc) return;
+    const C* uk = u + (size_t)kl * nband * nlines * N3;
+    const C* ua = uk + ((size_t)(nocc + a0 + pa) * nlines + line) * N3;
+    const C* uo = uk + ((size_t)o * nlines + line) * N3;
+    C x[N3];
+#pragma unroll
+    for (int z = 0; z < N3; ++z) x[z] = c_conjmul(ua[z], uo[z]);
+    LineFFT<C, N3, 1>::run(x, tw);
+    C* dst = T1 + ((size_t)(blockIdx.z * nocc + o) * nlines + line) * nz;
+#pragma unroll
+    for (int z = 0; z < N3; ++z) {
+        const int iz = zmap[z];
+        if (iz >= 0) dst[iz] = x[z];
+    }
+}
+
+// y transform (pruned) of PPC pairs per CTA into shared memory, then the x sum on the sphere points
+template <typename C, int N2, int PPC, typename CO>
+__global__ void __launch_bounds__(256) k_pair_yx(const C* __restrict__ T1, int npair, int N1, int nz,
+                                                 const int* __restrict__ ymap, int ny, const C* __restrict__ tw,
+                                                 const C* __restrict__ Ex, const int* __restrict__ gpos, int ng,
+                                                 typename Cx<C>::R scale, CO* __restrict__ M, long long ldm,
+                                                 long long col0) {
+    using R = typename Cx<C>::R;
+    extern __shared__ __align__(16) unsigned char sm_yx[];
+    C* T2 = (C*)sm_yx;   // [PPC][N1][ny][nz]
+    const int p0 = blockIdx.x * PPC;
+    const int tile = N1 * ny * nz;
+    for (int ln = threadIdx.x; ln < PPC * N1 * nz; ln += blockDim.x) {
+        const int j = ln / (N1 * nz);
+        const int x = (ln / nz) % N1, iz = ln % nz;
+        if (p0 + j >= npair) continue;
+        const C* src = T1 + ((size_t)(p0 + j) * N1 + x) * N2 * nz + iz;
+        C v[N2];
+#pragma unroll
+        for (int y = 0; y < N2; ++y) v[y] = src[(size_t)y * nz];
+        LineFFT<C, N2, 1>::run(v, tw);
+#pragma unroll
+        for (int y = 0; y < N2; ++y) {
+            const int iy = ymap[y];
+            if (iy >= 0) T2[j * tile + (x * ny + iy) * nz + iz] = v[y];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ng * PPC; t += blockDim.x) {
+        const int j = t % PPC, g = t / PPC;
+        if (p0 + j >= npair) continue;
+        const int gx = gpos[3 * g], gy = gpos[3 * g + 1], gz = gpos[3 * g + 2];
+        const C* src = T2 + j * tile + gy * nz + gz;
+        const C* e = Ex + (size_t)gx * N1;
+        R re = 0, im = 0;
+        for (int x = 0; x < N1; ++x) {
+            const C v = src[x * ny * nz];
+            const C w = e[x];
+            re += w.x * v.x - w.y * v.y;
+            im += w.x * v.y + w.y * v.x;
+        }
+        M[(size_t)g * ldm + col0 + p0 + j] = CT<CO>::make((typename CT<CO>::R)(re * scale), (typename CT<CO>::R)(im * scale));
+    }
+}
+
+template <typename C, int N3>
+static void launch_z(const C* u, int nkb, int nband, int nocc, int a0, int nab, int nlines, const int* zmap, int nz,
+                     const C* tw, C* T1, cudaStream_t st) {
+    dim3 grid((nlines + 31) / 32, (nocc + 3) / 4, nkb * nab);
+    k_pair_z<C, N3><<<grid, 128, 0, st>>>(u, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1);
+}
+
+template <typename C, int N2, typename CO>
+static void launch_yx(const C* T1, int npair, int N1, int nz, const int* ymap, int ny, const C* tw, const C* Ex,
+                      const int* gpos, int ng, typename Cx<C>::R scale, CO* M, long long ldm, long long col0,
+                      cudaStream_t st) {
+    constexpr int PPC = sizeof(C) == 8 ? 4 : 2;
+    const size_t smem = (size_t)PPC * N1 * ny * nz * sizeof(C);
+    cudaFuncSetAttribute(k_pair_yx<C, N2, PPC, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_pair_yx<C, N2, PPC, CO><<<(npair + PPC - 1) / PPC, 256, smem, st>>>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos,
+                                                                         ng, scale, M, ldm, col0);
+}
+
+// dispatch on the compile-time line lengths this build instantiates; false if not available
+template <typename C>
+static bool fused_z(int n, const C* u, int nkb, int nband, int nocc, int a0, int nab, int nlines, const int* zmap,
+                    int nz, const C* tw, C* T1, cudaStream_t st) {
+    switch (n) {
+        case 8: launch_z<C, 8>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
+        case 12: launch_z<C, 12>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
+        case 16: launch_z<C, 16>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
+        case 24: launch_z<C, 24>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
+        case 32: launch_z<C, 32>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
+        case 48: launch_z<C, 48>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
+        default: return false;
+    }
+}
+
+template <typename C, typename CO>
+static bool fused_yx(int n, const C* T1, int npair, int N1, int nz, const int* ymap, int ny, const C* tw,
+                     const C* Ex, const int* gpos, int ng, typename Cx<C>::R scale, CO* M, long long ldm,
+                     long long col0, cudaStream_t st) {
+    constexpr int PPC = sizeof(C) == 8 ? 4 : 2;
+    if ((size_t)PPC * N1 * ny * nz * sizeof(C) > 200 * 1024) return false;
+    switch (n) {
+        case 8: launch_yx<C, 8, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 12: launch_yx<C, 12, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 16: launch_yx<C, 16, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 24: launch_yx<C, 24, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 32: launch_yx<C, 32, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 48: launch_yx<C, 48, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        default: return false;
+    }
+}
+
+
+template <typename C>
+static cudaError_t gather_inverse_t(rp_ctx* c, int k0, int nkb, const C* const einv[3], cudaStream_t st) {
     const int B = 2 * c->lb + 1;
     const int N1 = c->fft[0], N2 = c->fft[1], N3 = c->fft[2];
     const long long nbands = (long long)nkb * c->nband;
     const size_t box = (size_t)nbands * B * B * B, u1 = (size_t)nbands * N1 * B * B,
                  u2 = (size_t)nbands * N1 * N2 * B, uu = (size_t)nbands * c->nr;
-    if (ensure(c, c->s_box, box * sizeof(double2)) || ensure(c, c->s_u1, u1 * sizeof(double2)) ||
-        ensure(c, c->s_u2, u2 * sizeof(double2)) || ensure(c, c->s_u, uu * sizeof(double2)))
+    if (ensure(c, c->s_box, box * sizeof(C)) || ensure(c, c->s_u1, u1 * sizeof(C)) ||
+        ensure(c, c->s_u2, u2 * sizeof(C)) || ensure(c, c->s_u, uu * sizeof(C)))
         return cudaErrorMemoryAllocation;
-    double2* dbox = (double2*)c->s_box.p;
-    cudaError_t e = cudaMemsetAsync(dbox, 0, box * sizeof(double2), st);
+    C* dbox = (C*)c->s_box.p;
+    cudaError_t e = cudaMemsetAsync(dbox, 0, box * sizeof(C), st);
     if (e != cudaSuccess) return e;
     const int bs = 256;
     long long n = (long long)nkb * c->nband * c->npw_max;
-    k_scatter_box<<<grid_for(n, bs), bs, 0, st>>>((const double2*)c->d_coef.p, (const int*)c->d_miller.p,
-                                                  (const int*)c->d_npw.p, c->npw_max, c->nband, c->nocc,
-                                                  (const int*)c->plan.d_kp.p, (const int*)c->plan.d_g0.p, k0,
-                                                  nkb, c->lb, dbox);
+    k_scatter_box<C><<<grid_for(n, bs), bs, 0, st>>>((const double2*)c->d_coef.p, (const int*)c->d_miller.p,
+                                                     (const int*)c->d_npw.p, c->npw_max, c->nband, c->nocc,
+                                                     (const int*)c->plan.d_kp.p, (const int*)c->plan.d_g0.p, k0,
+                                                     nkb, c->lb, dbox);
     // m1 -> x
     n = nbands * N1 * (long long)B * B;
-    k_axis_pass<double2><<<grid_for(n, bs), bs, 0, st>>>(dbox, (double2*)c->s_u1.p, (const double2*)c->d_einv[0].p,
-                                                         nbands, B, N1, B * B, (long long)B * B * B, (long long)B * B,
-                                                         (long long)N1 * B * B, (long long)B * B);
+    k_axis_pass<C><<<grid_for(n, bs), bs, 0, st>>>(dbox, (C*)c->s_u1.p, einv[0], nbands, B, N1, B * B,
+                                                   (long long)B * B * B, (long long)B * B, (long long)N1 * B * B,
+                                                   (long long)B * B);
     // m2 -> y
     n = nbands * N1 * (long long)N2 * B;
-    k_axis_pass<double2><<<grid_for(n, bs), bs, 0, st>>>((const double2*)c->s_u1.p, (double2*)c->s_u2.p,
-                                                         (const double2*)c->d_einv[1].p, nbands * N1, B, N2, B,
-                                                         (long long)B * B, (long long)B, (long long)N2 * B,
-                                                         (long long)B);
+    k_axis_pass<C><<<grid_for(n, bs), bs, 0, st>>>((const C*)c->s_u1.p, (C*)c->s_u2.p, einv[1], nbands * N1, B, N2, B,
+                                                   (long long)B * B, (long long)B, (long long)N2 * B, (long long)B);
     // m3 -> z
     n = nbands * N1 * (long long)N2 * N3;
-    k_axis_pass<double2><<<grid_for(n, bs), bs, 0, st>>>((const double2*)c->s_u2.p, (double2*)c->s_u.p,
-                                                         (const double2*)c->d_einv[2].p, nbands * N1 * N2, B, N3, 1,
-                                                         (long long)B, 1LL, (long long)N3, 1LL);
+    k_axis_pass<C><<<grid_for(n, bs), bs, 0, st>>>((const C*)c->s_u2.p, (C*)c->s_u.p, einv[2], nbands * N1 * N2, B, N3,
+                                                   1, (long long)B, 1LL, (long long)N3, 1LL);
     return cudaGetLastError();
+}
+
+template <typename C, typename CO>
+static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long long col0, const C* const efwd[3],
+                                  const C* const twz, const C* const twy, cudaStream_t st, int* nlaunch) {
+    const QPlan& P = c->plan;
+    const int N1 = c->fft[0], N2 = c->fft[1], N3 = c->fft[2];
+    const int ny = P.nset[1], nz = P.nset[2];
+    const long long nr = c->nr;
+    const int bs = 256;
+    // fused path over the whole k block when its partial transforms fit the scratch budget
+    {
+        const long long npair = (long long)nkb * c->nemp * c->nocc;
+        const size_t t1 = (size_t)npair * N1 * N2 * nz * sizeof(C);
+        if (P.fused && twz && twy && t1 <= (size_t)12 << 30 && ensure(c, c->s_t1, t1) == RP_OK &&
+            fused_z<C>(N3, (const C*)c->s_u.p, nkb, c->nband, c->nocc, 0, c->nemp, N1 * N2, (const int*)P.d_zmap.p,
+                       nz, twz, (C*)c->s_t1.p, st)) {
+            if (fused_yx<C, CO>(N2, (const C*)c->s_t1.p, (int)npair, N1, nz, (const int*)P.d_ymap.p, ny, twy, efwd[0],
+                                (const int*)P.d_gpos.p, P.ng, (typename CT<C>::R)(1.0 / (double)nr), M, ldm, col0,
+                                st)) {
+                *nlaunch += 2;
+                return cudaGetLastError();
+            }
+            if (ensure(c, c->s_t2, (size_t)npair * N1 * ny * nz * sizeof(C))) return cudaErrorMemoryAllocation;
+            long long n = npair * N1 * ny * nz;
+            k_axis_pass<C><<<grid_for(n, bs), bs, 0, st>>>((const C*)c->s_t1.p, (C*)c->s_t2.p, efwd[1], npair * N1, N2,
+                                                           ny, nz, (long long)N2 * nz, (long long)nz, (long long)ny * nz,
+                                                           (long long)nz);
+            n = (long long)P.ng * npair;
+            k_sphere_readout<C, CO><<<grid_for(n, bs), bs, 0, st>>>((const C*)c->s_t2.p, efwd[0], (const int*)P.d_gpos.p,
+                                                                    P.ng, (int)npair, N1, ny, nz,
+                                                                    (typename CT<C>::R)(1.0 / (double)nr), M, ldm, col0);
+            *nlaunch += 3;
+            return cudaGetLastError();
+        }
+    }
+    // empty bands per sub-block: keep the product scratch near 256 MB
+    const long long per = (long long)c->nocc * nr * (long long)sizeof(C);
+    int na = (int)std::max(1LL, std::min((long long)c->nemp, (256LL << 20) / per));
+    const size_t pbytes = (size_t)na * c->nocc * nr * sizeof(C);
+    const size_t t1 = (size_t)na * c->nocc * N1 * N2 * nz * sizeof(C);
+    const size_t t2 = (size_t)na * c->nocc * N1 * ny * nz * sizeof(C);
+    if (ensure(c, c->s_p, pbytes) || ensure(c, c->s_t1, t1) || ensure(c, c->s_t2, t2)) return cudaErrorMemoryAllocation;
+    for (int kl = 0; kl < nkb; ++kl) {
+        const C* u = (const C*)c->s_u.p + (size_t)kl * c->nband * nr;
+        for (int a0 = 0; a0 < c->nemp; a0 += na) {
+            int nab = std::min(na, c->nemp - a0);
+            long long npair = (long long)nab * c->nocc;
+            long long n = npair * nr;
+            k_pair_product<C><<<grid_for(n, bs), bs, 0, st>>>(u, nr, c->nocc, a0, nab, (C*)c->s_p.p);
+            // z -> gz (innermost axis)
+            n = npair * N1 * N2 * nz;
+            k_axis_pass<C><<<grid_for(n, bs), bs, 0, st>>>((const C*)c->s_p.p, (C*)c->s_t1.p, efwd[2], npair * N1 * N2,
+                                                           N3, nz, 1, (long long)N3, 1LL, (long long)nz, 1LL);
+            // y -> gy
+            n = npair * N1 * ny * nz;
+            k_axis_pass<C><<<grid_for(n, bs), bs, 0, st>>>((const C*)c->s_t1.p, (C*)c->s_t2.p, efwd[1], npair * N1, N2,
+                                                           ny, nz, (long long)N2 * nz, (long long)nz, (long long)ny * nz,
+                                                           (long long)nz);
+            // x -> gx on the sphere points
+            n = (long long)P.ng * npair;
+            long long col = col0 + (long long)kl * c->nemp * c->nocc + (long long)a0 * c->nocc;
+            k_sphere_readout<C, CO><<<grid_for(n, bs), bs, 0, st>>>((const C*)c->s_t2.p, efwd[0],
+                                                                    (const int*)P.d_gpos.p, P.ng, (int)npair, N1, ny,
+                                                                    nz, (typename CT<C>::R)(1.0 / (double)nr), M, ldm,
+                                                                    col);
+            *nlaunch += 4;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_inverse(rp_ctx* c, int k0, int nkb, bool fp32, cudaStream_t st) {
+    if (fp32) {
+        const float2* e[3] = {(const float2*)c->d_einv32[0].p, (const float2*)c->d_einv32[1].p,
+                              (const float2*)c->d_einv32[2].p};
+        return gather_inverse_t<float2>(c, k0, nkb, e, st);
+    }
+    const double2* e[3] = {(const double2*)c->d_einv[0].p, (const double2*)c->d_einv[1].p,
+                           (const double2*)c->d_einv[2].p};
+    return gather_inverse_t<double2>(c, k0, nkb, e, st);
 }
 
 cudaError_t launch_pair_forward(rp_ctx* c, int nkb, double2* M, long long ldm, long long col0, cudaStream_t st,
                                 int* nlaunch) {
     const QPlan& P = c->plan;
-    const int N1 = c->fft[0], N2 = c->fft[1], N3 = c->fft[2];
-    const int nx = P.nset[0], ny = P.nset[1], nz = P.nset[2];
-    (void)nx;
-    const long long nr = c->nr;
-    // empty bands per sub-block: keep the product scratch near 256 MB
-    int na = (int)std::max(1LL, std::min((long long)c->nemp, (256LL << 20) / ((long long)c->nocc * nr * 16)));
-    const size_t pbytes = (size_t)na * c->nocc * nr * sizeof(double2);
-    const size_t t1 = (size_t)na * c->nocc * N1 * N2 * nz * sizeof(double2);
-    const size_t t2 = (size_t)na * c->nocc * N1 * ny * nz * sizeof(double2);
-    if (ensure(c, c->s_p, pbytes) || ensure(c, c->s_t1, t1) || ensure(c, c->s_t2, t2)) return cudaErrorMemoryAllocation;
-    const int bs = 256;
-    for (int kl = 0; kl < nkb; ++kl) {
-        const double2* u = (const double2*)c->s_u.p + (size_t)kl * c->nband * nr;
-        for (int a0 = 0; a0 < c->nemp; a0 += na) {
-            int nab = std::min(na, c->nemp - a0);
-            long long npair = (long long)nab * c->nocc;
-            long long n = npair * nr;
-            k_pair_product<double2><<<grid_for(n, bs), bs, 0, st>>>(u, nr, c->nocc, a0, nab, (double2*)c->s_p.p);
-            // z -> gz (innermost axis)
-            n = npair * N1 * N2 * nz;
-            k_axis_pass<double2><<<grid_for(n, bs), bs, 0, st>>>((const double2*)c->s_p.p, (double2*)c->s_t1.p,
-                                                                 (const double2*)P.d_efwd[2].p, npair * N1 * N2, N3, nz,
-                                                                 1, (long long)N3, 1LL, (long long)nz, 1LL);
-            // y -> gy
-            n = npair * N1 * ny * nz;
-            k_axis_pass<double2><<<grid_for(n, bs), bs, 0, st>>>((const double2*)c->s_t1.p, (double2*)c->s_t2.p,
-                                                                 (const double2*)P.d_efwd[1].p, npair * N1, N2, ny, nz,
-                                                                 (long long)N2 * nz, (long long)nz,
-                                                                 (long long)ny * nz, (long long)nz);
-            // x -> gx on the sphere points
-            n = (long long)P.ng * npair;
-            long long col = col0 + (long long)kl * c->nemp * c->nocc + (long long)a0 * c->nocc;
-            k_sphere_readout<double2><<<grid_for(n, bs), bs, 0, st>>>((const double2*)c->s_t2.p,
-                                                                      (const double2*)P.d_efwd[0].p,
-                                                                      (const int*)P.d_gpos.p, P.ng, (int)npair, N1, ny,
-                                                                      nz, 1.0 / (double)nr, M, ldm, col);
-            *nlaunch += 4;
-        }
-    }
-    return cudaGetLastError();
+    const double2* e[3] = {(const double2*)P.d_efwd[0].p, (const double2*)P.d_efwd[1].p,
+                           (const double2*)P.d_efwd[2].p};
+    return pair_forward_t<double2, double2>(c, nkb, M, ldm, col0, e, (const double2*)P.d_tw[2].p,
+                                            (const double2*)P.d_tw[1].p, st, nlaunch);
+}
+
+cudaError_t launch_pair_forward32(rp_ctx* c, int nkb, float2* M, long long ldm, long long col0, cudaStream_t st,
+                                  int* nlaunch) {
+    const QPlan& P = c->plan;
+    const float2* e[3] = {(const float2*)P.d_efwd32[0].p, (const float2*)P.d_efwd32[1].p,
+                          (const float2*)P.d_efwd32[2].p};
+    return pair_forward_t<float2, float2>(c, nkb, M, ldm, col0, e, (const float2*)P.d_tw32[2].p,
+                                          (const float2*)P.d_tw32[1].p, st, nlaunch);
 }
 
 }  // namespace rp

@@ -112,12 +112,13 @@ __global__ void k_tetra_weights(const double* __restrict__ E, const double* __re
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long K = (long long)nk * nemp * nocc;
     if (t >= K) return;
+    const int f_begin = blockIdx.y * TT_FCH;
     const int o = (int)(t % nocc);
     const int a = (int)((t / nocc) % nemp);
     const int k = (int)(t / ((long long)nocc * nemp));
     double pref = 2.0 / (double)nk;
     if (Tw) pref *= 1.0 - Tw[(size_t)kp[k] * nband + nocc + a] * Tw[(size_t)k * nband + o];
-    for (int f0 = 0; f0 < nf; f0 += TT_FCH) {
+    for (int f0 = f_begin; f0 < nf && f0 < f_begin + TT_FCH; f0 += TT_FCH) {
         double2 z[TT_FCH][2];
         double2 acc[TT_FCH];
         for (int q = 0; q < TT_FCH; ++q) {
@@ -217,7 +218,8 @@ cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double
                          double da, double dr, double2* w, cudaStream_t st) {
     const long long K = (long long)c->nk * c->nemp * c->nocc;
     const int bs = 128;
-    k_tetra_weights<<<(unsigned)((K + bs - 1) / bs), bs, 0, st>>>(
+    dim3 grid((unsigned)((K + bs - 1) / bs), (unsigned)((nf + TT_FCH - 1) / TT_FCH));
+    k_tetra_weights<<<grid, bs, 0, st>>>(
         (const double*)c->d_energy.p, c->T.empty() ? nullptr : (const double*)c->d_T.p, c->nband, c->nocc,
         c->nemp, c->nk, (const int*)c->plan.d_kp.p, (const int*)c->d_tets.p, (const int*)c->d_tetk.p, nf, d_freq,
         axis, ordering, delta, da, dr, w);

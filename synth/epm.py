@@ -15,6 +15,7 @@ Two potentials are provided:
 from __future__ import annotations
 
 import os
+import sys
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -160,8 +161,23 @@ def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None):
     if work > 2e10 and workers > 1:
         import concurrent.futures as cf
         import multiprocessing as mp
-        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
-            res = list(ex.map(_solve_k, jobs, chunksize=max(1, nk // (4 * workers))))
+        # one BLAS thread per worker process (spawned children read these at start-up)
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = "1"
+        # fork is safe (and needs no importable __main__) while CUDA is not initialised here
+        torch = sys.modules.get("torch")
+        cuda_up = torch is not None and torch.cuda.is_initialized()
+        try:
+            with cf.ProcessPoolExecutor(max_workers=workers,
+                                        mp_context=mp.get_context("spawn" if cuda_up else "fork")) as ex:
+                res = list(ex.map(_solve_k, jobs, chunksize=max(1, nk // (4 * workers))))
+        finally:
+            for v, val in saved.items():
+                if val is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = val
     else:
         res = [_solve_k(j) for j in jobs]
     npw = np.array([r_[0].shape[0] for r_ in res], dtype=np.int32)

@@ -168,3 +168,38 @@ def test_errors_are_reported():
     # the context stays usable afterwards
     W, _ = ctx.rp_solve_w(q, np.zeros((1, len(G), len(G)), dtype=np.complex128))
     assert np.allclose(W[0], np.diag(vs * vs), rtol=1e-14, atol=0)
+
+
+# ---- BF16x3 split-precision contraction on tcgen05 ----
+# Each operand is carried as two bf16 (16 significant bits); the dropped lo*lo term and the
+# FP32 accumulation inside each 8192-real window bound the error near 2^-16 per product, which
+# averages down over the sum: 1e-4 relative Frobenius is the stated bound.
+BF16X3_TOL = 1e-4
+
+
+@pytest.mark.parametrize("ng,K,nf", [(150, 5000, 2), (64, 100, 1), (7, 33, 3), (300, 9000, 1)])
+def test_contract_bf16x3(ng, K, nf):
+    rng = np.random.default_rng(7 * ng + K)
+    M = rng.standard_normal((ng, K)) + 1j * rng.standard_normal((ng, K))
+    w = rng.standard_normal((nf, K)) + 1j * rng.standard_normal((nf, K))
+    ctx = _ctx(workload("micro"))
+    got = ctx.rp_contract_chi0(M, w, precision=rp.RP_BF16X3)
+    ref = OC.chi0(M, w)
+    err = _rel_fro(got, ref)
+    print("bf16x3 rel err", err)
+    assert np.all(err < BF16X3_TOL)
+    # a second call on the same context gives the same bits (no stale state)
+    got2 = ctx.rp_contract_chi0(M, w, precision=rp.RP_BF16X3)
+    assert np.array_equal(got, got2)
+
+
+def test_build_chi0_bf16x3_tiny(tiny, tiny_ref):
+    chi_ref, W_ref = tiny_ref
+    ctx = _ctx(tiny)
+    q = tiny.q[0]
+    chi = ctx.rp_build_chi0(q, _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, rp.RP_BF16X3)
+    e = _rel_fro(chi, chi_ref)
+    print("bf16x3 chi0 rel err per frequency", e)
+    assert np.all(e < BF16X3_TOL)
+    W, _ = ctx.rp_solve_w(q, chi)
+    assert np.all(_rel_fro(W, W_ref) < BF16X3_TOL)
