@@ -119,10 +119,13 @@ int rp_pair_density(rp_ctx* ctx, const double q_frac[3], int k_begin, int k_end,
  *   delta_ha        broadening d of Eq. Xakqbk (>= 0); both poles must stay off the real axis.
  *   delta_a (Ha), delta_r  degeneracy thresholds of Eq. tetrahedron: sorted nodes closer than
  *                   delta_a + delta_r*max(|x|) to their group's first node are merged.
- *   w_out [io]      c128 [nfreq][K].   FP64 throughout. */
+ *   precision       RP_FP64_NATIVE: FP64 throughout.  RP_BF16X3: FP32 evaluation, with every
+ *                   node set that has a near degeneracy evaluated again in FP64 (the weights the
+ *                   split-precision chi0 path uses).
+ *   w_out [io]      c128 [nfreq][K]. */
 int rp_tetra_weights(rp_ctx* ctx, const double q_frac[3], int axis, int ordering,
                      int nfreq, const double* freq_ha, double delta_ha, double delta_a,
-                     double delta_r, double* w_out, int on_device, void* cuda_stream);
+                     double delta_r, int precision, double* w_out, int on_device, void* cuda_stream);
 
 /* rp_contract_chi0 -- chi[f] = M diag(w[f]) M^H (Eq. chi as a weighted contraction).
  *   ng, K        sizes;  M [io] c128 [ng][K];  w [io] c128 [nfreq][K];

@@ -50,7 +50,7 @@ def library():
         "rp_load_bands": (I, [P, I, I, I, P, I, P, P, P, P]),
         "rp_sphere_size": (I, [P, P, ctypes.POINTER(I), ctypes.POINTER(I), P, P]),
         "rp_pair_density": (I, [P, P, I, I, P, I, P]),
-        "rp_tetra_weights": (I, [P, P, I, I, I, P, D, D, D, P, I, P]),
+        "rp_tetra_weights": (I, [P, P, I, I, I, P, D, D, D, I, P, I, P]),
         "rp_contract_chi0": (I, [P, I, LL, I, P, P, I, P, I, P]),
         "rp_build_chi0": (I, [P, P, I, I, I, P, D, D, D, I, P, I, P]),
         "rp_solve_w": (I, [P, P, I, P, P, P, I, P]),
@@ -161,13 +161,14 @@ class Context:
                                               _stream() if dev else None))
         return out
 
-    def rp_tetra_weights(self, q, axis, ordering, freq, delta, delta_a=1e-8, delta_r=1e-8, out=None):
+    def rp_tetra_weights(self, q, axis, ordering, freq, delta, delta_a=1e-8, delta_r=1e-8, out=None,
+                         precision=RP_FP64_NATIVE):
         fr, pf = _host(freq, np.float64)
         K = self.nk * self.nemp * self.nocc
         out, dev = self._out(out, (len(fr), K))
         q_, pq = _host(q, np.float64)
         self._check(self._lib.rp_tetra_weights(self._h, pq, int(axis), int(ordering), len(fr), pf, float(delta),
-                                               float(delta_a), float(delta_r), self._ptr(out, dev), dev,
+                                               float(delta_a), float(delta_r), int(precision), self._ptr(out, dev), dev,
                                                _stream() if dev else None))
         return out
 

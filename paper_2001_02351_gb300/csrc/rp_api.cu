@@ -456,14 +456,14 @@ static int check_freq(rp_ctx* c, int axis, int ordering, int nfreq, const double
 }
 
 static int weights_device(rp_ctx* c, int axis, int ordering, int nfreq, const double* freq, double delta,
-                          double da, double dr, double2* w, cudaStream_t st) {
+                          double da, double dr, bool fp32, double2* w, cudaStream_t st) {
     int s = ensure(c, c->s_io3, nfreq * sizeof(double));
     if (s) return s;
     cudaError_t e = cudaMemcpyAsync(c->s_io3.p, freq, nfreq * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "copy frequencies");
     prof_begin(c, 2, st);
-    e = launch_tetra(c, axis, ordering, nfreq, (const double*)c->s_io3.p, delta, da, dr, w, st);
-    prof_end(c, 2, st, 1);
+    e = launch_tetra(c, axis, ordering, nfreq, (const double*)c->s_io3.p, delta, da, dr, fp32, w, st);
+    prof_end(c, 2, st, fp32 ? 2 : 1);
     if (e != cudaSuccess) return cuda_fail(c, e, "tetrahedron weights");
     // the frequency copy is from pageable host memory; keep it valid until it has landed
     e = cudaStreamSynchronize(st);
@@ -471,7 +471,7 @@ static int weights_device(rp_ctx* c, int axis, int ordering, int nfreq, const do
 }
 
 int rp_tetra_weights(rp_ctx* c, const double q[3], int axis, int ordering, int nfreq, const double* freq,
-                     double delta, double da, double dr, double* w_out, int on_device, void* stream) {
+                     double delta, double da, double dr, int precision, double* w_out, int on_device, void* stream) {
     int s = check_ready(c, q);
     if (s) return s;
     if ((s = check_freq(c, axis, ordering, nfreq, freq, delta, da, dr))) return s;
@@ -484,7 +484,8 @@ int rp_tetra_weights(rp_ctx* c, const double q[3], int axis, int ordering, int n
         if ((s = ensure(c, c->s_io1, bytes))) return s;
         w = (double2*)c->s_io1.p;
     }
-    if ((s = weights_device(c, axis, ordering, nfreq, freq, delta, da, dr, w, st))) return s;
+    if (precision != RP_FP64_NATIVE && precision != RP_BF16X3) return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
+    if ((s = weights_device(c, axis, ordering, nfreq, freq, delta, da, dr, precision != RP_FP64_NATIVE, w, st))) return s;
     if (!on_device) {
         cudaError_t e = cudaMemcpyAsync(w_out, w, bytes, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "copy w");
@@ -506,13 +507,15 @@ static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, lon
     }
     const size_t sb = (size_t)ng * tc_kp2(K) * 2;
     int s;
-    if ((s = ensure(c, c->s_hi, sb)) || (s = ensure(c, c->s_lo, sb))) return s;
+    if ((s = ensure(c, c->s_hi, sb)) || (s = ensure(c, c->s_lo, sb)) ||
+        (s = ensure(c, c->s_w32, (size_t)nfreq * (tc_kp2(K) / 2) * sizeof(float2))))
+        return s;
     prof_begin(c, 3, st);
     e = launch_split_bf16(M, m32, ldm, col0m, K, ng, c->s_hi.p, c->s_lo.p, st);
     if (e == cudaSuccess)
-        e = launch_contract_bf16x3(c->s_hi.p, c->s_lo.p, K, ng, w, ldw, col0w, nfreq, chi, (int*)c->d_err.p + 1,
-                                   c->num_sms, st);
-    prof_end(c, 3, st, 2);
+        e = launch_contract_bf16x3(c->s_hi.p, c->s_lo.p, K, ng, w, ldw, col0w, nfreq, c->s_w32.p, chi,
+                                   (int*)c->d_err.p + 1, c->num_sms, st);
+    prof_end(c, 3, st, 3);
     return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "bf16x3 contraction");
 }
 
@@ -582,7 +585,7 @@ int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfre
         chi = (double2*)c->s_chi.p;
     }
     double2* w = (double2*)c->s_w.p;
-    if ((s = weights_device(c, axis, ordering, nfreq, freq, delta, da, dr, w, st))) return s;
+    if ((s = weights_device(c, axis, ordering, nfreq, freq, delta, da, dr, m32, w, st))) return s;
     if (precision == RP_BF16X3) {
         cudaError_t e = cudaMemsetAsync(chi, 0, bc, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "zero chi");
@@ -699,7 +702,7 @@ void rp_destroy(rp_ctx* c) {
                       &c->d_einv[0], &c->d_einv[1], &c->d_einv[2], &c->d_einv32[0], &c->d_einv32[1],
                       &c->d_einv32[2], &c->d_err, &c->s_box, &c->s_u1, &c->s_u2,
                       &c->s_u, &c->s_p, &c->s_t1, &c->s_t2, &c->s_m, &c->s_w, &c->s_chi, &c->s_io1, &c->s_io2,
-                      &c->s_io3, &c->s_hi, &c->s_lo, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
+                      &c->s_io3, &c->s_hi, &c->s_lo, &c->s_w32, &c->s_queue, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
                       &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_tw[0], &c->plan.d_tw[1],
                       &c->plan.d_tw[2], &c->plan.d_tw32[0], &c->plan.d_tw32[1], &c->plan.d_tw32[2],

@@ -9,9 +9,10 @@
 // a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs), accumulated in FP32 in tensor memory and
 // flushed into FP64 every FLUSH_STAGES stages (double-buffered accumulators).
 //
-// CTA: 10 warps.  warp 0 = TMA producer (A_hi, A_lo rows of the G tile; the same arrays'
-// rows of the G' tile as raw B), warp 1 = MMA issuer, warps 2-5 = B builders (scale by w,
-// split, write the 128B-swizzled K-major tile), warps 6-9 = epilogue (tcgen05.ld -> FP64).
+// CTA: 14 warps.  warp 0 = TMA producer (A_hi, A_lo rows of the G tile; the same arrays'
+// rows of the G' tile as raw B; the stage's 32 weights), warp 1 = MMA issuer, warps 2-9 =
+// B builders (scale by w, split, write the 128B-swizzled K-major tile), warps 10-13 =
+// epilogue (tcgen05.ld -> FP64).
 // Tile: 128 G rows x (64 G' re-rows + 64 G' im-rows), K step 64 reals per stage.
 // Every wait is bounded; a wait that gives up records where in err_flag[1] and the CTA
 // leaves through the common teardown (its copies in flight are waited for, TMEM is freed).
@@ -27,11 +28,14 @@ namespace rp {
 #define TC_BN 64                // G' per tile (128 real columns)
 #define TC_BK 64                // reals per stage
 #define TC_FLUSH_STAGES 128     // stages per FP32 accumulation window (8192 reals)
-#define TC_THREADS 320
+#define TC_THREADS 448
+#define TC_NBUILD 256           // B-builder threads (warps 2-9); epilogue = warps 10-13
 
 #define TC_A_BYTES (TC_BM * TC_BK * 2)            // 16 KB
 #define TC_R_BYTES (TC_BN * TC_BK * 2)            // 8 KB
-#define TC_STAGE_BYTES (2 * TC_A_BYTES + 2 * TC_R_BYTES)   // 48 KB
+#define TC_W_BYTES (TC_BK / 2 * 8)                // 32 complex float weights = 256 B
+#define TC_STAGE_LOAD (2 * TC_A_BYTES + 2 * TC_R_BYTES + TC_W_BYTES)
+#define TC_STAGE_BYTES (2 * TC_A_BYTES + 2 * TC_R_BYTES + 1024)   // 49 KB, keeps 1024-B alignment
 #define TC_B_BYTES (2 * TC_BN * TC_BK * 2)        // 16 KB (128 rows)
 #define TC_SMEM_B0 (TC_NS * TC_STAGE_BYTES)
 #define TC_SMEM_BAR (TC_SMEM_B0 + 2 * 2 * TC_B_BYTES)
@@ -75,6 +79,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
     }
     atomicExch(err, code);
     return false;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"((uint64_t)src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -121,8 +131,8 @@ __device__ __forceinline__ void split2(float x, float& hi, float& lo) {
 }
 
 struct TcArgs {
-    const double2* w;
-    long long ldw, col0, K;
+    const float2* w32;      // [nf][kp2/2] complex float weights of this block (zero padded)
+    long long K;
     int ng, nf, mt, nt, nst;
     double2* chi;
     int* err;
@@ -149,10 +159,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_NS; ++s) {
             mbar_init(full(s), 1);
-            mbar_init(empty(s), 128 + 1);
+            mbar_init(empty(s), TC_NBUILD + 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(bready(b), 128);
+            mbar_init(bready(b), TC_NBUILD);
             mbar_init(bfree(b), 1);
             mbar_init(accf(b), 1);
             mbar_init(acce(b), 128);
@@ -180,15 +190,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             long long sg = 0;
             bool ok = true;
+            const long long kpad = (long long)nst * (TC_BK / 2);
             for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
+                const int f = job / (args.mt * args.nt);
                 const int rem = job % (args.mt * args.nt);
                 const int m0 = (rem / args.nt) * TC_BM, n0 = (rem % args.nt) * TC_BN;
+                const float2* wrow = args.w32 + (size_t)f * kpad;
                 for (int st = 0; st < nst; ++st, ++sg) {
                     const int s = (int)(sg % TC_NS);
                     const uint32_t ph = (uint32_t)((sg / TC_NS) & 1);
                     if (!(ok = mbar_wait(empty(s), ph ^ 1, err, 101))) break;
                     const uint32_t base = sbase + s * TC_STAGE_BYTES;
-                    mbar_expect_tx(full(s), TC_STAGE_BYTES);
+                    mbar_expect_tx(full(s), TC_STAGE_LOAD);
+                    bulk_load(base + 2 * TC_A_BYTES + 2 * TC_R_BYTES, wrow + (size_t)st * (TC_BK / 2), TC_W_BYTES,
+                              full(s));
                     const int x = st * TC_BK;
                     tma_load_2d(base, &map_hi, x, m0, full(s));
                     tma_load_2d(base + TC_A_BYTES / 2, &map_hi, x, m0 + 64, full(s));
@@ -240,14 +255,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mma_commit(done_bar);
             mbar_wait(done_bar, 0, err, 114);
         }
-    } else if (warp < 6) {
-        // ---------------- B builders (128 threads) ----------------
+    } else if (warp < 2 + TC_NBUILD / 32) {
+        // ---------------- B builders (TC_NBUILD threads) ----------------
         const int t = threadIdx.x - 64;
         long long sg = 0;
         bool ok = true;
         for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
-            const int f = job / (args.mt * args.nt);
-            const double2* wf = args.w + (size_t)f * args.ldw + args.col0;
             for (int st = 0; st < nst; ++st, ++sg) {
                 const int s = (int)(sg % TC_NS);
                 const int bb = (int)(sg & 1);
@@ -255,15 +268,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!(ok = mbar_wait(bfree(bb), (uint32_t)(((sg >> 1) & 1) ^ 1), err, 122))) break;
                 const unsigned char* rhi = smem + s * TC_STAGE_BYTES + 2 * TC_A_BYTES;
                 const unsigned char* rlo = rhi + TC_R_BYTES;
+                const float2* ws = reinterpret_cast<const float2*>(rlo + TC_R_BYTES);
                 unsigned char* bhi = smem + TC_SMEM_B0 + bb * 2 * TC_B_BYTES;
                 unsigned char* blo = bhi + TC_B_BYTES;
 #pragma unroll
-                for (int it = 0; it < (TC_BN * 8) / 128; ++it) {
-                    const int task = t + it * 128;
+                for (int it = 0; it < (TC_BN * 8) / TC_NBUILD; ++it) {
+                    const int task = t + it * TC_NBUILD;
                     const int r = task >> 3, c = task & 7;
                     const uint32_t o = sw128_off(r, c);
                     const uint4 vh = *reinterpret_cast<const uint4*>(rhi + o);
                     const uint4 vl = *reinterpret_cast<const uint4*>(rlo + o);
+                    const float4 w01 = *reinterpret_cast<const float4*>(ws + 4 * c);
+                    const float4 w23 = *reinterpret_cast<const float4*>(ws + 4 * c + 2);
+                    const float wr[4] = {w01.x, w01.z, w23.x, w23.z};
+                    const float wi[4] = {w01.y, w01.w, w23.y, w23.w};
                     const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&vh);
                     const __nv_bfloat162* l2 = reinterpret_cast<const __nv_bfloat162*>(&vl);
                     uint32_t reh[4], rel[4], imh[4], iml[4];
@@ -272,15 +290,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const float2 hh = __bfloat1622float2(h2[i]);
                         const float2 ll = __bfloat1622float2(l2[i]);
                         const float mr = hh.x + ll.x, mi = hh.y + ll.y;
-                        const long long b = (long long)st * (TC_BK / 2) + 4 * c + i;
-                        float wr = 0.f, wi = 0.f;
-                        if (b < args.K) {
-                            const double2 wv = wf[b];
-                            wr = (float)wv.x;
-                            wi = (float)wv.y;
-                        }
-                        const float P = wr * mr + wi * mi;
-                        const float Q = wr * mi - wi * mr;
+                        const float P = wr[i] * mr + wi[i] * mi;
+                        const float Q = wr[i] * mi - wi[i] * mr;
                         float ph, pl, qh, ql;
                         split2(P, ph, pl);
                         split2(Q, qh, ql);
@@ -316,10 +327,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!(ok = mbar_wait(accf(ab), (uint32_t)((cg >> 1) & 1), err, 131))) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * 128);
-                float v[2][64];
 #pragma unroll
-                for (int part = 0; part < 4; ++part) {
-                    uint32_t r[32];
+                for (int half = 0; half < 2; ++half) {
+                    // columns [32 half, +32) hold Re, [64 + 32 half, +32) hold Im of G' = n0 + 32 half + j
+                    uint32_t r[32], s2[32];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -328,22 +339,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
                           "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
                           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                        : "r"(src + (uint32_t)(part * 32)));
+                        : "r"(src + (uint32_t)(half * 32)));
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        : "=r"(s2[0]), "=r"(s2[1]), "=r"(s2[2]), "=r"(s2[3]), "=r"(s2[4]), "=r"(s2[5]), "=r"(s2[6]),
+                          "=r"(s2[7]), "=r"(s2[8]), "=r"(s2[9]), "=r"(s2[10]), "=r"(s2[11]), "=r"(s2[12]),
+                          "=r"(s2[13]), "=r"(s2[14]), "=r"(s2[15]), "=r"(s2[16]), "=r"(s2[17]), "=r"(s2[18]),
+                          "=r"(s2[19]), "=r"(s2[20]), "=r"(s2[21]), "=r"(s2[22]), "=r"(s2[23]), "=r"(s2[24]),
+                          "=r"(s2[25]), "=r"(s2[26]), "=r"(s2[27]), "=r"(s2[28]), "=r"(s2[29]), "=r"(s2[30]),
+                          "=r"(s2[31])
+                        : "r"(src + (uint32_t)(64 + half * 32)));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (half == 1) {
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        mbar_arrive(acce(ab));
+                    }
+                    if (g < args.ng) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[part >> 1][(part & 1) * 32 + i] = __uint_as_float(r[i]);
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                mbar_arrive(acce(ab));
-                if (g < args.ng) {
-#pragma unroll
-                    for (int j = 0; j < TC_BN; ++j) {
-                        const int gp = n0 + j;
-                        if (gp < args.ng) {
-                            double2 o = out[gp];
-                            o.x += (double)v[0][j];
-                            o.y += (double)v[1][j];
-                            out[gp] = o;
+                        for (int j = 0; j < 32; ++j) {
+                            const int gp = n0 + half * 32 + j;
+                            if (gp < args.ng) {
+                                double2 o = out[gp];
+                                o.x += (double)__uint_as_float(r[j]);
+                                o.y += (double)__uint_as_float(s2[j]);
+                                out[gp] = o;
+                            }
                         }
                     }
                 }
@@ -380,6 +401,21 @@ __global__ void k_split_bf16(const CI* __restrict__ M, long long ldm, long long 
     l2.x = lx; l2.y = ly;
     reinterpret_cast<__nv_bfloat162*>(hi)[t] = h2;
     reinterpret_cast<__nv_bfloat162*>(lo)[t] = l2;
+}
+
+// complex float copy of the weights of this block: w32[f][b] = w[f][col0 + b], b < kpad (zero padded)
+__global__ void k_weights32(const double2* __restrict__ w, long long ldw, long long col0, long long K, int nf,
+                            long long kpad, float2* __restrict__ w32) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nf * kpad) return;
+    const int f = (int)(t / kpad);
+    const long long b = t % kpad;
+    float2 v = make_float2(0.f, 0.f);
+    if (b < K) {
+        const double2 d = w[(size_t)f * ldw + col0 + b];
+        v = make_float2((float)d.x, (float)d.y);
+    }
+    w32[t] = v;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -430,14 +466,17 @@ cudaError_t launch_split_bf16(const void* M, bool m32, long long ldm, long long 
 // chi (+)= ... over the K pairs whose bf16 split is in hi/lo ([ng][kp2]); chi must be zeroed by
 // the caller before the first accumulation
 cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, int ng, const double2* w,
-                                   long long ldw, long long col0, int nf, double2* chi, int* err, int num_sms,
-                                   cudaStream_t st) {
+                                   long long ldw, long long col0, int nf, void* w32, double2* chi, int* err,
+                                   int num_sms, cudaStream_t st) {
     const long long kp2 = tc_kp2(K);
+    const long long kpad = kp2 / 2;
     CUtensorMap mhi, mlo;
     if (!make_map(&mhi, const_cast<void*>(hi), ng, kp2) || !make_map(&mlo, const_cast<void*>(lo), ng, kp2))
         return cudaErrorInvalidValue;
+    const long long nw = (long long)nf * kpad;
+    k_weights32<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(w, ldw, col0, K, nf, kpad, (float2*)w32);
     TcArgs a;
-    a.w = w; a.ldw = ldw; a.col0 = col0; a.K = K;
+    a.w32 = (const float2*)w32; a.K = K;
     a.ng = ng; a.nf = nf;
     a.mt = (ng + TC_BM - 1) / TC_BM;
     a.nt = (ng + TC_BN - 1) / TC_BN;

@@ -66,6 +66,8 @@ struct rp_ctx {
     // scratch (grow-only)
     rp::DevBuf s_box, s_u1, s_u2, s_u, s_p, s_t1, s_t2, s_m, s_w, s_chi, s_io1, s_io2, s_io3;
     rp::DevBuf s_hi, s_lo;            // bf16 hi/lo split of a block of pair densities
+    rp::DevBuf s_w32;                 // complex float weights of that block
+    rp::DevBuf s_queue;               // FP64 work list of the FP32 weight pass (count + items)
     int num_sms = 0;
 
     rp::QPlan plan;
@@ -98,8 +100,9 @@ cudaError_t launch_pair_forward(rp_ctx* c, int nkb, double2* M, long long ldm, l
 cudaError_t launch_pair_forward32(rp_ctx* c, int nkb, float2* M, long long ldm, long long col0,
                                   cudaStream_t st, int* nlaunch);
 // tetrahedron weights for all pairs: w[nf][K]
+// (fp32: split-precision tiers, FP64 re-evaluation near degeneracies)
 cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double* d_freq,
-                         double delta, double delta_a, double delta_r, double2* w,
+                         double delta, double delta_a, double delta_r, bool fp32, double2* w,
                          cudaStream_t st);
 // chi[f] (+)= M diag(w[f][col0..]) M^H, FP64 tensor cores
 cudaError_t launch_contract_f64(const double2* M, long long ldm, long long K, const double2* w,
@@ -109,9 +112,10 @@ cudaError_t launch_contract_f64(const double2* M, long long ldm, long long K, co
 long long tc_kp2(long long K);
 cudaError_t launch_split_bf16(const void* M, bool m32, long long ldm, long long col0, long long K, int ng,
                               void* hi, void* lo, cudaStream_t st);
+// (w32: scratch of nf * tc_kp2(K) / 2 complex floats)
 cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, int ng, const double2* w,
-                                   long long ldw, long long col0, int nf, double2* chi, int* err, int num_sms,
-                                   cudaStream_t st);
+                                   long long ldw, long long col0, int nf, void* w32, double2* chi, int* err,
+                                   int num_sms, cudaStream_t st);
 // Dyson step
 cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W,
                          int* err_flag, cudaStream_t st);

@@ -15,214 +15,423 @@
 // Taylor series f[x_i..x_j] = sum_m f^(m)(c)/m! h_{m-n}(x - c) instead of the recursion;
 // when the whole set of five nodes qualifies, only the m >= 4 coefficients appear
 // (6 (m-4)!/m! (z-c)^(3-m)) and no logarithm is needed.
+// Precision: FP64 throughout for the FP64 tier; for the split-precision tiers FP32, with
+// every node set that has a near degeneracy evaluated again in FP64.
+#include <algorithm>
+
 #include "rp_internal.h"
 
 namespace rp {
 
 #define TT_TAU 0.5
-#define TT_KMAX 40
+#define TT_KMAX 48
 #define TT_FCH 4
 
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ double2 cinv(double2 a) {
-    double d = a.x * a.x + a.y * a.y;
-    return make_double2(a.x / d, -a.y / d);
-}
-__device__ __forceinline__ double2 clog_(double2 a) { return make_double2(log(hypot(a.x, a.y)), atan2(a.y, a.x)); }
+template <typename R>
+struct TT;
+template <>
+struct TT<double> {
+    using C = double2;
+    static __device__ __forceinline__ C mk(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ double hyp(double a, double b) { return hypot(a, b); }
+    static __device__ __forceinline__ C clog(C a) { return make_double2(log(hypot(a.x, a.y)), atan2(a.y, a.x)); }
+    static __device__ __forceinline__ double lg(double a) { return log(a); }
+};
+template <>
+struct TT<float> {
+    using C = float2;
+    static __device__ __forceinline__ C mk(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ float hyp(float a, float b) { return hypotf(a, b); }
+    static __device__ __forceinline__ C clog(C a) { return make_float2(logf(hypotf(a.x, a.y)), atan2f(a.y, a.x)); }
+    static __device__ __forceinline__ float lg(float a) { return logf(a); }
+};
 
-// f^(m)(c)/m! = (z-c)^(3-m) * b_m(log(z-c))
-__device__ __forceinline__ double2 bcoef(int m, double2 L) {
-    switch (m) {
-        case 0: return L;
-        case 1: return make_double2(-(3.0 * L.x + 1.0), -3.0 * L.y);
-        case 2: return make_double2((6.0 * L.x + 5.0) * 0.5, 3.0 * L.y);
-        case 3: return make_double2(-(6.0 * L.x + 11.0) / 6.0, -L.y);
-        default: return make_double2(6.0 / ((double)m * (m - 1) * (m - 2) * (m - 3)), 0.0);
-    }
+template <typename C>
+__device__ __forceinline__ C tadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C>
+__device__ __forceinline__ C tsub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C>
+__device__ __forceinline__ C tmul(C a, C b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename C, typename R>
+__device__ __forceinline__ C tscale(C a, R s) { return {a.x * s, a.y * s}; }
+template <typename C>
+__device__ __forceinline__ C tinv(C a) {
+    const auto d = a.x * a.x + a.y * a.y;
+    return {a.x / d, -a.y / d};
 }
 
-// number of series terms for ratio rho = max|x - c| / |z - c| (rho <= TAU/2)
-__device__ __forceinline__ int nterms(double rho) {
-    if (rho <= 0.0) return 0;
-    int k = (int)ceil(-39.2 / log(rho)) + 6;
+// f^(m)(c)/m! = (z-c)^(3-m) * b_m(log(z-c))  for f(x) = (z-x)^3 log(z-x)
+template <typename R>
+__device__ __forceinline__ typename TT<R>::C bcoef(int m, typename TT<R>::C L) {
+    if (m >= 4) return TT<R>::mk((R)6 / ((R)m * (m - 1) * (m - 2) * (m - 3)), (R)0);
+    if (m == 0) return L;
+    if (m == 1) return TT<R>::mk(-((R)3 * L.x + (R)1), (R)-3 * L.y);
+    if (m == 2) return TT<R>::mk(((R)6 * L.x + (R)5) * (R)0.5, (R)3 * L.y);
+    return TT<R>::mk(-((R)6 * L.x + (R)11) / (R)6, -L.y);
+}
+
+// number of series terms for ratio rho = max|x - c| / |z - c| (rho <= TAU/2), by precision
+template <typename R>
+__device__ __forceinline__ int nterms(R rho) {
+    if (rho <= (R)0) return 0;
+    const R target = sizeof(R) == 8 ? (R)-39.2 : (R)-18.0;
+    int k = (int)ceil(target / TT<R>::lg(rho)) + 6;
     return k > TT_KMAX ? TT_KMAX : k;
 }
 
-// divided difference over the sorted run x[i..j] by the Taylor series about its midpoint
-__device__ double2 dd_run_series(const double* x, int i, int j, double2 z) {
-    const int n = j - i;
-    const double c = 0.5 * (x[i] + x[j]);
-    const double2 y = make_double2(z.x - c, z.y);
-    const double R = hypot(y.x, y.y);
-    double tmax = 0.0;
-    for (int v = i; v <= j; ++v) tmax = fmax(tmax, fabs(x[v] - c));
-    const int K = nterms(tmax / R);
-    double h[TT_KMAX + 1];
-    h[0] = 1.0;
-    for (int k = 1; k <= K; ++k) h[k] = 0.0;
-    for (int v = i; v <= j; ++v) {
-        const double t = x[v] - c;
-        for (int k = 1; k <= K; ++k) h[k] += t * h[k - 1];
+// Divided difference of order n over the m = n+1 centred nodes t (t = x - c) by the Taylor
+// series about c:  y^(3-n) sum_k b_{n+k} h_k(t) y^-k,  y = z - c.  With r = |y| the sum is
+// taken as sum_k b_{n+k} h_k(t/r) (conj(y)/r)^k, so every power stays on the unit circle.
+// The complete homogeneous polynomials h_k come from the recurrence
+// h_k = e1 h_{k-1} - e2 h_{k-2} + ... with the elementary symmetric polynomials e_j of the
+// scaled nodes, so no array is needed.
+template <typename R>
+__device__ __forceinline__ typename TT<R>::C dd_series(const R (&t)[5], int m, typename TT<R>::C y, int K) {
+    using C = typename TT<R>::C;
+    const int n = m - 1;
+    const R r = TT<R>::hyp(y.x, y.y);
+    const R rinv = (R)1 / r;
+    R e[6] = {1, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        if (v < m) {
+            const R tv = t[v] * rinv;
+#pragma unroll
+            for (int j = 5; j >= 1; --j) e[j] += tv * e[j - 1];
+        }
     }
-    const double2 L = clog_(y);
-    const double2 w = cinv(y);
-    // sum_k b_{n+k} h_k w^k  by Horner
-    double2 S = cscale(bcoef(n + K, L), h[K]);
-    for (int k = K - 1; k >= 0; --k) S = cadd(cmul(S, w), cscale(bcoef(n + k, L), h[k]));
+    const C L = (n <= 3) ? TT<R>::clog(y) : TT<R>::mk(0, 0);
+    const C u = TT<R>::mk(y.x * rinv, -y.y * rinv);     // conj(y)/r, |u| = 1
+    R h1 = 0, h2 = 0, h3 = 0, h4 = 0;                    // h_{k-2} .. h_{k-5}
+    R hk = 1;                                            // h_{k-1}
+    C uk = TT<R>::mk(1, 0);
+    C S = bcoef<R>(n, L);
+    for (int k = 1; k <= K; ++k) {
+        const R hn = e[1] * hk - e[2] * h1 + e[3] * h2 - e[4] * h3 + e[5] * h4;
+        h4 = h3; h3 = h2; h2 = h1; h1 = hk; hk = hn;
+        uk = tmul(uk, u);
+        S = tadd(S, tscale(tmul(bcoef<R>(n + k, L), uk), hk));
+    }
     // times y^(3-n)
-    double2 p = make_double2(1.0, 0.0);
+    C p = TT<R>::mk(1, 0);
     if (n <= 3) {
-        for (int e = 0; e < 3 - n; ++e) p = cmul(p, y);
+        for (int q = 0; q < 3 - n; ++q) p = tmul(p, y);
     } else {
-        for (int e = 0; e < n - 3; ++e) p = cmul(p, w);
+        const C w = tinv(y);
+        for (int q = 0; q < n - 3; ++q) p = tmul(p, w);
     }
-    return cmul(S, p);
+    return tmul(S, p);
 }
 
-// full divided-difference table (recursion with series for narrow runs)
-__device__ double2 dd5_table(const double* x, double2 z) {
-    double2 D[5][5];
-    for (int i = 0; i < 5; ++i) {
-        double2 y = make_double2(z.x - x[i], z.y);
-        double2 L = clog_(y);
-        D[i][i] = cmul(cmul(cmul(y, y), y), L);
+// run x[i..j] of the sorted nodes by the series about its midpoint
+template <typename R>
+__device__ __forceinline__ typename TT<R>::C dd_run(const R (&x)[5], int i, int j, typename TT<R>::C z) {
+    R t[5] = {0, 0, 0, 0, 0};
+    const R c = (R)0.5 * (x[i] + x[j]);
+    R tmax = 0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        if (v >= i && v <= j) {
+            t[v - i] = x[v] - c;
+            tmax = fmax(tmax, fabs(x[v] - c));
+        }
     }
+    const typename TT<R>::C y = TT<R>::mk(z.x - c, z.y);
+    return dd_series<R>(t, j - i + 1, y, nterms<R>(tmax / TT<R>::hyp(y.x, y.y)));
+}
+
+// full divided-difference table (recursion, series for narrow runs).  *narrow is set when a
+// run of nonzero width narrower than TAU times its distance to the pole occurs.
+template <typename R>
+__device__ __noinline__ typename TT<R>::C dd5_table(const R (&x)[5], typename TT<R>::C z, bool* narrow) {
+    using C = typename TT<R>::C;
+    C D[5][5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const C y = TT<R>::mk(z.x - x[i], z.y);
+        D[i][i] = tmul(tmul(tmul(y, y), y), TT<R>::clog(y));
+    }
+#pragma unroll
     for (int n = 1; n < 5; ++n)
+#pragma unroll
         for (int i = 0; i + n < 5; ++i) {
             const int j = i + n;
-            const double s = x[j] - x[i];
-            const double c = 0.5 * (x[i] + x[j]);
-            const double R = hypot(z.x - c, z.y);
-            if (s <= TT_TAU * R) D[i][j] = dd_run_series(x, i, j, z);
-            else D[i][j] = cscale(csub(D[i + 1][j], D[i][j - 1]), 1.0 / s);
+            const R s = x[j] - x[i];
+            const R c = (R)0.5 * (x[i] + x[j]);
+            const R Rr = TT<R>::hyp(z.x - c, z.y);
+            if (s <= (R)TT_TAU * Rr) {
+                if (s > 0) *narrow = true;
+                D[i][j] = dd_run<R>(x, i, j, z);
+            } else {
+                D[i][j] = tscale(tsub(D[i + 1][j], D[i][j - 1]), (R)1 / s);
+            }
         }
     return D[0][4];
 }
 
-// One thread per (k, a, o); frequencies in chunks of TT_FCH.
-__global__ void k_tetra_weights(const double* __restrict__ E, const double* __restrict__ Tw, int nband, int nocc,
-                                int nemp, int nk, const int* __restrict__ kp, const int* __restrict__ tets,
-                                const int* __restrict__ tetk, int nf, const double* __restrict__ freq, int axis,
-                                int ordering, double delta, double da, double dr, double2* __restrict__ wout) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cswap(double& a, double& b) {
+    const double lo = fmin(a, b), hi = fmax(a, b);
+    a = lo;
+    b = hi;
+}
+
+// nodes of tetrahedron-vertex entry `code` for pair (a, o): loaded, sorted, degenerate groups
+// merged into their mean (Eq. tetrahedron thresholds), all in FP64
+__device__ __forceinline__ void tetra_nodes(const double* __restrict__ E, int nband, int nocc, int a, int o,
+                                            const int* __restrict__ kp, const int* __restrict__ tets, int code,
+                                            double da, double dr, double (&x)[5]) {
+    const int tt = code >> 2, jv = code & 3;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int kv = tets[4 * tt + v];
+        x[v] = E[(size_t)kp[kv] * nband + nocc + a] - E[(size_t)kv * nband + o];
+    }
+    x[4] = jv == 0 ? x[0] : jv == 1 ? x[1] : jv == 2 ? x[2] : x[3];
+    cswap(x[0], x[1]); cswap(x[3], x[4]); cswap(x[2], x[4]); cswap(x[2], x[3]); cswap(x[0], x[3]);
+    cswap(x[0], x[2]); cswap(x[1], x[4]); cswap(x[1], x[3]); cswap(x[1], x[2]);
+    bool brk[5];
+    brk[0] = true;
+    double start = x[0];
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        const double thr = da + dr * fmax(fabs(start), fabs(x[i]));
+        brk[i] = (x[i] - start) >= thr;
+        if (brk[i]) start = x[i];
+    }
+    if (brk[1] && brk[2] && brk[3] && brk[4]) return;
+    double y[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        double sum = 0.0;
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            bool same = true;
+#pragma unroll
+            for (int b = 1; b < 5; ++b)
+                if (b > (i < j ? i : j) && b <= (i < j ? j : i) && brk[b]) same = false;
+            if (same) { sum += x[j]; ++cnt; }
+        }
+        y[i] = sum / cnt;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) x[i] = y[i];
+}
+
+// one divided difference in FP64 from the nodes themselves (used for near-degenerate sets of
+// the FP32 path)
+__device__ __noinline__ double2 dd_fp64_entry(const double* __restrict__ E, int nband, int nocc, int a, int o,
+                                              const int* __restrict__ kp, const int* __restrict__ tets, int code,
+                                              double da, double dr, double2 z) {
+    double x[5];
+    tetra_nodes(E, nband, nocc, a, o, kp, tets, code, da, dr, x);
+    const double c = 0.5 * (x[0] + x[4]);
+    const double2 y = make_double2(z.x - c, z.y);
+    const double Rr = hypot(y.x, y.y);
+    const double spread = x[4] - x[0];
+    if (spread <= TT_TAU * Rr) {
+        double t[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) t[i] = x[i] - c;
+        return dd_series<double>(t, 5, y, nterms<double>(0.5 * spread / Rr));
+    }
+    bool unused = false;
+    return dd5_table<double>(x, z, &unused);
+}
+
+template <typename R>
+__device__ __noinline__ typename TT<R>::C dd_table_entry(const R (&x)[5], typename TT<R>::C z) {
+    bool unused = false;
+    return dd5_table<R>(x, z, &unused);
+}
+
+// Append a (pair, frequency, tetrahedron-vertex, pole) item to the FP64 work list; when the list
+// is full, evaluate it here instead (slower, same result).
+template <typename C>
+__device__ __forceinline__ void defer_or_eval(unsigned long long* queue, unsigned long long qcap,
+                                              unsigned long long* qcount, long long t, int f, int s, int side,
+                                              C& sacc, const double* __restrict__ E, int nband, int nocc, int a,
+                                              int o, const int* __restrict__ kp, const int* __restrict__ tets,
+                                              int code, double da, double dr, double2 zd) {
+    const unsigned long long slot = atomicAdd(qcount, 1ULL);
+    if (slot < qcap) {
+        queue[slot] = ((unsigned long long)t << 32) | ((unsigned long long)f << 16) | ((unsigned long long)s << 8) |
+                      (unsigned long long)side;
+        return;
+    }
+    const double2 r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, code, da, dr, zd);
+    sacc.x += r.x;
+    sacc.y += r.y;
+}
+
+// FP64 pass over the deferred items: one item per thread, result added to the weight
+__global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ E, const double* __restrict__ Tw,
+                                                     int nband, int nocc, int nemp, int nk,
+                                                     const int* __restrict__ kp, const int* __restrict__ tets,
+                                                     const int* __restrict__ tetk, const double* __restrict__ freq,
+                                                     int axis, int ordering, double delta, double da, double dr,
+                                                     const unsigned long long* __restrict__ queue,
+                                                     const unsigned long long* __restrict__ qcount,
+                                                     unsigned long long qcap, double2* __restrict__ wout) {
+    const unsigned long long n = min(*qcount, qcap);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long item = queue[i];
+    const long long t = (long long)(item >> 32);
+    const int f = (int)((item >> 16) & 0xFFFF), s = (int)((item >> 8) & 0xFF), side = (int)(item & 1);
     const long long K = (long long)nk * nemp * nocc;
-    if (t >= K) return;
-    const int f_begin = blockIdx.y * TT_FCH;
     const int o = (int)(t % nocc);
     const int a = (int)((t / nocc) % nemp);
     const int k = (int)(t / ((long long)nocc * nemp));
     double pref = 2.0 / (double)nk;
     if (Tw) pref *= 1.0 - Tw[(size_t)kp[k] * nband + nocc + a] * Tw[(size_t)k * nband + o];
-    for (int f0 = f_begin; f0 < nf && f0 < f_begin + TT_FCH; f0 += TT_FCH) {
-        double2 z[TT_FCH][2];
-        double2 acc[TT_FCH];
-        for (int q = 0; q < TT_FCH; ++q) {
-            acc[q] = make_double2(0.0, 0.0);
-            const int f = f0 + q < nf ? f0 + q : nf - 1;
-            const double wv = freq[f];
-            if (axis == RP_AXIS_REAL) {
-                z[q][0] = make_double2(wv, delta);
-                z[q][1] = make_double2(-wv, ordering == RP_TIME_ORDERED ? delta : -delta);
-            } else {
-                z[q][0] = make_double2(0.0, wv + delta);
-                z[q][1] = make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
-            }
+    const double wv = freq[f];
+    double2 zd;
+    if (axis == RP_AXIS_REAL)
+        zd = side == 0 ? make_double2(wv, delta) : make_double2(-wv, ordering == RP_TIME_ORDERED ? delta : -delta);
+    else
+        zd = side == 0 ? make_double2(0.0, wv + delta)
+                       : make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
+    const double2 r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, zd);
+    double* dst = reinterpret_cast<double*>(wout + (size_t)f * K + t);
+    atomicAdd(dst, r.x * pref / 6.0);
+    atomicAdd(dst + 1, r.y * pref / 6.0);
+    }
+}
+
+// Weights for one (k, a, o) per thread and a chunk of frequencies per grid row.  The 24
+// tetrahedron-vertex node sets are prepared once in FP64 (sort, merge, centre) and kept in
+// shared memory; every frequency is then evaluated from them in precision R.  Nodes and poles
+// are taken relative to the pair's own transition energy D0 so that R = float keeps its
+// resolution.  With R = float only the series branch (pole farther than 2x the node spread)
+// runs in FP32; resonant node sets (recursion branch) and node sets with two nodes closer than
+// TT_NEAR but not merged (near degeneracy) are evaluated in FP64.
+#define TT_NEAR 1e-5
+#define TT_FIELDS 5   // t1, t2, t3, centre - D0, spread (negative: near-degenerate set)
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_tetra_weights(const double* __restrict__ E, const double* __restrict__ Tw,
+                                                       int nband, int nocc, int nemp, int nk,
+                                                       const int* __restrict__ kp, const int* __restrict__ tets,
+                                                       const int* __restrict__ tetk, int nf, int fch,
+                                                       const double* __restrict__ freq, int axis, int ordering,
+                                                       double delta, double da, double dr,
+                                                       double2* __restrict__ wout,
+                                                       unsigned long long* __restrict__ queue,
+                                                       unsigned long long qcap, unsigned long long* qcount) {
+    using C = typename TT<R>::C;
+    extern __shared__ __align__(16) unsigned char tsm_raw[];
+    R* tsm = reinterpret_cast<R*>(tsm_raw);
+    const int bd = blockDim.x, tid = threadIdx.x;
+    auto fld = [&](int s, int f) -> R& { return tsm[(s * TT_FIELDS + f) * bd + tid]; };
+    const long long t = (long long)blockIdx.x * bd + tid;
+    const long long K = (long long)nk * nemp * nocc;
+    if (t >= K) return;
+    const int o = (int)(t % nocc);
+    const int a = (int)((t / nocc) % nemp);
+    const int k = (int)(t / ((long long)nocc * nemp));
+    double pref = 2.0 / (double)nk;
+    if (Tw) pref *= 1.0 - Tw[(size_t)kp[k] * nband + nocc + a] * Tw[(size_t)k * nband + o];
+    const double d0 = E[(size_t)kp[k] * nband + nocc + a] - E[(size_t)k * nband + o];
+    for (int s = 0; s < 24; ++s) {
+        double x[5];
+        tetra_nodes(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, x);
+        const double cd = 0.5 * (x[0] + x[4]);
+        bool near = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const double g = x[i + 1] - x[i];
+            near = near || (g > 0.0 && g < TT_NEAR);
         }
-        for (int s = 0; s < 24; ++s) {
-            const int code = tetk[24 * k + s];
-            const int tt = code >> 2, jv = code & 3;
-            double x[5];
-            for (int v = 0; v < 4; ++v) {
-                const int kv = tets[4 * tt + v];
-                x[v] = E[(size_t)kp[kv] * nband + nocc + a] - E[(size_t)kv * nband + o];
-            }
-            x[4] = x[jv];
-            // sort (insertion, 5 elements)
-            for (int i = 1; i < 5; ++i) {
-                double v = x[i];
-                int j = i - 1;
-                while (j >= 0 && x[j] > v) { x[j + 1] = x[j]; --j; }
-                x[j + 1] = v;
-            }
-            // merge degenerate groups into their mean
-            {
-                int gid[5];
-                gid[0] = 0;
-                double start = x[0];
-                for (int i = 1; i < 5; ++i) {
-                    const double thr = da + dr * fmax(fabs(start), fabs(x[i]));
-                    const bool nw = (x[i] - start) >= thr;
-                    gid[i] = gid[i - 1] + (nw ? 1 : 0);
-                    if (nw) start = x[i];
+        fld(s, 0) = (R)(x[1] - cd);
+        fld(s, 1) = (R)(x[2] - cd);
+        fld(s, 2) = (R)(x[3] - cd);
+        fld(s, 3) = (R)(cd - d0);
+        fld(s, 4) = near ? -(R)(x[4] - x[0]) - (R)1 : (R)(x[4] - x[0]);
+    }
+    const int f1 = min(nf, (int)(blockIdx.y + 1) * fch);
+    for (int f = blockIdx.y * fch; f < f1; ++f) {
+        const double wv = freq[f];
+        double2 acc = make_double2(0.0, 0.0);
+        for (int side = 0; side < 2; ++side) {
+            double2 zd;
+            if (axis == RP_AXIS_REAL)
+                zd = side == 0 ? make_double2(wv, delta) : make_double2(-wv, ordering == RP_TIME_ORDERED ? delta : -delta);
+            else
+                zd = side == 0 ? make_double2(0.0, wv + delta)
+                               : make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
+            const C zr = TT<R>::mk((R)(zd.x - d0), (R)zd.y);    // pole relative to D0
+            C sacc = TT<R>::mk(0, 0);
+            for (int s = 0; s < 24; ++s) {
+                const R sp = fld(s, 4);
+                const R spread = sp < (R)0 ? -sp - (R)1 : sp;
+                R tr[5] = {(R)-0.5 * spread, fld(s, 0), fld(s, 1), fld(s, 2), (R)0.5 * spread};
+                const R ct = fld(s, 3);
+                if (sizeof(R) == 4 && sp < (R)0) {
+                    defer_or_eval(queue, qcap, qcount, t, f, s, side, sacc, E, nband, nocc, a, o, kp, tets,
+                                  tetk[24 * k + s], da, dr, zd);
+                    continue;
                 }
-                double m[5];
-                for (int g = 0; g < 5; ++g) {
-                    double sum = 0.0;
-                    int cnt = 0;
-                    for (int i = 0; i < 5; ++i)
-                        if (gid[i] == g) { sum += x[i]; ++cnt; }
-                    m[g] = cnt ? sum / cnt : 0.0;
-                }
-                for (int i = 0; i < 5; ++i) x[i] = m[gid[i]];
-            }
-            const double c = 0.5 * (x[0] + x[4]);
-            const double spread = x[4] - x[0];
-            double h[TT_KMAX + 1];
-            int hk = -1;   // h_k(x - c) computed up to this order
-            for (int q = 0; q < TT_FCH; ++q) {
-                if (f0 + q >= nf) break;
-                for (int side = 0; side < 2; ++side) {
-                    const double2 zz = z[q][side];
-                    const double2 y = make_double2(zz.x - c, zz.y);
-                    const double R = hypot(y.x, y.y);
-                    double2 dd;
-                    if (spread <= TT_TAU * R) {
-                        const int K = nterms(0.5 * spread / R);
-                        if (K > hk) {
-                            h[0] = 1.0;
-                            for (int kk = 1; kk <= K; ++kk) h[kk] = 0.0;
-                            for (int v = 0; v < 5; ++v) {
-                                const double tv = x[v] - c;
-                                for (int kk = 1; kk <= K; ++kk) h[kk] += tv * h[kk - 1];
-                            }
-                            hk = K;
-                        }
-                        const double2 w = cinv(y);
-                        double2 S = make_double2(6.0 / ((double)(4 + K) * (3 + K) * (2 + K) * (1 + K)) * h[K], 0.0);
-                        for (int kk = K - 1; kk >= 0; --kk) {
-                            const double b = 6.0 / ((double)(4 + kk) * (3 + kk) * (2 + kk) * (1 + kk));
-                            S = cmul(S, w);
-                            S.x += b * h[kk];
-                        }
-                        dd = cmul(S, w);
-                    } else {
-                        dd = dd5_table(x, zz);
-                    }
-                    acc[q] = cadd(acc[q], dd);
+                const C y = TT<R>::mk(zr.x - ct, zr.y);
+                const R Rr = TT<R>::hyp(y.x, y.y);
+                if (spread <= (R)TT_TAU * Rr) {
+                    sacc = tadd(sacc, dd_series<R>(tr, 5, y, nterms<R>((R)0.5 * spread / Rr)));
+                } else if (sizeof(R) == 4) {
+                    // the recursion can amplify rounding by a few thousand near the series boundary:
+                    // resonant node sets (about 1%) go to the FP64 pass
+                    defer_or_eval(queue, qcap, qcount, t, f, s, side, sacc, E, nband, nocc, a, o, kp, tets,
+                                  tetk[24 * k + s], da, dr, zd);
+                } else {
+                    R xr[5];
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) xr[i] = ct + tr[i];
+                    sacc = tadd(sacc, dd_table_entry<R>(xr, zr));
                 }
             }
+            acc.x += (double)sacc.x;
+            acc.y += (double)sacc.y;
         }
-        for (int q = 0; q < TT_FCH; ++q) {
-            if (f0 + q >= nf) break;
-            wout[(size_t)(f0 + q) * K + t] = cscale(acc[q], pref / 6.0);
-        }
+        wout[(size_t)f * K + t] = make_double2(acc.x * pref / 6.0, acc.y * pref / 6.0);
     }
 }
 
 cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double* d_freq, double delta,
-                         double da, double dr, double2* w, cudaStream_t st) {
+                         double da, double dr, bool fp32, double2* w, cudaStream_t st) {
+    // FP64 work list of the FP32 pass: up to 2% of all evaluations (overflow is evaluated in place)
+    const long long Kp = (long long)c->nk * c->nemp * c->nocc;
+    unsigned long long qcap = (unsigned long long)std::max(1LL << 16, (long long)(0.02 * 48.0 * nf * Kp));
+    if (fp32 && ensure(c, c->s_queue, (qcap + 1) * sizeof(unsigned long long)) != RP_OK)
+        return cudaErrorMemoryAllocation;
+    unsigned long long* qcount = fp32 ? (unsigned long long*)c->s_queue.p : nullptr;
+    unsigned long long* queue = fp32 ? qcount + 1 : nullptr;
+    if (fp32) {
+        cudaError_t e = cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+    }
     const long long K = (long long)c->nk * c->nemp * c->nocc;
     const int bs = 128;
-    dim3 grid((unsigned)((K + bs - 1) / bs), (unsigned)((nf + TT_FCH - 1) / TT_FCH));
-    k_tetra_weights<<<grid, bs, 0, st>>>(
-        (const double*)c->d_energy.p, c->T.empty() ? nullptr : (const double*)c->d_T.p, c->nband, c->nocc,
-        c->nemp, c->nk, (const int*)c->plan.d_kp.p, (const int*)c->d_tets.p, (const int*)c->d_tetk.p, nf, d_freq,
-        axis, ordering, delta, da, dr, w);
+    // frequencies per grid row: all of them when the pairs alone fill the GPU
+    const int fch = K >= 4LL * 152 * bs ? nf : std::max(1, (int)((nf * K + 4LL * 152 * bs - 1) / (4LL * 152 * bs)));
+    dim3 grid((unsigned)((K + bs - 1) / bs), (unsigned)((nf + fch - 1) / fch));
+    const size_t smem = (size_t)24 * TT_FIELDS * bs * (fp32 ? sizeof(float) : sizeof(double));
+    if (fp32) {
+        cudaFuncSetAttribute(k_tetra_weights<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_tetra_weights<float><<<grid, bs, smem, st>>>(
+            (const double*)c->d_energy.p, c->T.empty() ? nullptr : (const double*)c->d_T.p, c->nband, c->nocc,
+            c->nemp, c->nk, (const int*)c->plan.d_kp.p, (const int*)c->d_tets.p, (const int*)c->d_tetk.p, nf, fch,
+            d_freq, axis, ordering, delta, da, dr, w, queue, qcap, qcount);
+        // the deferred items (count read on the device): a grid-stride pass
+        k_tetra_fixup<<<c->num_sms * 8, 128, 0, st>>>(
+            (const double*)c->d_energy.p, c->T.empty() ? nullptr : (const double*)c->d_T.p, c->nband, c->nocc,
+            c->nemp, c->nk, (const int*)c->plan.d_kp.p, (const int*)c->d_tets.p, (const int*)c->d_tetk.p, d_freq,
+            axis, ordering, delta, da, dr, queue, qcount, qcap, w);
+    } else {
+        cudaFuncSetAttribute(k_tetra_weights<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_tetra_weights<double><<<grid, bs, smem, st>>>(
+            (const double*)c->d_energy.p, c->T.empty() ? nullptr : (const double*)c->d_T.p, c->nband, c->nocc,
+            c->nemp, c->nk, (const int*)c->plan.d_kp.p, (const int*)c->d_tets.p, (const int*)c->d_tetk.p, nf, fch,
+            d_freq, axis, ordering, delta, da, dr, w, nullptr, 0, nullptr);
+    }
     return cudaGetLastError();
 }
 

@@ -203,3 +203,37 @@ def test_build_chi0_bf16x3_tiny(tiny, tiny_ref):
     assert np.all(e < BF16X3_TOL)
     W, _ = ctx.rp_solve_w(q, chi)
     assert np.all(_rel_fro(W, W_ref) < BF16X3_TOL)
+
+
+# ---- FP32 weights of the split-precision path (FP64 re-evaluation near degeneracies) ----
+@pytest.mark.parametrize("name,axis,delta", [("micro", "imag", 0.0), ("small", "real", 0.02),
+                                             ("small", "real", 0.05 / 27.211386245988)])
+def test_tetra_weights_fp32_path(name, axis, delta):
+    from dataclasses import replace
+    wl = workload(name)
+    freq = wl.freq if axis == wl.axis else (np.linspace(0.0, 0.8, 5) if axis == "real" else wl.freq)
+    wl = replace(wl, axis=axis, delta=delta, freq=freq)
+    ctx = _ctx(wl)
+    q = wl.q[0]
+    ref = OC.pair_weights(wl, q)
+    got = ctx.rp_tetra_weights(q, _axis(wl), _ordering(wl), wl.freq, wl.delta, precision=rp.RP_BF16X3)
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    err = np.abs(got - ref).max(axis=1, keepdims=True) / scale
+    print("fp32 weights max err / max |w|", err.ravel())
+    assert np.all(np.isfinite(got))
+    assert np.all(err < 1e-5)
+
+
+def test_build_chi0_bf16x3_real_axis_small_broadening():
+    from dataclasses import replace
+    wl = workload("small")
+    wl = replace(wl, axis="real", delta=0.05 / 27.211386245988, freq=np.linspace(0.0, 0.7, 6))
+    ctx = _ctx(wl)
+    q = wl.q[0]
+    G = OL.eps_sphere(wl.cell.lat, q, wl.ecut_eps[0])
+    M = OP.pair_density(wl.bands, wl.nocc, wl.nemp, q, G, fft=wl.fft)
+    chi_ref = OC.chi0(M, OC.pair_weights(wl, q))
+    chi = ctx.rp_build_chi0(q, rp.RP_AXIS_REAL, rp.RP_TIME_ORDERED, wl.freq, wl.delta, rp.RP_BF16X3)
+    e = _rel_fro(chi, chi_ref)
+    print("bf16x3 real-axis chi0 rel err", e)
+    assert np.all(e < BF16X3_TOL)
