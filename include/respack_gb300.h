@@ -157,6 +157,26 @@ int rp_solve_w(rp_ctx* ctx, const double q_frac[3], int nfreq, const double* chi
  *   if an asynchronous rp_solve_w met a bad pivot since the previous check, else RP_OK. */
 int rp_check_numeric(rp_ctx* ctx);
 
+/* rp_contract_chi0_static -- the RP_BF16X3 contraction of rp_contract_chi0 without any
+ *   device allocation, for callers that cannot allocate device memory when they need chi0
+ *   (for example a host program that hands the whole device memory budget to its own pool at
+ *   start-up and forbids later cudaMalloc calls, or a loop that must not risk the device-wide
+ *   synchronisation an allocation can cause).  The paper has no counterpart; this is an
+ *   interface variant only.  No context is needed.
+ *   ng, K, nfreq  sizes;  M c128 [ng][K], w c128 [nfreq][K] and chi_out c128 [nfreq][ng][ng] are
+ *                 device pointers of the current device owned by the caller; work is queued on
+ *                 cuda_stream and the call returns without synchronising.
+ *   Scratch: a 64 MiB array inside the library, held by every GPU that loads it until the
+ *   process exits.  Limits: with kp2 = 2 K rounded up to a multiple of 64,
+ *   ng * kp2 <= 12582912 and nfreq * kp2 / 2 <= 1048576; larger requests return RP_ERR_ARG
+ *   before anything is queued.  The first call on a device looks up the array's device address
+ *   (once per device); make that first call before any stream capture.  Every call uses the
+ *   same array: calls whose work overlaps on the GPU (other streams, other threads) race and
+ *   must be serialised by the caller.  A device-side wait that gives up leaves chi_out
+ *   unspecified.  Returns RP_OK, RP_ERR_ARG or RP_ERR_CUDA. */
+int rp_contract_chi0_static(int ng, long long K, int nfreq, const double* M, const double* w,
+                            double* chi_out, void* cuda_stream);
+
 /* rp_profile_enable -- measurement aid (no counterpart in the paper).  enable = 1 starts
  *   recording a CUDA event pair on the launching stream around every stage of the path and
  *   counting kernel launches per stage; enable = 0 stops.  Either call resets the totals.

@@ -24,7 +24,7 @@ _STATUS = {0: "RP_OK", -1: "RP_ERR_ARG", -2: "RP_ERR_STATE", -3: "RP_ERR_OOM", -
 # every symbol the header declares
 EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density", "rp_tetra_weights",
            "rp_contract_chi0", "rp_build_chi0", "rp_solve_w", "rp_check_numeric", "rp_profile_enable",
-           "rp_profile_read", "rp_last_error", "rp_destroy"]
+           "rp_profile_read", "rp_last_error", "rp_destroy", "rp_contract_chi0_static"]
 
 
 class RPError(RuntimeError):
@@ -59,6 +59,7 @@ def library():
         "rp_profile_read": (I, [P, P, P]),
         "rp_last_error": (ctypes.c_char_p, [P]),
         "rp_destroy": (None, [P]),
+        "rp_contract_chi0_static": (I, [I, LL, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
