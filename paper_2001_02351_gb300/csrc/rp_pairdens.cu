@@ -123,28 +123,44 @@ static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs
 // ---- fused pair kernels (line transforms in registers) ----
 
 // product and z transform: one (pair, x, y) line per thread, pruned to the z values of the sphere
-// u holds the bands of nkb k points ([kl][band][line][z]); grid.z runs over (kl, pa), pa < nab;
-// T1 pair index (kl * nab + pa) * nocc + o
+// u holds the bands of nkb k points ([kl][band][line][z]).  A CTA takes 32 consecutive lines of
+// one empty band (grid.y runs over (kl, pa), pa < nab) and loops over the occupied bands four at
+// a time; the lines are staged in shared memory with coalesced loads (rows padded by one element
+// against bank conflicts).  T1 pair index (kl * nab + pa) * nocc + o.
 template <typename C, int N3>
 __global__ void __launch_bounds__(128) k_pair_z(const C* __restrict__ u, int nband, int nocc, int a0, int nab,
                                                 int nlines, const int* __restrict__ zmap, int nz,
                                                 const C* __restrict__ tw, C* __restrict__ T1) {
-    const int line = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int o = blockIdx.y * 4 + (threadIdx.x >> 5);
-    const int kl = blockIdx.z / nab, pa = blockIdx.z % nab;
-    if (line >= nlines || o >= nocc) return;
+    constexpr int LD = N3 + 1;
+    extern __shared__ __align__(16) unsigned char sm_z[];
+    C* sa = reinterpret_cast<C*>(sm_z);              // [32][LD]
+    C* so = sa + 32 * LD;                            // [4][32][LD]
+    const int l0 = blockIdx.x * 32;
+    const int kl = blockIdx.y / nab, pa = blockIdx.y % nab;
+    const int nl = min(32, nlines - l0);
     const C* uk = u + (size_t)kl * nband * nlines * N3;
-    const C* ua = uk + ((size_t)(nocc + a0 + pa) * nlines + line) * N3;
-    const C* uo = uk + ((size_t)o * nlines + line) * N3;
-    C x[N3];
+    const C* ua = uk + ((size_t)(nocc + a0 + pa) * nlines + l0) * N3;
+    for (int e = threadIdx.x; e < nl * N3; e += 128) sa[(e / N3) * LD + e % N3] = ua[e];
+    const int li = threadIdx.x & 31, oi = threadIdx.x >> 5;
+    for (int o0 = 0; o0 < nocc; o0 += 4) {
+        __syncthreads();
+        for (int q = 0; q < 4 && o0 + q < nocc; ++q) {
+            const C* uo = uk + ((size_t)(o0 + q) * nlines + l0) * N3;
+            for (int e = threadIdx.x; e < nl * N3; e += 128) so[q * 32 * LD + (e / N3) * LD + e % N3] = uo[e];
+        }
+        __syncthreads();
+        const int o = o0 + oi;
+        if (li >= nl || o >= nocc) continue;
+        C x[N3];
 #pragma unroll
-    for (int z = 0; z < N3; ++z) x[z] = c_conjmul(ua[z], uo[z]);
-    LineFFT<C, N3, 1>::run(x, tw);
-    C* dst = T1 + ((size_t)(blockIdx.z * nocc + o) * nlines + line) * nz;
+        for (int z = 0; z < N3; ++z) x[z] = c_conjmul(sa[li * LD + z], so[oi * 32 * LD + li * LD + z]);
+        LineFFT<C, N3, 1>::run(x, tw);
+        C* dst = T1 + ((size_t)(blockIdx.y * nocc + o) * nlines + l0 + li) * nz;
 #pragma unroll
-    for (int z = 0; z < N3; ++z) {
-        const int iz = zmap[z];
-        if (iz >= 0) dst[iz] = x[z];
+        for (int z = 0; z < N3; ++z) {
+            const int iz = zmap[z];
+            if (iz >= 0) dst[iz] = x[z];
+        }
     }
 }
 
@@ -196,8 +212,10 @@ __global__ void __launch_bounds__(256) k_pair_yx(const C* __restrict__ T1, int n
 template <typename C, int N3>
 static void launch_z(const C* u, int nkb, int nband, int nocc, int a0, int nab, int nlines, const int* zmap, int nz,
                      const C* tw, C* T1, cudaStream_t st) {
-    dim3 grid((nlines + 31) / 32, (nocc + 3) / 4, nkb * nab);
-    k_pair_z<C, N3><<<grid, 128, 0, st>>>(u, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1);
+    dim3 grid((nlines + 31) / 32, nkb * nab);
+    const size_t smem = (size_t)5 * 32 * (N3 + 1) * sizeof(C);
+    cudaFuncSetAttribute(k_pair_z<C, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_pair_z<C, N3><<<grid, 128, smem, st>>>(u, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1);
 }
 
 template <typename C, int N2, typename CO>

@@ -123,33 +123,70 @@ __device__ __forceinline__ typename TT<R>::C dd_series(const R (&t)[5], int m, t
     return tmul(S, p);
 }
 
-// run x[i..j] of the sorted nodes by the series about its midpoint
+// 6 / (m (m-1) (m-2) (m-3)) for m = 0 .. 63 (entries below 4 unused)
+__constant__ double c_bq[64];
+
+// Divided difference of order n = m - 1 over the sorted run x[i..j] (m nodes) by the Taylor
+// series about its first node x_i, whose logarithm L = log(z - x_i) is known:
+//   sum_q f^(q)(x_i)/q! h_{q-n}(x - x_i),  f^(q)(x_i)/q! = y^(3-q) b_q(L),  y = z - x_i.
+// The sum runs over scaled nodes (x - x_i)/|y| and unit-modulus powers conj(y)/|y|.
 template <typename R>
-__device__ __forceinline__ typename TT<R>::C dd_run(const R (&x)[5], int i, int j, typename TT<R>::C z) {
-    R t[5] = {0, 0, 0, 0, 0};
-    const R c = (R)0.5 * (x[i] + x[j]);
-    R tmax = 0;
+__device__ typename TT<R>::C dd_run_about_node(const R (&x)[5], int i, int j, typename TT<R>::C y,
+                                               typename TT<R>::C L, R rho) {
+    using C = typename TT<R>::C;
+    const int n = j - i;
+    const R r = TT<R>::hyp(y.x, y.y);
+    const R rinv = (R)1 / r;
+    R e[6] = {1, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-        if (v >= i && v <= j) {
-            t[v - i] = x[v] - c;
-            tmax = fmax(tmax, fabs(x[v] - c));
+        if (v > i && v <= j) {   // node x_i itself contributes a zero offset
+            const R tv = (x[v] - x[i]) * rinv;
+#pragma unroll
+            for (int q = 5; q >= 1; --q) e[q] += tv * e[q - 1];
         }
     }
-    const typename TT<R>::C y = TT<R>::mk(z.x - c, z.y);
-    return dd_series<R>(t, j - i + 1, y, nterms<R>(tmax / TT<R>::hyp(y.x, y.y)));
+    const int K = nterms<R>(rho);
+    const C u = TT<R>::mk(y.x * rinv, -y.y * rinv);
+    R h1 = 0, h2 = 0, h3 = 0, h4 = 0, hk = 1;
+    C uk = TT<R>::mk(1, 0);
+    C S = bcoef<R>(n, L);
+    for (int k = 1; k <= K; ++k) {
+        const R hn = e[1] * hk - e[2] * h1 + e[3] * h2 - e[4] * h3 + e[5] * h4;
+        h4 = h3; h3 = h2; h2 = h1; h1 = hk; hk = hn;
+        uk = tmul(uk, u);
+        const int q = n + k;
+        const C b = q >= 4 ? TT<R>::mk((R)c_bq[q < 64 ? q : 63], 0) : bcoef<R>(q, L);
+        S = tadd(S, tscale(tmul(b, uk), hk));
+    }
+    C p = TT<R>::mk(1, 0);
+    if (n <= 3) {
+        for (int q = 0; q < 3 - n; ++q) p = tmul(p, y);
+    } else {
+        const C w = tinv(y);
+        for (int q = 0; q < n - 3; ++q) p = tmul(p, w);
+    }
+    return tmul(S, p);
 }
 
-// full divided-difference table (recursion, series for narrow runs).  *narrow is set when a
-// run of nonzero width narrower than TAU times its distance to the pole occurs.
+#define TT_TAU_RUN 0.3
+
+// full divided-difference table: recursion between well separated nodes, closed forms for
+// coincident nodes, Taylor series about the run's first node for narrow runs (no logarithm
+// beyond the five node logarithms).  *narrow is set when a narrow run of nonzero width occurs.
 template <typename R>
-__device__ __noinline__ typename TT<R>::C dd5_table(const R (&x)[5], typename TT<R>::C z, bool* narrow) {
+__device__ typename TT<R>::C dd5_table(const R (&x)[5], typename TT<R>::C z, bool* narrow) {
     using C = typename TT<R>::C;
-    C D[5][5];
+    C D[5][5], L[5], Y[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const C y = TT<R>::mk(z.x - x[i], z.y);
-        D[i][i] = tmul(tmul(tmul(y, y), y), TT<R>::clog(y));
+        Y[i] = TT<R>::mk(z.x - x[i], z.y);
+        if (i > 0 && x[i] == x[i - 1]) {
+            L[i] = L[i - 1];
+        } else {
+            L[i] = TT<R>::clog(Y[i]);
+        }
+        D[i][i] = tmul(tmul(tmul(Y[i], Y[i]), Y[i]), L[i]);
     }
 #pragma unroll
     for (int n = 1; n < 5; ++n)
@@ -157,11 +194,22 @@ __device__ __noinline__ typename TT<R>::C dd5_table(const R (&x)[5], typename TT
         for (int i = 0; i + n < 5; ++i) {
             const int j = i + n;
             const R s = x[j] - x[i];
-            const R c = (R)0.5 * (x[i] + x[j]);
-            const R Rr = TT<R>::hyp(z.x - c, z.y);
-            if (s <= (R)TT_TAU * Rr) {
-                if (s > 0) *narrow = true;
-                D[i][j] = dd_run<R>(x, i, j, z);
+            if (s == (R)0) {
+                // confluent: f^(n)(x_i)/n!
+                C p = TT<R>::mk(1, 0);
+                if (n <= 3) {
+                    for (int q = 0; q < 3 - n; ++q) p = tmul(p, Y[i]);
+                } else {
+                    const C w = tinv(Y[i]);
+                    for (int q = 0; q < n - 3; ++q) p = tmul(p, w);
+                }
+                D[i][j] = tmul(bcoef<R>(n, L[i]), p);
+                continue;
+            }
+            const R Ri = TT<R>::hyp(Y[i].x, Y[i].y);
+            if (s <= (R)TT_TAU_RUN * Ri) {
+                *narrow = true;
+                D[i][j] = dd_run_about_node<R>(x, i, j, Y[i], L[i], s / Ri);
             } else {
                 D[i][j] = tscale(tsub(D[i + 1][j], D[i][j - 1]), (R)1 / s);
             }
@@ -397,6 +445,12 @@ __global__ void __launch_bounds__(128) k_tetra_weights(const double* __restrict_
 
 cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double* d_freq, double delta,
                          double da, double dr, bool fp32, double2* w, cudaStream_t st) {
+    {   // series coefficients 6 / (m (m-1) (m-2) (m-3)) of the resonant path
+        static double bq[64];
+        for (int m = 0; m < 64; ++m) bq[m] = m >= 4 ? 6.0 / ((double)m * (m - 1) * (m - 2) * (m - 3)) : 0.0;
+        cudaError_t e = cudaMemcpyToSymbolAsync(c_bq, bq, sizeof(bq), 0, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
     // FP64 work list of the FP32 pass: up to 2% of all evaluations (overflow is evaluated in place)
     const long long Kp = (long long)c->nk * c->nemp * c->nocc;
     unsigned long long qcap = (unsigned long long)std::max(1LL << 16, (long long)(0.02 * 48.0 * nf * Kp));
