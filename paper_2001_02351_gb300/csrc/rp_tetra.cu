@@ -351,9 +351,8 @@ __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ 
 // tetrahedron-vertex node sets are prepared once in FP64 (sort, merge, centre) and kept in
 // shared memory; every frequency is then evaluated from them in precision R.  Nodes and poles
 // are taken relative to the pair's own transition energy D0 so that R = float keeps its
-// resolution.  With R = float only the series branch (pole farther than 2x the node spread)
-// runs in FP32; resonant node sets (recursion branch) and node sets with two nodes closer than
-// TT_NEAR but not merged (near degeneracy) are evaluated in FP64.
+// resolution.  With R = float every node set is evaluated in FP32 except those with two nodes
+// closer than TT_NEAR but not merged (near degeneracy), which go to an FP64 pass.
 #define TT_NEAR 1e-5
 #define TT_FIELDS 5   // t1, t2, t3, centre - D0, spread (negative: near-degenerate set)
 
@@ -424,11 +423,6 @@ __global__ void __launch_bounds__(128) k_tetra_weights(const double* __restrict_
                 const R Rr = TT<R>::hyp(y.x, y.y);
                 if (spread <= (R)TT_TAU * Rr) {
                     sacc = tadd(sacc, dd_series<R>(tr, 5, y, nterms<R>((R)0.5 * spread / Rr)));
-                } else if (sizeof(R) == 4) {
-                    // the recursion can amplify rounding by a few thousand near the series boundary:
-                    // resonant node sets (about 1%) go to the FP64 pass
-                    defer_or_eval(queue, qcap, qcount, t, f, s, side, sacc, E, nband, nocc, a, o, kp, tets,
-                                  tetk[24 * k + s], da, dr, zd);
                 } else {
                     R xr[5];
 #pragma unroll
