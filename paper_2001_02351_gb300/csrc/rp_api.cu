@@ -406,7 +406,7 @@ static int pair_density_device(rp_ctx* c, int k0, int k1, void* M, bool fp32, lo
         const int nkb = std::min(kb, k1 - k);
         prof_begin(c, 0, st);
         cudaError_t e = launch_gather_inverse(c, k, nkb, fp32, st);
-        prof_end(c, 0, st, 5);
+        prof_end(c, 0, st, 1);
         if (e != cudaSuccess) return cuda_fail(c, e, "gather/inverse transform");
         prof_begin(c, 1, st);
         int nl = 0;

@@ -120,6 +120,77 @@ __global__ void k_sphere_readout(const C* __restrict__ T2, const C* __restrict__
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Gather + inverse transform of one band per CTA: the Miller box of the band (shifted by -G0 for
+// the empty bands at k' = k + q - G0) is built in shared memory, then every x plane of the
+// real-space grid is formed by three small sums (m1 -> x, m2 -> y, m3 -> z) and written once.
+template <typename C>
+__global__ void __launch_bounds__(256) k_gather_grid(const double2* __restrict__ coef, const int* __restrict__ miller,
+                                                     const int* __restrict__ npw, int npw_max, int nband, int nocc,
+                                                     const int* __restrict__ kp, const int* __restrict__ g0, int k0,
+                                                     int lb, int N1, int N2, int N3, const C* __restrict__ ex,
+                                                     const C* __restrict__ ey, const C* __restrict__ ez,
+                                                     C* __restrict__ u) {
+    using R = typename CT<C>::R;
+    const int B = 2 * lb + 1;
+    extern __shared__ __align__(16) unsigned char sm_g[];
+    C* box = reinterpret_cast<C*>(sm_g);     // [B][B][B]
+    C* u1 = box + B * B * B;                 // [B][B]   (m2, m3) of one x
+    C* u2 = u1 + B * B;                      // [N2][B]  (y, m3) of one x
+    const int band = blockIdx.x;             // kl * nband + s
+    const int kl = band / nband, s = band % nband;
+    const int k = k0 + kl;
+    const int ks = (s < nocc) ? k : kp[k];
+    for (int e = threadIdx.x; e < B * B * B; e += blockDim.x) box[e] = CT<C>::make(0, 0);
+    __syncthreads();
+    int sh0 = 0, sh1 = 0, sh2 = 0;
+    if (s >= nocc) { sh0 = g0[3 * k]; sh1 = g0[3 * k + 1]; sh2 = g0[3 * k + 2]; }
+    for (int p = threadIdx.x; p < npw[ks]; p += blockDim.x) {
+        const int* m = miller + ((size_t)ks * npw_max + p) * 3;
+        const double2 v = coef[((size_t)ks * nband + s) * npw_max + p];
+        box[((m[0] - sh0 + lb) * B + (m[1] - sh1 + lb)) * B + (m[2] - sh2 + lb)] = CT<C>::make((R)v.x, (R)v.y);
+    }
+    C* dst = u + (size_t)band * N1 * N2 * N3;
+    for (int x = 0; x < N1; ++x) {
+        __syncthreads();
+        const C* e1 = ex + (size_t)x * B;
+        for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+            R re = 0, im = 0;
+            for (int m1 = 0; m1 < B; ++m1) {
+                const C v = box[m1 * B * B + e], w = e1[m1];
+                re += w.x * v.x - w.y * v.y;
+                im += w.x * v.y + w.y * v.x;
+            }
+            u1[e] = CT<C>::make(re, im);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < N2 * B; e += blockDim.x) {
+            const int y = e / B, m3 = e % B;
+            const C* e2 = ey + (size_t)y * B;
+            R re = 0, im = 0;
+            for (int m2 = 0; m2 < B; ++m2) {
+                const C v = u1[m2 * B + m3], w = e2[m2];
+                re += w.x * v.x - w.y * v.y;
+                im += w.x * v.y + w.y * v.x;
+            }
+            u2[e] = CT<C>::make(re, im);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < N2 * N3; e += blockDim.x) {
+            const int y = e / N3, z = e % N3;
+            const C* e3 = ez + (size_t)z * B;
+            const C* src = u2 + y * B;
+            R re = 0, im = 0;
+            for (int m3 = 0; m3 < B; ++m3) {
+                const C v = src[m3], w = e3[m3];
+                re += w.x * v.x - w.y * v.y;
+                im += w.x * v.y + w.y * v.x;
+            }
+            dst[(size_t)x * N2 * N3 + e] = CT<C>::make(re, im);
+        }
+    }
+}
+
+
 // ---- fused pair kernels (line transforms in registers) ----
 
 // product and z transform: one (pair, x, y) line per thread, pruned to the z values of the sphere
@@ -267,6 +338,19 @@ static cudaError_t gather_inverse_t(rp_ctx* c, int k0, int nkb, const C* const e
     const int B = 2 * c->lb + 1;
     const int N1 = c->fft[0], N2 = c->fft[1], N3 = c->fft[2];
     const long long nbands = (long long)nkb * c->nband;
+    {   // one CTA per band with the Miller box in shared memory
+        const size_t smem = sizeof(C) * ((size_t)B * B * B + (size_t)B * B + (size_t)N2 * B);
+        if (smem <= 200 * 1024) {
+            if (ensure(c, c->s_u, (size_t)nbands * c->nr * sizeof(C))) return cudaErrorMemoryAllocation;
+            cudaError_t e = cudaFuncSetAttribute(k_gather_grid<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_gather_grid<C><<<(unsigned)nbands, 256, smem, st>>>(
+                (const double2*)c->d_coef.p, (const int*)c->d_miller.p, (const int*)c->d_npw.p, c->npw_max, c->nband,
+                c->nocc, (const int*)c->plan.d_kp.p, (const int*)c->plan.d_g0.p, k0, c->lb, N1, N2, N3, einv[0], einv[1],
+                einv[2], (C*)c->s_u.p);
+            return cudaGetLastError();
+        }
+    }
     const size_t box = (size_t)nbands * B * B * B, u1 = (size_t)nbands * N1 * B * B,
                  u2 = (size_t)nbands * N1 * N2 * B, uu = (size_t)nbands * c->nr;
     if (ensure(c, c->s_box, box * sizeof(C)) || ensure(c, c->s_u1, u1 * sizeof(C)) ||
