@@ -1,19 +1,25 @@
 // chi[f][G][G'] = sum_b w[f][b] M[G][b] conj(M[G'][b])   (Eq. chi)  --  BF16x3 on tcgen05.
 //
 // Real form of the complex product: with b running over pairs and the real index
-// k' = 2b + {0,1} interleaving (re, im), the G row of A is exactly the interleaved storage of
-// M[G][.], and for each G' the weighted operand B = w conj(M) contributes two rows:
+// k' = 2b + {0,1} interleaving (re, im), the stored row M[G][.] is the interleaved real row, and
+// for each frequency f and each G' the weighted operand w_f conj(M[G']) contributes two rows:
 //   re-row (P, Q), im-row (-Q, P)  with  P = wr mr + wi mi,  Q = wr mi - wi mr,
-// so that  D[G][re-row G'] = Re chi[G][G'],  D[G][im-row G'] = Im chi[G][G'].
+// so that  <re-row G', row G> = Re chi_f[G][G'],  <im-row G', row G> = Im chi_f[G][G'].
 // Each real operand x is split x = hi + lo into two bf16 and the product is
-// a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs), accumulated in FP32 in tensor memory and
-// flushed into FP64 every FLUSH_STAGES stages (double-buffered accumulators).
+// a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs), accumulated in FP32 in tensor memory over a
+// window of TC_FLUSH_STAGES stages and then added into the FP64 result.
 //
-// CTA: 14 warps.  warp 0 = TMA producer (A_hi, A_lo rows of the G tile; the same arrays'
-// rows of the G' tile as raw B; the stage's 32 weights), warp 1 = MMA issuer, warps 2-9 =
-// B builders (scale by w, split, write the 128B-swizzled K-major tile), warps 10-13 =
-// epilogue (tcgen05.ld -> FP64).
-// Tile: 128 G rows x (64 G' re-rows + 64 G' im-rows), K step 64 reals per stage.
+// Tile (one tcgen05.mma M = 128, N = 208, K = 16 per step): the 128 rows of the MMA's A side are
+// built in shared memory from 32 rows M[G'] and the weights of two frequencies
+// (re f0 | im f0 | re f1 | im f1, 32 rows each); the 208 rows of the B side are raw rows M[G],
+// loaded by TMA.  Padding of NG is to multiples of 32 and 208 only, and one load of M[G'] serves
+// two frequencies.  A job is one tile over one accumulation window; the windows of a tile are
+// added into chi with FP64 atomics, so jobs spread evenly over the SMs.
+//
+// CTA: 14 warps.  warp 0 = TMA producer (raw rows M[G] of the tile, rows M[G'], the stage's
+// weights of both frequencies; the stages two ahead are prefetched into L2), warp 1 = MMA
+// issuer, warps 2-9 = builders of the weighted rows (scale by w, split, write the
+// 128B-swizzled K-major tile), warps 10-13 = epilogue (tcgen05.ld -> FP64 atomics).
 // Every wait is bounded; a wait that gives up records where in err_flag[1] and the CTA
 // leaves through the common teardown (its copies in flight are waited for, TMEM is freed).
 #include <cuda.h>
@@ -23,20 +29,24 @@
 
 namespace rp {
 
-#define TC_NS 3                 // load stages
-#define TC_BM 128               // G rows per tile
-#define TC_BN 64                // G' per tile (128 real columns)
+#define TC_NS 2                 // load stages (two, plus L2 prefetch of the stages ahead)
+#define TC_BM 128               // built rows per tile (MMA M)
+#define TC_GN 32                // G' per tile and frequency
+#define TC_BN 208               // raw G rows per tile (MMA N)
 #define TC_BK 64                // reals per stage
 #define TC_FLUSH_STAGES 128     // stages per FP32 accumulation window (8192 reals)
 #define TC_THREADS 448
-#define TC_NBUILD 256           // B-builder threads (warps 2-9); epilogue = warps 10-13
+#define TC_NBUILD 256           // builder threads (warps 2-9); epilogue = warps 10-13
+#define TC_TMEM_COLS 512        // two accumulators of TC_BN columns, 256 apart
 
-#define TC_A_BYTES (TC_BM * TC_BK * 2)            // 16 KB
-#define TC_R_BYTES (TC_BN * TC_BK * 2)            // 8 KB
+#define TC_RAW_BYTES (TC_BN * TC_BK * 2)          // 26 KB (26 swizzle atoms)
+#define TC_R_BYTES (TC_GN * TC_BK * 2)            // 4 KB
 #define TC_W_BYTES (TC_BK / 2 * 8)                // 32 complex float weights = 256 B
-#define TC_STAGE_LOAD (2 * TC_A_BYTES + 2 * TC_R_BYTES + TC_W_BYTES)
-#define TC_STAGE_BYTES (2 * TC_A_BYTES + 2 * TC_R_BYTES + 1024)   // 49 KB, keeps 1024-B alignment
-#define TC_B_BYTES (2 * TC_BN * TC_BK * 2)        // 16 KB (128 rows)
+#define TC_OFF_R (2 * TC_RAW_BYTES)
+#define TC_OFF_W (2 * TC_RAW_BYTES + 2 * TC_R_BYTES)
+#define TC_STAGE_LOAD (2 * TC_RAW_BYTES + 2 * TC_R_BYTES + 2 * TC_W_BYTES)
+#define TC_STAGE_BYTES (TC_OFF_W + 1024)          // 61 KB, keeps 1024-B alignment
+#define TC_B_BYTES (TC_BM * TC_BK * 2)            // 16 KB (128 built rows)
 #define TC_SMEM_B0 (TC_NS * TC_STAGE_BYTES)
 #define TC_SMEM_BAR (TC_SMEM_B0 + 2 * 2 * TC_B_BYTES)
 #define TC_SMEM_TOTAL (TC_SMEM_BAR + 256 + 1024)
@@ -87,6 +97,11 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                  : "memory");
 }
 
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x), "r"(y)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
@@ -100,9 +115,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// kind::f16 instruction descriptor: D f32, A bf16, B bf16, both K-major, M = 128, N = 128
+// kind::f16 instruction descriptor: D f32, A bf16, B bf16, both K-major, M = 128, N = TC_BN
 __host__ __device__ constexpr uint32_t tc_idesc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
@@ -131,15 +146,20 @@ __device__ __forceinline__ void split2(float x, float& hi, float& lo) {
 }
 
 struct TcArgs {
-    const float2* w32;      // [nf][kp2/2] complex float weights of this block (zero padded)
+    const float2* w32;      // [2 * nfp][kp2/2] complex float weights of this block (zero padded)
     long long K;
-    int ng, nf, mt, nt, nst;
+    int ng, nf, nfp, nblk, mt, nst, nwin;
     double2* chi;
     int* err;
 };
 
+static_assert(TC_BN % 16 == 0 && TC_BN <= 256 && TC_BN % 32 == 16, "epilogue reads TC_BN in 32- and one 16-column load");
+static_assert(TC_BN <= 256 && 256 + TC_BN <= TC_TMEM_COLS, "two accumulators fit the allocation");
+static_assert(TC_SMEM_TOTAL <= 232448, "shared memory per CTA");
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_contract_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+    k_contract_bf16x3(const __grid_constant__ CUtensorMap raw_hi, const __grid_constant__ CUtensorMap raw_lo,
+                      const __grid_constant__ CUtensorMap row_hi, const __grid_constant__ CUtensorMap row_lo,
                       TcArgs args) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -172,7 +192,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(taddr_slot)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_slot)),
+                     "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -180,10 +201,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *taddr_slot;
 
-    const int njobs = args.nf * args.mt * args.nt;
+    const int ntile = args.nfp * args.nblk * args.mt;
+    const int njobs = ntile * args.nwin;
     const int nst = args.nst;
-    const int nchunk = (nst + TC_FLUSH_STAGES - 1) / TC_FLUSH_STAGES;
     int* err = args.err;
+    // job -> (accumulation window, frequency pair, G' block, G tile); consecutive jobs share a
+    // window.  The last block and tile are moved back to end at ng, so that (for ng >= TC_BN) every
+    // box lies inside the arrays; a block or tile writes only the rows from its own start (nown,
+    // mown) on, so rows covered twice are added once.
+    auto job_tile = [&](int job, int& w0, int& w1, int& fp, int& n0, int& m0, int& nown, int& mown) {
+        const int win = job / ntile, t = job % ntile;
+        fp = t / (args.nblk * args.mt);
+        const int r = t % (args.nblk * args.mt);
+        nown = (r / args.mt) * TC_GN;
+        mown = (r % args.mt) * TC_BN;
+        n0 = min(nown, max(0, args.ng - TC_GN));
+        m0 = min(mown, max(0, args.ng - TC_BN));
+        w0 = win * TC_FLUSH_STAGES;
+        w1 = min(nst, w0 + TC_FLUSH_STAGES);
+    };
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -192,25 +228,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bool ok = true;
             const long long kpad = (long long)nst * (TC_BK / 2);
             for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
-                const int f = job / (args.mt * args.nt);
-                const int rem = job % (args.mt * args.nt);
-                const int m0 = (rem / args.nt) * TC_BM, n0 = (rem % args.nt) * TC_BN;
-                const float2* wrow = args.w32 + (size_t)f * kpad;
-                for (int st = 0; st < nst; ++st, ++sg) {
+                int w0, w1, fp, n0, m0, nown, mown;
+                job_tile(job, w0, w1, fp, n0, m0, nown, mown);
+                // L2 prefetch only of boxes that lie inside the arrays
+                const bool pf_raw = m0 + TC_BN <= args.ng, pf_row = n0 + TC_GN <= args.ng;
+                const float2* wrow0 = args.w32 + (size_t)(2 * fp) * kpad;
+                const float2* wrow1 = wrow0 + kpad;
+                for (int st = w0; st < w1; ++st, ++sg) {
                     const int s = (int)(sg % TC_NS);
                     const uint32_t ph = (uint32_t)((sg / TC_NS) & 1);
+                    if (st + 2 < w1) {
+                        const int xp = (st + 2) * TC_BK;
+                        if (pf_raw) {
+                            tma_prefetch_2d(&raw_hi, xp, m0);
+                            tma_prefetch_2d(&raw_lo, xp, m0);
+                        }
+                        if (pf_row) {
+                            tma_prefetch_2d(&row_hi, xp, n0);
+                            tma_prefetch_2d(&row_lo, xp, n0);
+                        }
+                    }
                     if (!(ok = mbar_wait(empty(s), ph ^ 1, err, 101))) break;
                     const uint32_t base = sbase + s * TC_STAGE_BYTES;
                     mbar_expect_tx(full(s), TC_STAGE_LOAD);
-                    bulk_load(base + 2 * TC_A_BYTES + 2 * TC_R_BYTES, wrow + (size_t)st * (TC_BK / 2), TC_W_BYTES,
-                              full(s));
+                    bulk_load(base + TC_OFF_W, wrow0 + (size_t)st * (TC_BK / 2), TC_W_BYTES, full(s));
+                    bulk_load(base + TC_OFF_W + TC_W_BYTES, wrow1 + (size_t)st * (TC_BK / 2), TC_W_BYTES, full(s));
                     const int x = st * TC_BK;
-                    tma_load_2d(base, &map_hi, x, m0, full(s));
-                    tma_load_2d(base + TC_A_BYTES / 2, &map_hi, x, m0 + 64, full(s));
-                    tma_load_2d(base + TC_A_BYTES, &map_lo, x, m0, full(s));
-                    tma_load_2d(base + TC_A_BYTES + TC_A_BYTES / 2, &map_lo, x, m0 + 64, full(s));
-                    tma_load_2d(base + 2 * TC_A_BYTES, &map_hi, x, n0, full(s));
-                    tma_load_2d(base + 2 * TC_A_BYTES + TC_R_BYTES, &map_lo, x, n0, full(s));
+                    tma_load_2d(base, &raw_hi, x, m0, full(s));
+                    tma_load_2d(base + TC_RAW_BYTES, &raw_lo, x, m0, full(s));
+                    tma_load_2d(base + TC_OFF_R, &row_hi, x, n0, full(s));
+                    tma_load_2d(base + TC_OFF_R + TC_R_BYTES, &row_lo, x, n0, full(s));
                 }
             }
             // copies still in flight land before the CTA leaves
@@ -222,76 +269,82 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             long long sg = 0, cg = 0;
             bool ok = true;
-            for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
-                for (int ch = 0; ch < nchunk && ok; ++ch, ++cg) {
-                    const int ab = (int)(cg & 1);
-                    if (!(ok = mbar_wait(acce(ab), (uint32_t)(((cg >> 1) & 1) ^ 1), err, 111))) break;
+            for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x, ++cg) {
+                int w0, w1, fp, n0, m0, nown, mown;
+                job_tile(job, w0, w1, fp, n0, m0, nown, mown);
+                const int ab = (int)(cg & 1);
+                if (!(ok = mbar_wait(acce(ab), (uint32_t)(((cg >> 1) & 1) ^ 1), err, 111))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(ab * 256);
+                for (int st = w0; st < w1; ++st, ++sg) {
+                    const int s = (int)(sg % TC_NS);
+                    const int bb = (int)(sg & 1);
+                    if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 112))) break;
+                    if (!(ok = mbar_wait(bready(bb), (uint32_t)((sg >> 1) & 1), err, 113))) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t d = tmem + (uint32_t)(ab * 128);
-                    const int st1 = min(nst, (ch + 1) * TC_FLUSH_STAGES);
-                    for (int st = ch * TC_FLUSH_STAGES; st < st1; ++st, ++sg) {
-                        const int s = (int)(sg % TC_NS);
-                        const int bb = (int)(sg & 1);
-                        if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 112))) break;
-                        if (!(ok = mbar_wait(bready(bb), (uint32_t)((sg >> 1) & 1), err, 113))) break;
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t a_hi = sbase + s * TC_STAGE_BYTES, a_lo = a_hi + TC_A_BYTES;
-                        const uint32_t b_hi = sbase + TC_SMEM_B0 + bb * 2 * TC_B_BYTES, b_lo = b_hi + TC_B_BYTES;
+                    const uint32_t g_hi = sbase + s * TC_STAGE_BYTES, g_lo = g_hi + TC_RAW_BYTES;
+                    const uint32_t b_hi = sbase + TC_SMEM_B0 + bb * 2 * TC_B_BYTES, b_lo = b_hi + TC_B_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                            const uint32_t off = kk * 32;
-                            const uint32_t first = (st == ch * TC_FLUSH_STAGES && kk == 0) ? 0u : 1u;
-                            mma_bf16(d, sw128_desc(a_hi + off), sw128_desc(b_hi + off), first);
-                            mma_bf16(d, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
-                            mma_bf16(d, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
-                        }
-                        mma_commit(empty(s));
-                        mma_commit(bfree(bb));
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        const uint32_t first = (st == w0 && kk == 0) ? 0u : 1u;
+                        mma_bf16(d, sw128_desc(b_hi + off), sw128_desc(g_hi + off), first);
+                        mma_bf16(d, sw128_desc(b_hi + off), sw128_desc(g_lo + off), 1u);
+                        mma_bf16(d, sw128_desc(b_lo + off), sw128_desc(g_hi + off), 1u);
                     }
-                    if (ok) mma_commit(accf(ab));
+                    mma_commit(empty(s));
+                    mma_commit(bfree(bb));
                 }
+                if (ok) mma_commit(accf(ab));
             }
             // all issued MMAs complete before teardown
             mma_commit(done_bar);
             mbar_wait(done_bar, 0, err, 114);
         }
     } else if (warp < 2 + TC_NBUILD / 32) {
-        // ---------------- B builders (TC_NBUILD threads) ----------------
+        // ---------------- builders of the weighted rows (TC_NBUILD threads, one 16-B chunk each) ----
         const int t = threadIdx.x - 64;
+        const int r = t >> 3, c = t & 7;
         long long sg = 0;
         bool ok = true;
         for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
-            for (int st = 0; st < nst; ++st, ++sg) {
+            int w0, w1, fp, n0, m0, nown, mown;
+            job_tile(job, w0, w1, fp, n0, m0, nown, mown);
+            for (int st = w0; st < w1; ++st, ++sg) {
                 const int s = (int)(sg % TC_NS);
                 const int bb = (int)(sg & 1);
                 if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 121))) break;
                 if (!(ok = mbar_wait(bfree(bb), (uint32_t)(((sg >> 1) & 1) ^ 1), err, 122))) break;
-                const unsigned char* rhi = smem + s * TC_STAGE_BYTES + 2 * TC_A_BYTES;
+                const unsigned char* stage = smem + s * TC_STAGE_BYTES;
+                const unsigned char* rhi = stage + TC_OFF_R;
                 const unsigned char* rlo = rhi + TC_R_BYTES;
-                const float2* ws = reinterpret_cast<const float2*>(rlo + TC_R_BYTES);
                 unsigned char* bhi = smem + TC_SMEM_B0 + bb * 2 * TC_B_BYTES;
                 unsigned char* blo = bhi + TC_B_BYTES;
+                const uint32_t o = sw128_off(r, c);
+                const uint4 vh = *reinterpret_cast<const uint4*>(rhi + o);
+                const uint4 vl = *reinterpret_cast<const uint4*>(rlo + o);
+                const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&vh);
+                const __nv_bfloat162* l2 = reinterpret_cast<const __nv_bfloat162*>(&vl);
+                float mr[4], mi[4];
 #pragma unroll
-                for (int it = 0; it < (TC_BN * 8) / TC_NBUILD; ++it) {
-                    const int task = t + it * TC_NBUILD;
-                    const int r = task >> 3, c = task & 7;
-                    const uint32_t o = sw128_off(r, c);
-                    const uint4 vh = *reinterpret_cast<const uint4*>(rhi + o);
-                    const uint4 vl = *reinterpret_cast<const uint4*>(rlo + o);
+                for (int i = 0; i < 4; ++i) {
+                    const float2 hh = __bfloat1622float2(h2[i]);
+                    const float2 ll = __bfloat1622float2(l2[i]);
+                    mr[i] = hh.x + ll.x;
+                    mi[i] = hh.y + ll.y;
+                }
+#pragma unroll
+                for (int fq = 0; fq < 2; ++fq) {
+                    const float2* ws = reinterpret_cast<const float2*>(stage + TC_OFF_W + fq * TC_W_BYTES);
                     const float4 w01 = *reinterpret_cast<const float4*>(ws + 4 * c);
                     const float4 w23 = *reinterpret_cast<const float4*>(ws + 4 * c + 2);
                     const float wr[4] = {w01.x, w01.z, w23.x, w23.z};
                     const float wi[4] = {w01.y, w01.w, w23.y, w23.w};
-                    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&vh);
-                    const __nv_bfloat162* l2 = reinterpret_cast<const __nv_bfloat162*>(&vl);
                     uint32_t reh[4], rel[4], imh[4], iml[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const float2 hh = __bfloat1622float2(h2[i]);
-                        const float2 ll = __bfloat1622float2(l2[i]);
-                        const float mr = hh.x + ll.x, mi = hh.y + ll.y;
-                        const float P = wr[i] * mr + wi[i] * mi;
-                        const float Q = wr[i] * mi - wi[i] * mr;
+                        const float P = wr[i] * mr[i] + wi[i] * mi[i];
+                        const float Q = wr[i] * mi[i] - wi[i] * mr[i];
                         float ph, pl, qh, ql;
                         split2(P, ph, pl);
                         split2(Q, qh, ql);
@@ -300,10 +353,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         imh[i] = pack_bf16(-qh, ph);
                         iml[i] = pack_bf16(-ql, pl);
                     }
-                    *reinterpret_cast<uint4*>(bhi + sw128_off(r, c)) = make_uint4(reh[0], reh[1], reh[2], reh[3]);
-                    *reinterpret_cast<uint4*>(blo + sw128_off(r, c)) = make_uint4(rel[0], rel[1], rel[2], rel[3]);
-                    *reinterpret_cast<uint4*>(bhi + sw128_off(r + TC_BN, c)) = make_uint4(imh[0], imh[1], imh[2], imh[3]);
-                    *reinterpret_cast<uint4*>(blo + sw128_off(r + TC_BN, c)) = make_uint4(iml[0], iml[1], iml[2], iml[3]);
+                    const int rre = fq * 2 * TC_GN + r, rim = rre + TC_GN;
+                    *reinterpret_cast<uint4*>(bhi + sw128_off(rre, c)) = make_uint4(reh[0], reh[1], reh[2], reh[3]);
+                    *reinterpret_cast<uint4*>(blo + sw128_off(rre, c)) = make_uint4(rel[0], rel[1], rel[2], rel[3]);
+                    *reinterpret_cast<uint4*>(bhi + sw128_off(rim, c)) = make_uint4(imh[0], imh[1], imh[2], imh[3]);
+                    *reinterpret_cast<uint4*>(blo + sw128_off(rim, c)) = make_uint4(iml[0], iml[1], iml[2], iml[3]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(empty(s));
@@ -312,61 +366,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ---------------- epilogue (128 threads, TMEM lanes by warp % 4) ----------------
+        // lane quarter q4: 0 = Re f0, 1 = Im f0, 2 = Re f1, 3 = Im f1; lane = G' - n0
         const int q4 = warp & 3;
-        const int row_in_tile = q4 * 32 + lane;
         long long cg = 0;
         bool ok = true;
-        for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
-            const int f = job / (args.mt * args.nt);
-            const int rem = job % (args.mt * args.nt);
-            const int m0 = (rem / args.nt) * TC_BM, n0 = (rem % args.nt) * TC_BN;
-            const int g = m0 + row_in_tile;
-            double2* out = args.chi + (size_t)f * args.ng * args.ng + (size_t)g * args.ng;
-            for (int ch = 0; ch < nchunk; ++ch, ++cg) {
-                const int ab = (int)(cg & 1);
-                if (!(ok = mbar_wait(accf(ab), (uint32_t)((cg >> 1) & 1), err, 131))) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * 128);
+        double* chi = reinterpret_cast<double*>(args.chi);
+        for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x, ++cg) {
+            int w0, w1, fp, n0, m0, nown, mown;
+            job_tile(job, w0, w1, fp, n0, m0, nown, mown);
+            const int f = 2 * fp + (q4 >> 1), comp = q4 & 1;
+            const int gp = n0 + lane;
+            const bool live = f < args.nf && gp >= nown && gp < args.ng;
+            const int gmin = mown - m0;
+            double* out = chi + (((size_t)f * args.ng + m0) * args.ng + gp) * 2 + comp;
+            const size_t ldo = (size_t)args.ng * 2;
+            const int ab = (int)(cg & 1);
+            if (!(ok = mbar_wait(accf(ab), (uint32_t)((cg >> 1) & 1), err, 131))) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * 256);
+            const int gmax = min(TC_BN, args.ng - m0);   // columns [gmin, gmax) are this tile's
+#pragma unroll 1
+            for (int ch = 0; ch < TC_BN / 32; ++ch) {
+                uint32_t v[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                      "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                      "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(src + (uint32_t)(ch * 32)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (live) {
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    // columns [32 half, +32) hold Re, [64 + 32 half, +32) hold Im of G' = n0 + 32 half + j
-                    uint32_t r[32], s2[32];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-                          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-                          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                        : "r"(src + (uint32_t)(half * 32)));
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                        : "=r"(s2[0]), "=r"(s2[1]), "=r"(s2[2]), "=r"(s2[3]), "=r"(s2[4]), "=r"(s2[5]), "=r"(s2[6]),
-                          "=r"(s2[7]), "=r"(s2[8]), "=r"(s2[9]), "=r"(s2[10]), "=r"(s2[11]), "=r"(s2[12]),
-                          "=r"(s2[13]), "=r"(s2[14]), "=r"(s2[15]), "=r"(s2[16]), "=r"(s2[17]), "=r"(s2[18]),
-                          "=r"(s2[19]), "=r"(s2[20]), "=r"(s2[21]), "=r"(s2[22]), "=r"(s2[23]), "=r"(s2[24]),
-                          "=r"(s2[25]), "=r"(s2[26]), "=r"(s2[27]), "=r"(s2[28]), "=r"(s2[29]), "=r"(s2[30]),
-                          "=r"(s2[31])
-                        : "r"(src + (uint32_t)(64 + half * 32)));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (half == 1) {
-                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                        mbar_arrive(acce(ab));
-                    }
-                    if (g < args.ng) {
+                    for (int j = 0; j < 32; ++j)
+                        if (ch * 32 + j >= gmin && ch * 32 + j < gmax)
+                            atomicAdd(out + (size_t)(ch * 32 + j) * ldo, (double)__uint_as_float(v[j]));
+                }
+            }
+            {
+                constexpr int ch = TC_BN / 32;
+                uint32_t v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(src + (uint32_t)(ch * 32)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(acce(ab));
+                if (live) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int gp = n0 + half * 32 + j;
-                            if (gp < args.ng) {
-                                double2 o = out[gp];
-                                o.x += (double)__uint_as_float(r[j]);
-                                o.y += (double)__uint_as_float(s2[j]);
-                                out[gp] = o;
-                            }
-                        }
-                    }
+                    for (int j = 0; j < 16; ++j)
+                        if (ch * 32 + j >= gmin && ch * 32 + j < gmax)
+                            atomicAdd(out + (size_t)(ch * 32 + j) * ldo, (double)__uint_as_float(v[j]));
                 }
             }
         }
@@ -374,7 +430,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
 // hi/lo bf16 split of M (complex double [ng][ldm] from column col0, K columns) into
@@ -403,15 +459,16 @@ __global__ void k_split_bf16(const CI* __restrict__ M, long long ldm, long long 
     reinterpret_cast<__nv_bfloat162*>(lo)[t] = l2;
 }
 
-// complex float copy of the weights of this block: w32[f][b] = w[f][col0 + b], b < kpad (zero padded)
+// complex float copy of the weights of this block: w32[f][b] = w[f][col0 + b], b < kpad, for
+// f < nrow (rows f >= nf and columns b >= K are zero)
 __global__ void k_weights32(const double2* __restrict__ w, long long ldw, long long col0, long long K, int nf,
-                            long long kpad, float2* __restrict__ w32) {
+                            int nrow, long long kpad, float2* __restrict__ w32) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)nf * kpad) return;
+    if (t >= (long long)nrow * kpad) return;
     const int f = (int)(t / kpad);
     const long long b = t % kpad;
     float2 v = make_float2(0.f, 0.f);
-    if (b < K) {
+    if (f < nf && b < K) {
         const double2 d = w[(size_t)f * ldw + col0 + b];
         v = make_float2((float)d.x, (float)d.y);
     }
@@ -435,12 +492,12 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-static bool make_map(CUtensorMap* map, void* base, int ng, long long kp2) {
+static bool make_map(CUtensorMap* map, void* base, int ng, long long kp2, int rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)kp2, (cuuint64_t)ng};
     cuuint64_t strides[1] = {(cuuint64_t)kp2 * 2};
-    cuuint32_t box[2] = {TC_BK, 64};
+    cuuint32_t box[2] = {TC_BK, (cuuint32_t)rows};
     cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -470,23 +527,29 @@ cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, 
                                    int num_sms, cudaStream_t st) {
     const long long kp2 = tc_kp2(K);
     const long long kpad = kp2 / 2;
-    CUtensorMap mhi, mlo;
-    if (!make_map(&mhi, const_cast<void*>(hi), ng, kp2) || !make_map(&mlo, const_cast<void*>(lo), ng, kp2))
+    CUtensorMap mraw_hi, mraw_lo, mrow_hi, mrow_lo;
+    if (!make_map(&mraw_hi, const_cast<void*>(hi), ng, kp2, TC_BN) ||
+        !make_map(&mraw_lo, const_cast<void*>(lo), ng, kp2, TC_BN) ||
+        !make_map(&mrow_hi, const_cast<void*>(hi), ng, kp2, TC_GN) ||
+        !make_map(&mrow_lo, const_cast<void*>(lo), ng, kp2, TC_GN))
         return cudaErrorInvalidValue;
-    const long long nw = (long long)nf * kpad;
-    k_weights32<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(w, ldw, col0, K, nf, kpad, (float2*)w32);
+    const int nfp = (nf + 1) / 2;
+    const long long nw = (long long)2 * nfp * kpad;
+    k_weights32<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(w, ldw, col0, K, nf, 2 * nfp, kpad, (float2*)w32);
     TcArgs a;
     a.w32 = (const float2*)w32; a.K = K;
-    a.ng = ng; a.nf = nf;
-    a.mt = (ng + TC_BM - 1) / TC_BM;
-    a.nt = (ng + TC_BN - 1) / TC_BN;
+    a.ng = ng; a.nf = nf; a.nfp = nfp;
+    a.nblk = (ng + TC_GN - 1) / TC_GN;
+    a.mt = (ng + TC_BN - 1) / TC_BN;
     a.nst = (int)(kp2 / TC_BK);
+    a.nwin = (a.nst + TC_FLUSH_STAGES - 1) / TC_FLUSH_STAGES;
     a.chi = chi; a.err = err;
-    const int njobs = nf * a.mt * a.nt;
+    const long long njobs = (long long)a.nfp * a.nblk * a.mt * a.nwin;
+    if (njobs > 0x7fffffffLL) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_contract_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_TOTAL);
     if (e != cudaSuccess) return e;
-    const int grid = njobs < num_sms ? njobs : num_sms;
-    k_contract_bf16x3<<<grid, TC_THREADS, TC_SMEM_TOTAL, st>>>(mhi, mlo, a);
+    const int grid = njobs < num_sms ? (int)njobs : num_sms;
+    k_contract_bf16x3<<<grid, TC_THREADS, TC_SMEM_TOTAL, st>>>(mraw_hi, mraw_lo, mrow_hi, mrow_lo, a);
     return cudaGetLastError();
 }
 

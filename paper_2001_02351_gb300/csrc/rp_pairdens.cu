@@ -280,6 +280,170 @@ __global__ void __launch_bounds__(256) k_pair_yx(const C* __restrict__ T1, int n
     }
 }
 
+
+// ---- plane-wise pair transform: z and y on chip, one x plane per CTA ----
+//
+// k_pair_zy: CTA = one x plane of one k of the block and A = 128 / N2 empty bands, whose planes
+// stay in shared memory while the occupied bands stream through, one plane per step: the plane
+// of band o + 1 is fetched with coalesced 16-byte loads into registers while thread (a, y) forms
+// conj(u_a) u_o on its z line of band o, transforms it in registers (pruned to the sphere's z
+// values) and parks it in a double-buffered tile.  Then one thread per (a, sphere z) column
+// transforms along y in registers and writes the sphere's y values to T2[pair][x][iy][iz]; the
+// warps without a column go straight on to the next band.  One barrier per occupied band.
+// k_pair_x: the x sum on the sphere points, M[g][col0 + pair] = scale * sum_x Ex[gx][x] T2[...],
+// one thread per sphere point with all of the CTA's pairs in flight.
+template <typename C, int N3, int N2>
+__global__ void __launch_bounds__(128) k_pair_zy(const C* __restrict__ u, int nband, int nocc, int nemp, int N1,
+                                                 const int* __restrict__ zmap, int nz,
+                                                 const int* __restrict__ ymap, int ny,
+                                                 const C* __restrict__ twz, const C* __restrict__ twy,
+                                                 C* __restrict__ T2) {
+    constexpr int A = 128 / N2;
+    constexpr int LD = N3 + 1;
+    constexpr int PER = 16 / sizeof(C);                 // complex values per 16-byte load
+    constexpr int NV = N2 * N3 / (128 * PER);           // 16-byte loads per thread per plane
+    static_assert(NV * 128 * PER == N2 * N3, "plane must split evenly into 16-byte loads");
+    extern __shared__ __align__(16) unsigned char sm_zy[];
+    C* sa = reinterpret_cast<C*>(sm_zy);          // [A][N2][LD]
+    C* so = sa + A * N2 * LD;                     // [2][N2][LD]
+    C* tz = so + 2 * N2 * LD;                     // [2][A][N2][nz]
+    const int x = blockIdx.x, a0 = blockIdx.y * A, kl = blockIdx.z;
+    const int na = min(A, nemp - a0);
+    const size_t plane = (size_t)N2 * N3;
+    const C* uk = u + (size_t)kl * nband * N1 * plane + x * plane;
+    for (int q = 0; q < na; ++q) {
+        const C* ua = uk + (size_t)(nocc + a0 + q) * N1 * plane;
+        for (int e = threadIdx.x; e < N2 * N3; e += 128) sa[(q * N2 + e / N3) * LD + e % N3] = ua[e];
+    }
+    // occupied plane 0
+    for (int e = threadIdx.x; e < N2 * N3; e += 128) so[(e / N3) * LD + e % N3] = uk[e];
+    __syncthreads();
+    const int y = threadIdx.x % N2, ai = threadIdx.x / N2;
+    const int nyz = ny * nz;
+    for (int o = 0; o < nocc; ++o) {
+        const C* sb = so + (o & 1) * N2 * LD;
+        C* tb = tz + (o & 1) * A * N2 * nz;
+        // prefetch plane o + 1 (16-byte loads, consecutive threads on consecutive addresses)
+        float4 pf[NV];
+        const bool more = o + 1 < nocc;
+        if (more) {
+            const float4* src = reinterpret_cast<const float4*>(uk + (size_t)(o + 1) * N1 * plane);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) pf[i] = __ldg(src + i * 128 + threadIdx.x);
+        }
+        if (ai < na) {
+            C v[N3];
+#pragma unroll
+            for (int z = 0; z < N3; ++z) v[z] = c_conjmul(sa[(ai * N2 + y) * LD + z], sb[y * LD + z]);
+            LineFFT<C, N3, 1>::run(v, twz);
+#pragma unroll
+            for (int z = 0; z < N3; ++z) {
+                const int iz = zmap[z];
+                if (iz >= 0) tb[(ai * N2 + y) * nz + iz] = v[z];
+            }
+        }
+        if (more) {
+            C* dst = so + ((o + 1) & 1) * N2 * LD;
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const C* c = reinterpret_cast<const C*>(&pf[i]);
+                const int e0 = (i * 128 + threadIdx.x) * PER;
+#pragma unroll
+                for (int j = 0; j < PER; ++j) dst[((e0 + j) / N3) * LD + (e0 + j) % N3] = c[j];
+            }
+        }
+        __syncthreads();
+        for (int col = threadIdx.x; col < na * nz; col += 128) {
+            const int q = col / nz, iz = col % nz;
+            C v[N2];
+#pragma unroll
+            for (int yy = 0; yy < N2; ++yy) v[yy] = tb[(q * N2 + yy) * nz + iz];
+            LineFFT<C, N2, 1>::run(v, twy);
+            const size_t pair = ((size_t)kl * nemp + a0 + q) * nocc + o;
+            C* dst = T2 + (pair * N1 + x) * nyz + iz;
+#pragma unroll
+            for (int yy = 0; yy < N2; ++yy) {
+                const int iy = ymap[yy];
+                if (iy >= 0) dst[iy * nz] = v[yy];
+            }
+        }
+    }
+}
+
+// pairs per read-out CTA; a thread takes two of them for one sphere point
+#define PX_PB 4
+
+template <typename C, typename CO>
+__global__ void __launch_bounds__(256) k_pair_x(const C* __restrict__ T2, long long npair, int N1, int nyz, int nz,
+                                                const C* __restrict__ Ex, int nx, const int* __restrict__ gpos, int ng,
+                                                typename Cx<C>::R scale, CO* __restrict__ M, long long ldm,
+                                                long long col0) {
+    using R = typename Cx<C>::R;
+    extern __shared__ __align__(16) unsigned char sm_x[];
+    C* ex = reinterpret_cast<C*>(sm_x);           // [nx][N1]
+    C* out = ex + nx * N1;                        // [ng][PX_PB]
+    const long long p0 = (long long)blockIdx.x * PX_PB;
+    const int np = (int)min((long long)PX_PB, npair - p0);
+    const size_t per = (size_t)N1 * nyz;
+    for (int e = threadIdx.x; e < nx * N1; e += 256) ex[e] = Ex[e];
+    __syncthreads();
+    // consecutive threads take consecutive sphere points of the same pairs: their loads fall in
+    // one nyz-long row of T2 per x
+    for (int e = threadIdx.x; e < ng * (PX_PB / 2); e += 256) {
+        const int g = e % ng, h = e / ng;
+        const int j0 = 2 * h;
+        if (j0 >= np) continue;
+        const bool two = j0 + 1 < np;
+        const int gx = gpos[3 * g], gyz = gpos[3 * g + 1] * nz + gpos[3 * g + 2];
+        const C* s0 = T2 + (size_t)(p0 + j0) * per + gyz;
+        const C* s1 = two ? s0 + per : s0;
+        const C* w = ex + gx * N1;
+        R r0 = 0, i0 = 0, r1 = 0, i1 = 0;
+#pragma unroll 4
+        for (int xx = 0; xx < N1; ++xx) {
+            const C c = w[xx];
+            const C v0 = __ldg(s0 + (size_t)xx * nyz), v1 = __ldg(s1 + (size_t)xx * nyz);
+            r0 += c.x * v0.x - c.y * v0.y;
+            i0 += c.x * v0.y + c.y * v0.x;
+            r1 += c.x * v1.x - c.y * v1.y;
+            i1 += c.x * v1.y + c.y * v1.x;
+        }
+        out[g * PX_PB + j0] = Cx<C>::mk(r0 * scale, i0 * scale);
+        out[g * PX_PB + j0 + 1] = Cx<C>::mk(r1 * scale, i1 * scale);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ng * np; e += 256) {
+        const int g = e / np, j = e % np;
+        const C v = out[g * PX_PB + j];
+        M[(size_t)g * ldm + col0 + p0 + j] = CT<CO>::make((typename CT<CO>::R)v.x, (typename CT<CO>::R)v.y);
+    }
+}
+
+template <typename C, int N>
+static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int N1, const int* zmap, int nz,
+                        const int* ymap, int ny, const C* twz, const C* twy, C* T2, cudaStream_t st) {
+    constexpr int A = 128 / N;
+    const size_t smem = sizeof(C) * ((size_t)(A + 2) * N * (N + 1) + (size_t)2 * A * N * nz);
+    if (smem > 200 * 1024) return false;
+    if (cudaFuncSetAttribute(k_pair_zy<C, N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return false;
+    dim3 grid(N1, (nemp + A - 1) / A, nkb);
+    k_pair_zy<C, N, N><<<grid, 128, smem, st>>>(u, nband, nocc, nemp, N1, zmap, nz, ymap, ny, twz, twy, T2);
+    return true;
+}
+
+// plane-wise path for square planes N2 == N3 of a supported length
+template <typename C>
+static bool launch_zy(int n2, int n3, const C* u, int nkb, int nband, int nocc, int nemp, int N1, const int* zmap,
+                      int nz, const int* ymap, int ny, const C* twz, const C* twy, C* T2, cudaStream_t st) {
+    if (n2 != n3) return false;
+    switch (n3) {
+        case 16: return launch_zy_n<C, 16>(u, nkb, nband, nocc, nemp, N1, zmap, nz, ymap, ny, twz, twy, T2, st);
+        case 32: return launch_zy_n<C, 32>(u, nkb, nband, nocc, nemp, N1, zmap, nz, ymap, ny, twz, twy, T2, st);
+        default: return false;
+    }
+}
+
 template <typename C, int N3>
 static void launch_z(const C* u, int nkb, int nband, int nocc, int a0, int nab, int nlines, const int* zmap, int nz,
                      const C* tw, C* T1, cudaStream_t st) {
@@ -389,6 +553,23 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
     const int ny = P.nset[1], nz = P.nset[2];
     const long long nr = c->nr;
     const int bs = 256;
+    // plane-wise path: z and y transforms on chip, then the x sum on the sphere points
+    {
+        const long long npair = (long long)nkb * c->nemp * c->nocc;
+        const size_t t2 = (size_t)npair * N1 * ny * nz * sizeof(C);
+        const size_t xsm = ((size_t)P.nset[0] * N1 + (size_t)P.ng * PX_PB) * sizeof(C);
+        if (P.fused && twz && twy && xsm <= 200 * 1024 && t2 <= (size_t)16 << 30 && ensure(c, c->s_t2, t2) == RP_OK &&
+            launch_zy<C>(N2, N3, (const C*)c->s_u.p, nkb, c->nband, c->nocc, c->nemp, N1, (const int*)P.d_zmap.p,
+                         nz, (const int*)P.d_ymap.p, ny, twz, twy, (C*)c->s_t2.p, st)) {
+            cudaError_t e = cudaFuncSetAttribute(k_pair_x<C, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
+            if (e != cudaSuccess) return e;
+            k_pair_x<C, CO><<<(unsigned)((npair + PX_PB - 1) / PX_PB), 256, xsm, st>>>(
+                (const C*)c->s_t2.p, npair, N1, ny * nz, nz, efwd[0], P.nset[0], (const int*)P.d_gpos.p, P.ng,
+                (typename CT<C>::R)(1.0 / (double)nr), M, ldm, col0);
+            *nlaunch += 2;
+            return cudaGetLastError();
+        }
+    }
     // fused path over the whole k block when its partial transforms fit the scratch budget
     {
         const long long npair = (long long)nkb * c->nemp * c->nocc;
