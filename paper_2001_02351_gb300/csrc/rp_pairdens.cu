@@ -120,6 +120,87 @@ __global__ void k_sphere_readout(const C* __restrict__ T2, const C* __restrict__
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Gather + inverse transform by line FFTs, one CTA per band (grid N^3, Miller box B^3, B <= N).
+// The box is scattered into the first B planes of T[x][m2][m3]; the x transform then runs in
+// place, each thread on its own (m2, m3) column of every plane (it reads the column's B entries
+// into registers before it writes the N outputs), so no other thread's data is touched.  The y
+// and z transforms follow for XG = 256 / N planes at a time through U[x][y][m3], and the z lines
+// go straight from registers to u.  Frequency n of a line holds Miller value n (n <= lb) or
+// n - N (n >= N - lb); with B <= N the two ranges do not meet.
+template <typename C, int N>
+__global__ void __launch_bounds__(256) k_gather_fft(const double2* __restrict__ coef, const int* __restrict__ miller,
+                                                    const int* __restrict__ npw, int npw_max, int nband, int nocc,
+                                                    const int* __restrict__ kp, const int* __restrict__ g0, int k0,
+                                                    int lb, const C* __restrict__ tw, C* __restrict__ u) {
+    using R = typename CT<C>::R;
+    constexpr int XG = 256 / N;
+    const int B = 2 * lb + 1, BB = B * B;
+    extern __shared__ __align__(16) unsigned char sm_gf[];
+    C* T = reinterpret_cast<C*>(sm_gf);      // [N][B][B]; its first B planes are the box
+    C* U = T + (size_t)N * BB;               // [XG][N][B]
+    const int band = blockIdx.x;             // kl * nband + s
+    const int kl = band / nband, s = band % nband;
+    const int k = k0 + kl;
+    const int ks = (s < nocc) ? k : kp[k];
+    for (int e = threadIdx.x; e < B * BB; e += 256) T[e] = CT<C>::make(0, 0);
+    __syncthreads();
+    int sh0 = 0, sh1 = 0, sh2 = 0;
+    if (s >= nocc) { sh0 = g0[3 * k]; sh1 = g0[3 * k + 1]; sh2 = g0[3 * k + 2]; }
+    for (int p = threadIdx.x; p < npw[ks]; p += 256) {
+        const int* m = miller + ((size_t)ks * npw_max + p) * 3;
+        const double2 v = coef[((size_t)ks * nband + s) * npw_max + p];
+        T[((m[0] - sh0 + lb) * B + (m[1] - sh1 + lb)) * B + (m[2] - sh2 + lb)] = CT<C>::make((R)v.x, (R)v.y);
+    }
+    __syncthreads();
+    // box index of the Miller value at frequency n, or -1
+    auto slot = [&](int n) { return n <= lb ? n + lb : (n >= N - lb ? n - N + lb : -1); };
+    // x: m1 -> x on every (m2, m3) column, in place
+    for (int l = threadIdx.x; l < BB; l += 256) {
+        C v[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            const int m = slot(n);
+            v[n] = m >= 0 ? T[m * BB + l] : CT<C>::make(0, 0);
+        }
+        LineFFT<C, N, 1>::run(v, tw);
+#pragma unroll
+        for (int x = 0; x < N; ++x) T[x * BB + l] = v[x];
+    }
+    C* dst = u + (size_t)band * N * N * N;
+    for (int x0 = 0; x0 < N; x0 += XG) {
+        __syncthreads();
+        // y: m2 -> y on the (x, m3) lines of XG planes
+        for (int l = threadIdx.x; l < XG * B; l += 256) {
+            const int xl = l / B, m3 = l % B;
+            const C* src = T + (size_t)(x0 + xl) * BB + m3;
+            C v[N];
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                const int m = slot(n);
+                v[n] = m >= 0 ? src[m * B] : CT<C>::make(0, 0);
+            }
+            LineFFT<C, N, 1>::run(v, tw);
+#pragma unroll
+            for (int y = 0; y < N; ++y) U[(xl * N + y) * B + m3] = v[y];
+        }
+        __syncthreads();
+        // z: m3 -> z on the (x, y) lines, written to the grid
+        for (int l = threadIdx.x; l < XG * N; l += 256) {
+            const C* src = U + (size_t)l * B;
+            C v[N];
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                const int m = slot(n);
+                v[n] = m >= 0 ? src[m] : CT<C>::make(0, 0);
+            }
+            LineFFT<C, N, 1>::run(v, tw);
+            C* d = dst + ((size_t)x0 * N + l) * N;
+#pragma unroll
+            for (int z = 0; z < N; ++z) d[z] = v[z];
+        }
+    }
+}
+
 // Gather + inverse transform of one band per CTA: the Miller box of the band (shifted by -G0 for
 // the empty bands at k' = k + q - G0) is built in shared memory, then every x plane of the
 // real-space grid is formed by three small sums (m1 -> x, m2 -> y, m3 -> z) and written once.
@@ -497,11 +578,33 @@ static bool fused_yx(int n, const C* T1, int npair, int N1, int nz, const int* y
 }
 
 
+template <typename C, int N>
+static bool gather_fft_n(rp_ctx* c, int k0, long long nbands, const C* tw, cudaStream_t st) {
+    const int B = 2 * c->lb + 1;
+    const size_t smem = sizeof(C) * ((size_t)N * B * B + (size_t)256 * B);
+    if (B > N || smem > 200 * 1024) return false;
+    if (ensure(c, c->s_u, (size_t)nbands * c->nr * sizeof(C))) return false;
+    if (cudaFuncSetAttribute(k_gather_fft<C, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return false;
+    k_gather_fft<C, N><<<(unsigned)nbands, 256, smem, st>>>(
+        (const double2*)c->d_coef.p, (const int*)c->d_miller.p, (const int*)c->d_npw.p, c->npw_max, c->nband, c->nocc,
+        (const int*)c->plan.d_kp.p, (const int*)c->plan.d_g0.p, k0, c->lb, tw, (C*)c->s_u.p);
+    return true;
+}
+
 template <typename C>
-static cudaError_t gather_inverse_t(rp_ctx* c, int k0, int nkb, const C* const einv[3], cudaStream_t st) {
+static cudaError_t gather_inverse_t(rp_ctx* c, int k0, int nkb, const C* const einv[3], const C* tw,
+                                    cudaStream_t st) {
     const int B = 2 * c->lb + 1;
     const int N1 = c->fft[0], N2 = c->fft[1], N3 = c->fft[2];
     const long long nbands = (long long)nkb * c->nband;
+    // line-FFT path on cubic grids of a supported length
+    if (tw && N1 == N2 && N2 == N3) {
+        bool done = false;
+        if (N1 == 16) done = gather_fft_n<C, 16>(c, k0, nbands, tw, st);
+        else if (N1 == 32) done = gather_fft_n<C, 32>(c, k0, nbands, tw, st);
+        if (done) return cudaGetLastError();
+    }
     {   // one CTA per band with the Miller box in shared memory
         const size_t smem = sizeof(C) * ((size_t)B * B * B + (size_t)B * B + (size_t)N2 * B);
         if (smem <= 200 * 1024) {
@@ -636,11 +739,11 @@ cudaError_t launch_gather_inverse(rp_ctx* c, int k0, int nkb, bool fp32, cudaStr
     if (fp32) {
         const float2* e[3] = {(const float2*)c->d_einv32[0].p, (const float2*)c->d_einv32[1].p,
                               (const float2*)c->d_einv32[2].p};
-        return gather_inverse_t<float2>(c, k0, nkb, e, st);
+        return gather_inverse_t<float2>(c, k0, nkb, e, (const float2*)c->plan.d_tw32[0].p, st);
     }
     const double2* e[3] = {(const double2*)c->d_einv[0].p, (const double2*)c->d_einv[1].p,
                            (const double2*)c->d_einv[2].p};
-    return gather_inverse_t<double2>(c, k0, nkb, e, st);
+    return gather_inverse_t<double2>(c, k0, nkb, e, (const double2*)c->plan.d_tw[0].p, st);
 }
 
 cudaError_t launch_pair_forward(rp_ctx* c, int nkb, double2* M, long long ldm, long long col0, cudaStream_t st,
