@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(256) k_pair_yx(const C* __restrict__ T1, int n
 // k_pair_x: the x sum on the sphere points, M[g][col0 + pair] = scale * sum_x Ex[gx][x] T2[...],
 // one thread per sphere point with all of the CTA's pairs in flight.
 template <typename C, int N3, int N2>
-__global__ void __launch_bounds__(128) k_pair_zy(const C* __restrict__ u, int nband, int nocc, int nemp, int N1,
+__global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const C* __restrict__ u, int nband, int nocc, int nemp, int N1,
                                                  const int* __restrict__ zmap, int nz,
                                                  const int* __restrict__ ymap, int ny,
                                                  const C* __restrict__ twz, const C* __restrict__ twy,

@@ -36,6 +36,7 @@ struct TT<double> {
     static __device__ __forceinline__ double hyp(double a, double b) { return hypot(a, b); }
     static __device__ __forceinline__ C clog(C a) { return make_double2(log(hypot(a.x, a.y)), atan2(a.y, a.x)); }
     static __device__ __forceinline__ double lg(double a) { return log(a); }
+    static __device__ __forceinline__ double rsq(double a) { return rsqrt(a); }
 };
 template <>
 struct TT<float> {
@@ -44,6 +45,7 @@ struct TT<float> {
     static __device__ __forceinline__ float hyp(float a, float b) { return hypotf(a, b); }
     static __device__ __forceinline__ C clog(C a) { return make_float2(logf(hypotf(a.x, a.y)), atan2f(a.y, a.x)); }
     static __device__ __forceinline__ float lg(float a) { return logf(a); }
+    static __device__ __forceinline__ float rsq(float a) { return rsqrtf(a); }
 };
 
 template <typename C>
@@ -121,6 +123,52 @@ __device__ __forceinline__ typename TT<R>::C dd_series(const R (&t)[5], int m, t
         for (int q = 0; q < n - 3; ++q) p = tmul(p, w);
     }
     return tmul(S, p);
+}
+
+// Fourth divided difference over the five nodes c + {-s/2, t1, t2, t3, s/2} by the Taylor series
+// about the centre c:  y^-1 sum_k b_{4+k} h_k(t/r) u^k,  y = z - c, r = |y|, u = conj(y)/r,
+// b_q = 6 / (q (q-1) (q-2) (q-3)).  With every scaled node within rho = s / (2 r) of zero,
+// |h_k| <= C(k+4, 4) rho^k, so |b_{4+k} h_k u^k| <= rho^k / 4 while the sum is at least
+// (1 - 2 rho) / (4 (1 - rho)): after K terms the remainder is below 2 rho^(K+1) of the sum for
+// rho <= 1/4, and K is the smallest count that puts it under half the unit roundoff.
+template <typename R>
+__device__ __forceinline__ typename TT<R>::C dd5_series(R t1, R t2, R t3, R s, typename TT<R>::C y) {
+    using C = typename TT<R>::C;
+    constexpr int KM = sizeof(R) == 8 ? 28 : 13;            // K at rho = 1/4
+    const R rinv = TT<R>::rsq(y.x * y.x + y.y * y.y);
+    const R rho = (R)0.5 * s * rinv;
+    int K = 0;
+    if (rho > (R)0) {
+        const R target = sizeof(R) == 8 ? (R)-38.5 : (R)-17.5;   // log of half the roundoff, with margin
+        K = (int)ceil(target / TT<R>::lg(rho));
+        K = K < KM ? K : KM;
+    }
+    const R nd[5] = {-rho, t1 * rinv, t2 * rinv, t3 * rinv, rho};
+    R e1 = 0, e2 = 0, e3 = 0, e4 = 0, e5 = 0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        e5 += nd[v] * e4;
+        e4 += nd[v] * e3;
+        e3 += nd[v] * e2;
+        e2 += nd[v] * e1;
+        e1 += nd[v];
+    }
+    const C u = TT<R>::mk(y.x * rinv, -y.y * rinv);
+    R h1 = 0, h2 = 0, h3 = 0, h4 = 0, hk = 1;
+    C uk = TT<R>::mk(1, 0);
+    C S = TT<R>::mk((R)0.25, 0);
+#pragma unroll
+    for (int k = 1; k <= KM; ++k) {
+        if (k > K) break;
+        const R hn = e1 * hk - e2 * h1 + e3 * h2 - e4 * h3 + e5 * h4;
+        h4 = h3; h3 = h2; h2 = h1; h1 = hk; hk = hn;
+        uk = tmul(uk, u);
+        const R bh = (R)(6.0 / ((double)(k + 4) * (k + 3) * (k + 2) * (k + 1))) * hk;
+        S.x += bh * uk.x;
+        S.y += bh * uk.y;
+    }
+    const C p = tmul(S, u);
+    return TT<R>::mk(p.x * rinv, p.y * rinv);
 }
 
 // 6 / (m (m-1) (m-2) (m-3)) for m = 0 .. 63 (entries below 4 unused)
@@ -275,14 +323,9 @@ __device__ __noinline__ double2 dd_fp64_entry(const double* __restrict__ E, int 
     tetra_nodes(E, nband, nocc, a, o, kp, tets, code, da, dr, x);
     const double c = 0.5 * (x[0] + x[4]);
     const double2 y = make_double2(z.x - c, z.y);
-    const double Rr = hypot(y.x, y.y);
     const double spread = x[4] - x[0];
-    if (spread <= TT_TAU * Rr) {
-        double t[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) t[i] = x[i] - c;
-        return dd_series<double>(t, 5, y, nterms<double>(0.5 * spread / Rr));
-    }
+    if (spread * spread <= TT_TAU * TT_TAU * (y.x * y.x + y.y * y.y))
+        return dd5_series<double>(x[1] - c, x[2] - c, x[3] - c, spread, y);
     bool unused = false;
     return dd5_table<double>(x, z, &unused);
 }
@@ -420,9 +463,8 @@ __global__ void __launch_bounds__(128) k_tetra_weights(const double* __restrict_
                     continue;
                 }
                 const C y = TT<R>::mk(zr.x - ct, zr.y);
-                const R Rr = TT<R>::hyp(y.x, y.y);
-                if (spread <= (R)TT_TAU * Rr) {
-                    sacc = tadd(sacc, dd_series<R>(tr, 5, y, nterms<R>((R)0.5 * spread / Rr)));
+                if (spread * spread <= (R)(TT_TAU * TT_TAU) * (y.x * y.x + y.y * y.y)) {
+                    sacc = tadd(sacc, dd5_series<R>(tr[1], tr[2], tr[3], spread, y));
                 } else {
                     R xr[5];
 #pragma unroll
