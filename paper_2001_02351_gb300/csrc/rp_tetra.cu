@@ -336,6 +336,26 @@ __device__ __noinline__ typename TT<R>::C dd_table_entry(const R (&x)[5], typena
     return dd5_table<R>(x, z, &unused);
 }
 
+// nodes of entry `code` relative to the pair's transition energy d0, as the FP32 pass forms them:
+// centre ct, offsets tr (outer nodes at -+ spread / 2)
+__device__ __forceinline__ void fp32_nodes(const double (&x)[5], double d0, float& ct, float (&tr)[5]) {
+    const double cd = 0.5 * (x[0] + x[4]);
+    const float spread = (float)(x[4] - x[0]);
+    tr[0] = -0.5f * spread;
+    tr[1] = (float)(x[1] - cd);
+    tr[2] = (float)(x[2] - cd);
+    tr[3] = (float)(x[3] - cd);
+    tr[4] = 0.5f * spread;
+    ct = (float)(cd - d0);
+}
+
+// item of the deferred work list: pair t, frequency f, tetrahedron-vertex entry s, pole side,
+// kind (0: near-degenerate set, evaluated in FP64; 1: wide set of the FP32 pass, full table in FP32)
+__device__ __forceinline__ unsigned long long tetra_item(long long t, int f, int s, int side, int kind) {
+    return ((unsigned long long)t << 32) | ((unsigned long long)f << 16) | ((unsigned long long)s << 8) |
+           ((unsigned long long)kind << 1) | (unsigned long long)side;
+}
+
 // Append a (pair, frequency, tetrahedron-vertex, pole) item to the FP64 work list; when the list
 // is full, evaluate it here instead (slower, same result).
 template <typename C>
@@ -346,8 +366,7 @@ __device__ __forceinline__ void defer_or_eval(unsigned long long* queue, unsigne
                                               int code, double da, double dr, double2 zd) {
     const unsigned long long slot = atomicAdd(qcount, 1ULL);
     if (slot < qcap) {
-        queue[slot] = ((unsigned long long)t << 32) | ((unsigned long long)f << 16) | ((unsigned long long)s << 8) |
-                      (unsigned long long)side;
+        queue[slot] = tetra_item(t, f, s, side, 0);
         return;
     }
     const double2 r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, code, da, dr, zd);
@@ -355,7 +374,7 @@ __device__ __forceinline__ void defer_or_eval(unsigned long long* queue, unsigne
     sacc.y += r.y;
 }
 
-// FP64 pass over the deferred items: one item per thread, result added to the weight
+// Pass over the deferred items: one item per thread, result added to the weight
 __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ E, const double* __restrict__ Tw,
                                                      int nband, int nocc, int nemp, int nk,
                                                      const int* __restrict__ kp, const int* __restrict__ tets,
@@ -370,6 +389,7 @@ __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ 
     const unsigned long long item = queue[i];
     const long long t = (long long)(item >> 32);
     const int f = (int)((item >> 16) & 0xFFFF), s = (int)((item >> 8) & 0xFF), side = (int)(item & 1);
+    const int kind = (int)((item >> 1) & 1);
     const long long K = (long long)nk * nemp * nocc;
     const int o = (int)(t % nocc);
     const int a = (int)((t / nocc) % nemp);
@@ -383,7 +403,20 @@ __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ 
     else
         zd = side == 0 ? make_double2(0.0, wv + delta)
                        : make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
-    const double2 r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, zd);
+    double2 r;
+    if (kind == 0) {
+        r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, zd);
+    } else {
+        double x[5];
+        tetra_nodes(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, x);
+        const double d0 = E[(size_t)kp[k] * nband + nocc + a] - E[(size_t)k * nband + o];
+        float ct, tr[5], xr[5];
+        fp32_nodes(x, d0, ct, tr);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) xr[j] = ct + tr[j];
+        const float2 rf = dd_table_entry<float>(xr, make_float2((float)(zd.x - d0), (float)zd.y));
+        r = make_double2((double)rf.x, (double)rf.y);
+    }
     double* dst = reinterpret_cast<double*>(wout + (size_t)f * K + t);
     atomicAdd(dst, r.x * pref / 6.0);
     atomicAdd(dst + 1, r.y * pref / 6.0);
@@ -466,6 +499,15 @@ __global__ void __launch_bounds__(128) k_tetra_weights(const double* __restrict_
                 if (spread * spread <= (R)(TT_TAU * TT_TAU) * (y.x * y.x + y.y * y.y)) {
                     sacc = tadd(sacc, dd5_series<R>(tr[1], tr[2], tr[3], spread, y));
                 } else {
+                    // a wide set: in the FP32 pass it goes to the work list (evaluated there with
+                    // the full table, so that the warps here stay on the series path)
+                    if (sizeof(R) == 4) {
+                        const unsigned long long slot = atomicAdd(qcount, 1ULL);
+                        if (slot < qcap) {
+                            queue[slot] = tetra_item(t, f, s, side, 1);
+                            continue;
+                        }
+                    }
                     R xr[5];
 #pragma unroll
                     for (int i = 0; i < 5; ++i) xr[i] = ct + tr[i];
