@@ -81,78 +81,33 @@ __device__ __forceinline__ int nterms(R rho) {
     return k > TT_KMAX ? TT_KMAX : k;
 }
 
-// Divided difference of order n over the m = n+1 centred nodes t (t = x - c) by the Taylor
-// series about c:  y^(3-n) sum_k b_{n+k} h_k(t) y^-k,  y = z - c.  With r = |y| the sum is
-// taken as sum_k b_{n+k} h_k(t/r) (conj(y)/r)^k, so every power stays on the unit circle.
-// The complete homogeneous polynomials h_k come from the recurrence
-// h_k = e1 h_{k-1} - e2 h_{k-2} + ... with the elementary symmetric polynomials e_j of the
-// scaled nodes, so no array is needed.
-template <typename R>
-__device__ __forceinline__ typename TT<R>::C dd_series(const R (&t)[5], int m, typename TT<R>::C y, int K) {
-    using C = typename TT<R>::C;
-    const int n = m - 1;
-    const R r = TT<R>::hyp(y.x, y.y);
-    const R rinv = (R)1 / r;
-    R e[6] = {1, 0, 0, 0, 0, 0};
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        if (v < m) {
-            const R tv = t[v] * rinv;
-#pragma unroll
-            for (int j = 5; j >= 1; --j) e[j] += tv * e[j - 1];
-        }
-    }
-    const C L = (n <= 3) ? TT<R>::clog(y) : TT<R>::mk(0, 0);
-    const C u = TT<R>::mk(y.x * rinv, -y.y * rinv);     // conj(y)/r, |u| = 1
-    R h1 = 0, h2 = 0, h3 = 0, h4 = 0;                    // h_{k-2} .. h_{k-5}
-    R hk = 1;                                            // h_{k-1}
-    C uk = TT<R>::mk(1, 0);
-    C S = bcoef<R>(n, L);
-    for (int k = 1; k <= K; ++k) {
-        const R hn = e[1] * hk - e[2] * h1 + e[3] * h2 - e[4] * h3 + e[5] * h4;
-        h4 = h3; h3 = h2; h2 = h1; h1 = hk; hk = hn;
-        uk = tmul(uk, u);
-        S = tadd(S, tscale(tmul(bcoef<R>(n + k, L), uk), hk));
-    }
-    // times y^(3-n)
-    C p = TT<R>::mk(1, 0);
-    if (n <= 3) {
-        for (int q = 0; q < 3 - n; ++q) p = tmul(p, y);
-    } else {
-        const C w = tinv(y);
-        for (int q = 0; q < n - 3; ++q) p = tmul(p, w);
-    }
-    return tmul(S, p);
-}
-
-// Fourth divided difference over the five nodes c + {-s/2, t1, t2, t3, s/2} by the Taylor series
-// about the centre c:  y^-1 sum_k b_{4+k} h_k(t/r) u^k,  y = z - c, r = |y|, u = conj(y)/r,
-// b_q = 6 / (q (q-1) (q-2) (q-3)).  With every scaled node within rho = s / (2 r) of zero,
+// Fourth divided difference over the five nodes c + t_v (t_0 = -s/2, t_4 = s/2, |t_v| <= s/2) by
+// the Taylor series about the centre c:  y^-1 sum_k b_{4+k} h_k(t/r) u^k,  y = z - c, r = |y|,
+// u = conj(y)/r, b_q = 6 / (q (q-1) (q-2) (q-3)).  The complete homogeneous polynomials h_k of the
+// scaled nodes follow from their elementary symmetric polynomials, e_j(t/r) = e_j(t) r^-j, passed
+// in unscaled (they do not depend on z).  With every scaled node within rho = s / (2 r) of zero,
 // |h_k| <= C(k+4, 4) rho^k, so |b_{4+k} h_k u^k| <= rho^k / 4 while the sum is at least
 // (1 - 2 rho) / (4 (1 - rho)): after K terms the remainder is below 2 rho^(K+1) of the sum for
-// rho <= 1/4, and K is the smallest count that puts it under half the unit roundoff.
+// rho <= 1/4, and K is the smallest count that puts it under half the unit roundoff.  In FP32 the
+// count is made uniform over the converged lanes of the warp (the largest of theirs).
 template <typename R>
-__device__ __forceinline__ typename TT<R>::C dd5_series(R t1, R t2, R t3, R s, typename TT<R>::C y) {
+__device__ __forceinline__ typename TT<R>::C dd5_series(const R (&e)[5], R s, typename TT<R>::C y, R r2) {
     using C = typename TT<R>::C;
     constexpr int KM = sizeof(R) == 8 ? 28 : 13;            // K at rho = 1/4
-    const R rinv = TT<R>::rsq(y.x * y.x + y.y * y.y);
+    const R rinv = TT<R>::rsq(r2);
     const R rho = (R)0.5 * s * rinv;
     int K = 0;
-    if (rho > (R)0) {
-        const R target = sizeof(R) == 8 ? (R)-38.5 : (R)-17.5;   // log of half the roundoff, with margin
-        K = (int)ceil(target / TT<R>::lg(rho));
+    if constexpr (sizeof(R) == 4) {
+        if (rho > 0.f) K = (int)ceilf(__fdividef(-25.25f, __log2f(rho)));   // log2 of half the roundoff
+        K = K < KM ? K : KM;
+        K = __reduce_max_sync(__activemask(), K);
+    } else {
+        if (rho > 0.0) K = (int)ceil(-38.5 / log(rho));
         K = K < KM ? K : KM;
     }
-    const R nd[5] = {-rho, t1 * rinv, t2 * rinv, t3 * rinv, rho};
-    R e1 = 0, e2 = 0, e3 = 0, e4 = 0, e5 = 0;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        e5 += nd[v] * e4;
-        e4 += nd[v] * e3;
-        e3 += nd[v] * e2;
-        e2 += nd[v] * e1;
-        e1 += nd[v];
-    }
+    const R r_2 = rinv * rinv;
+    const R e1 = e[0] * rinv, e2 = e[1] * r_2, e3 = e[2] * r_2 * rinv, e4 = e[3] * r_2 * r_2,
+            e5 = e[4] * r_2 * r_2 * rinv;
     const C u = TT<R>::mk(y.x * rinv, -y.y * rinv);
     R h1 = 0, h2 = 0, h3 = 0, h4 = 0, hk = 1;
     C uk = TT<R>::mk(1, 0);
@@ -169,6 +124,20 @@ __device__ __forceinline__ typename TT<R>::C dd5_series(R t1, R t2, R t3, R s, t
     }
     const C p = tmul(S, u);
     return TT<R>::mk(p.x * rinv, p.y * rinv);
+}
+
+// elementary symmetric polynomials e_1 .. e_5 of five values
+template <typename R>
+__device__ __forceinline__ void esym5(const R (&t)[5], R (&e)[5]) {
+    e[0] = e[1] = e[2] = e[3] = e[4] = 0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        e[4] += t[v] * e[3];
+        e[3] += t[v] * e[2];
+        e[2] += t[v] * e[1];
+        e[1] += t[v] * e[0];
+        e[0] += t[v];
+    }
 }
 
 // 6 / (m (m-1) (m-2) (m-3)) for m = 0 .. 63 (entries below 4 unused)
@@ -314,6 +283,52 @@ __device__ __forceinline__ void tetra_nodes(const double* __restrict__ E, int nb
     for (int i = 0; i < 5; ++i) x[i] = y[i];
 }
 
+// nodes of entry `code` for pair (a, o) relative to the pair's transition energy d0, in FP32:
+// the vertex energies are differenced in FP64 and rounded once, then sorted and merged (Eq.
+// tetrahedron thresholds on the absolute energies d0 + x) in FP32
+__device__ __forceinline__ void tetra_nodes_rel32(const double* __restrict__ E, int nband, int nocc, int a, int o,
+                                                  const int* __restrict__ kp, const int* __restrict__ tets, int code,
+                                                  double d0, float da, float dr, float (&x)[5]) {
+    const int tt = code >> 2, jv = code & 3;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int kv = tets[4 * tt + v];
+        x[v] = (float)((E[(size_t)kp[kv] * nband + nocc + a] - E[(size_t)kv * nband + o]) - d0);
+    }
+    x[4] = jv == 0 ? x[0] : jv == 1 ? x[1] : jv == 2 ? x[2] : x[3];
+    auto sw = [](float& p, float& q) { const float lo = fminf(p, q), hi = fmaxf(p, q); p = lo; q = hi; };
+    sw(x[0], x[1]); sw(x[3], x[4]); sw(x[2], x[4]); sw(x[2], x[3]); sw(x[0], x[3]);
+    sw(x[0], x[2]); sw(x[1], x[4]); sw(x[1], x[3]); sw(x[1], x[2]);
+    const float d0f = (float)d0;
+    bool brk[5];
+    brk[0] = true;
+    float start = x[0];
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        const float thr = da + dr * fmaxf(fabsf(d0f + start), fabsf(d0f + x[i]));
+        brk[i] = (x[i] - start) >= thr;
+        if (brk[i]) start = x[i];
+    }
+    if (brk[1] && brk[2] && brk[3] && brk[4]) return;
+    float y[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        float sum = 0.f;
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            bool same = true;
+#pragma unroll
+            for (int b = 1; b < 5; ++b)
+                if (b > (i < j ? i : j) && b <= (i < j ? j : i) && brk[b]) same = false;
+            if (same) { sum += x[j]; ++cnt; }
+        }
+        y[i] = sum / cnt;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) x[i] = y[i];
+}
+
 // one divided difference in FP64 from the nodes themselves (used for near-degenerate sets of
 // the FP32 path)
 __device__ __noinline__ double2 dd_fp64_entry(const double* __restrict__ E, int nband, int nocc, int a, int o,
@@ -324,8 +339,13 @@ __device__ __noinline__ double2 dd_fp64_entry(const double* __restrict__ E, int 
     const double c = 0.5 * (x[0] + x[4]);
     const double2 y = make_double2(z.x - c, z.y);
     const double spread = x[4] - x[0];
-    if (spread * spread <= TT_TAU * TT_TAU * (y.x * y.x + y.y * y.y))
-        return dd5_series<double>(x[1] - c, x[2] - c, x[3] - c, spread, y);
+    const double r2 = y.x * y.x + y.y * y.y;
+    if (spread * spread <= TT_TAU * TT_TAU * r2) {
+        const double t[5] = {-0.5 * spread, x[1] - c, x[2] - c, x[3] - c, 0.5 * spread};
+        double e[5];
+        esym5<double>(t, e);
+        return dd5_series<double>(e, spread, y, r2);
+    }
     bool unused = false;
     return dd5_table<double>(x, z, &unused);
 }
@@ -336,19 +356,6 @@ __device__ __noinline__ typename TT<R>::C dd_table_entry(const R (&x)[5], typena
     return dd5_table<R>(x, z, &unused);
 }
 
-// nodes of entry `code` relative to the pair's transition energy d0, as the FP32 pass forms them:
-// centre ct, offsets tr (outer nodes at -+ spread / 2)
-__device__ __forceinline__ void fp32_nodes(const double (&x)[5], double d0, float& ct, float (&tr)[5]) {
-    const double cd = 0.5 * (x[0] + x[4]);
-    const float spread = (float)(x[4] - x[0]);
-    tr[0] = -0.5f * spread;
-    tr[1] = (float)(x[1] - cd);
-    tr[2] = (float)(x[2] - cd);
-    tr[3] = (float)(x[3] - cd);
-    tr[4] = 0.5f * spread;
-    ct = (float)(cd - d0);
-}
-
 // item of the deferred work list: pair t, frequency f, tetrahedron-vertex entry s, pole side,
 // kind (0: near-degenerate set, evaluated in FP64; 1: wide set of the FP32 pass, full table in FP32)
 __device__ __forceinline__ unsigned long long tetra_item(long long t, int f, int s, int side, int kind) {
@@ -356,22 +363,20 @@ __device__ __forceinline__ unsigned long long tetra_item(long long t, int f, int
            ((unsigned long long)kind << 1) | (unsigned long long)side;
 }
 
-// Append a (pair, frequency, tetrahedron-vertex, pole) item to the FP64 work list; when the list
-// is full, evaluate it here instead (slower, same result).
-template <typename C>
-__device__ __forceinline__ void defer_or_eval(unsigned long long* queue, unsigned long long qcap,
-                                              unsigned long long* qcount, long long t, int f, int s, int side,
-                                              C& sacc, const double* __restrict__ E, int nband, int nocc, int a,
-                                              int o, const int* __restrict__ kp, const int* __restrict__ tets,
-                                              int code, double da, double dr, double2 zd) {
-    const unsigned long long slot = atomicAdd(qcount, 1ULL);
-    if (slot < qcap) {
-        queue[slot] = tetra_item(t, f, s, side, 0);
-        return;
-    }
-    const double2 r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, code, da, dr, zd);
-    sacc.x += r.x;
-    sacc.y += r.y;
+// Append an item to the work list with one counter update per warp (the converged lanes that
+// push take consecutive slots); false when the list is full.
+__device__ __forceinline__ bool queue_push(unsigned long long* queue, unsigned long long qcap,
+                                           unsigned long long* qcount, unsigned long long item) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(qcount, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    const unsigned long long slot = base + (unsigned long long)__popc(mask & ((1u << lane) - 1u));
+    if (slot >= qcap) return false;
+    queue[slot] = item;
+    return true;
 }
 
 // Pass over the deferred items: one item per thread, result added to the weight
@@ -407,13 +412,9 @@ __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ 
     if (kind == 0) {
         r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, zd);
     } else {
-        double x[5];
-        tetra_nodes(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, x);
         const double d0 = E[(size_t)kp[k] * nband + nocc + a] - E[(size_t)k * nband + o];
-        float ct, tr[5], xr[5];
-        fp32_nodes(x, d0, ct, tr);
-#pragma unroll
-        for (int j = 0; j < 5; ++j) xr[j] = ct + tr[j];
+        float xr[5];
+        tetra_nodes_rel32(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], d0, (float)da, (float)dr, xr);
         const float2 rf = dd_table_entry<float>(xr, make_float2((float)(zd.x - d0), (float)zd.y));
         r = make_double2((double)rf.x, (double)rf.y);
     }
@@ -424,24 +425,35 @@ __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ 
 }
 
 // Weights for one (k, a, o) per thread and a chunk of frequencies per grid row.  The 24
-// tetrahedron-vertex node sets are prepared once in FP64 (sort, merge, centre) and kept in
-// shared memory; every frequency is then evaluated from them in precision R.  Nodes and poles
-// are taken relative to the pair's own transition energy D0 so that R = float keeps its
-// resolution.  With R = float every node set is evaluated in FP32 except those with two nodes
-// closer than TT_NEAR but not merged (near degeneracy), which go to an FP64 pass.
+// tetrahedron-vertex node sets are prepared once (sorted, merged, centred; FP64 for R = double,
+// FP32 relative to the pair's own transition energy D0 for R = float) and kept in shared memory as
+// their centre, spread and the elementary symmetric polynomials of the centred nodes; the
+// frequencies are then taken TT_FC at a time, each node set read once for the 2 TT_FC poles.
+// With R = float, node sets with two nodes closer than TT_NEAR but not merged (near degeneracy)
+// go to the work list for FP64, and so do (for the FP32 table) the sets too wide for the series.
 #define TT_NEAR 1e-5
-#define TT_FIELDS 5   // t1, t2, t3, centre - D0, spread (negative: near-degenerate set)
+#define TT_FIELDS 7   // e1 .. e5, centre - D0, spread (negative: near-degenerate set)
+#define TT_FC 4
+
+__device__ __forceinline__ double2 tetra_pole(const double* __restrict__ freq, int f, int side, int axis,
+                                              int ordering, double delta) {
+    const double wv = freq[f];
+    if (axis == RP_AXIS_REAL)
+        return side == 0 ? make_double2(wv, delta) : make_double2(-wv, ordering == RP_TIME_ORDERED ? delta : -delta);
+    return side == 0 ? make_double2(0.0, wv + delta)
+                     : make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
+}
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_tetra_weights(const double* __restrict__ E, const double* __restrict__ Tw,
-                                                       int nband, int nocc, int nemp, int nk,
-                                                       const int* __restrict__ kp, const int* __restrict__ tets,
-                                                       const int* __restrict__ tetk, int nf, int fch,
-                                                       const double* __restrict__ freq, int axis, int ordering,
-                                                       double delta, double da, double dr,
-                                                       double2* __restrict__ wout,
-                                                       unsigned long long* __restrict__ queue,
-                                                       unsigned long long qcap, unsigned long long* qcount) {
+__global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__ E, const double* __restrict__ Tw,
+                                                      int nband, int nocc, int nemp, int nk,
+                                                      const int* __restrict__ kp, const int* __restrict__ tets,
+                                                      const int* __restrict__ tetk, int nf, int fch,
+                                                      const double* __restrict__ freq, int axis, int ordering,
+                                                      double delta, double da, double dr,
+                                                      double2* __restrict__ wout,
+                                                      unsigned long long* __restrict__ queue,
+                                                      unsigned long long qcap, unsigned long long* qcount) {
     using C = typename TT<R>::C;
     extern __shared__ __align__(16) unsigned char tsm_raw[];
     R* tsm = reinterpret_cast<R*>(tsm_raw);
@@ -457,67 +469,91 @@ __global__ void __launch_bounds__(128) k_tetra_weights(const double* __restrict_
     if (Tw) pref *= 1.0 - Tw[(size_t)kp[k] * nband + nocc + a] * Tw[(size_t)k * nband + o];
     const double d0 = E[(size_t)kp[k] * nband + nocc + a] - E[(size_t)k * nband + o];
     for (int s = 0; s < 24; ++s) {
-        double x[5];
-        tetra_nodes(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, x);
-        const double cd = 0.5 * (x[0] + x[4]);
+        R x[5];
+        if constexpr (sizeof(R) == 4) {
+            tetra_nodes_rel32(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], d0, (float)da, (float)dr, x);
+        } else {
+            double xa[5];
+            tetra_nodes(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, xa);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) x[i] = xa[i] - d0;
+        }
+        const R cd = (R)0.5 * (x[0] + x[4]);
+        const R spread = x[4] - x[0];
         bool near = false;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const double g = x[i + 1] - x[i];
-            near = near || (g > 0.0 && g < TT_NEAR);
+            const R g = x[i + 1] - x[i];
+            near = near || (g > (R)0 && g < (R)TT_NEAR);
         }
-        fld(s, 0) = (R)(x[1] - cd);
-        fld(s, 1) = (R)(x[2] - cd);
-        fld(s, 2) = (R)(x[3] - cd);
-        fld(s, 3) = (R)(cd - d0);
-        fld(s, 4) = near ? -(R)(x[4] - x[0]) - (R)1 : (R)(x[4] - x[0]);
+        const R tc[5] = {(R)-0.5 * spread, x[1] - cd, x[2] - cd, x[3] - cd, (R)0.5 * spread};
+        R e[5];
+        esym5<R>(tc, e);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) fld(s, j) = e[j];
+        fld(s, 5) = cd;
+        fld(s, 6) = near ? -spread - (R)1 : spread;
     }
-    const int f1 = min(nf, (int)(blockIdx.y + 1) * fch);
-    for (int f = blockIdx.y * fch; f < f1; ++f) {
-        const double wv = freq[f];
-        double2 acc = make_double2(0.0, 0.0);
-        for (int side = 0; side < 2; ++side) {
-            double2 zd;
-            if (axis == RP_AXIS_REAL)
-                zd = side == 0 ? make_double2(wv, delta) : make_double2(-wv, ordering == RP_TIME_ORDERED ? delta : -delta);
-            else
-                zd = side == 0 ? make_double2(0.0, wv + delta)
-                               : make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
-            const C zr = TT<R>::mk((R)(zd.x - d0), (R)zd.y);    // pole relative to D0
-            C sacc = TT<R>::mk(0, 0);
-            for (int s = 0; s < 24; ++s) {
-                const R sp = fld(s, 4);
-                const R spread = sp < (R)0 ? -sp - (R)1 : sp;
-                R tr[5] = {(R)-0.5 * spread, fld(s, 0), fld(s, 1), fld(s, 2), (R)0.5 * spread};
-                const R ct = fld(s, 3);
-                if (sizeof(R) == 4 && sp < (R)0) {
-                    defer_or_eval(queue, qcap, qcount, t, f, s, side, sacc, E, nband, nocc, a, o, kp, tets,
-                                  tetk[24 * k + s], da, dr, zd);
-                    continue;
-                }
-                const C y = TT<R>::mk(zr.x - ct, zr.y);
-                if (spread * spread <= (R)(TT_TAU * TT_TAU) * (y.x * y.x + y.y * y.y)) {
-                    sacc = tadd(sacc, dd5_series<R>(tr[1], tr[2], tr[3], spread, y));
-                } else {
-                    // a wide set: in the FP32 pass it goes to the work list (evaluated there with
-                    // the full table, so that the warps here stay on the series path)
+    const int fend = min(nf, (int)(blockIdx.y + 1) * fch);
+    for (int f0 = blockIdx.y * fch; f0 < fend; f0 += TT_FC) {
+        C zr[TT_FC][2], acc[TT_FC];
+#pragma unroll
+        for (int fi = 0; fi < TT_FC; ++fi) {
+            acc[fi] = TT<R>::mk(0, 0);
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const double2 zd = tetra_pole(freq, min(f0 + fi, nf - 1), side, axis, ordering, delta);
+                zr[fi][side] = TT<R>::mk((R)(zd.x - d0), (R)zd.y);    // pole relative to D0
+            }
+        }
+        for (int s = 0; s < 24; ++s) {
+            const R sp = fld(s, 6);
+            const bool near = sp < (R)0;
+            const R spread = near ? -sp - (R)1 : sp;
+            const R e[5] = {fld(s, 0), fld(s, 1), fld(s, 2), fld(s, 3), fld(s, 4)};
+            const R ct = fld(s, 5);
+#pragma unroll
+            for (int fi = 0; fi < TT_FC; ++fi) {
+                if (f0 + fi >= fend) break;
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const C y = TT<R>::mk(zr[fi][side].x - ct, zr[fi][side].y);
+                    const R r2 = y.x * y.x + y.y * y.y;
+                    if (spread * spread <= (R)(TT_TAU * TT_TAU) * r2) {
+                        acc[fi] = tadd(acc[fi], dd5_series<R>(e, spread, y, r2));
+                        continue;
+                    }
+                    // a wide set (the series does not apply): in the FP32 pass it goes to the work
+                    // list, for the full table in FP32 there, or in FP64 when two of its nodes
+                    // nearly coincide, so that the warps here stay on the series path
                     if (sizeof(R) == 4) {
-                        const unsigned long long slot = atomicAdd(qcount, 1ULL);
-                        if (slot < qcap) {
-                            queue[slot] = tetra_item(t, f, s, side, 1);
+                        if (queue_push(queue, qcap, qcount, tetra_item(t, f0 + fi, s, side, near ? 0 : 1))) continue;
+                        if (near) {
+                            const double2 r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr,
+                                                            tetra_pole(freq, f0 + fi, side, axis, ordering, delta));
+                            acc[fi] = tadd(acc[fi], TT<R>::mk((R)r.x, (R)r.y));
                             continue;
                         }
                     }
                     R xr[5];
+                    if constexpr (sizeof(R) == 4) {
+                        tetra_nodes_rel32(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], d0, (float)da,
+                                          (float)dr, xr);
+                    } else {
+                        double xa[5];
+                        tetra_nodes(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, xa);
 #pragma unroll
-                    for (int i = 0; i < 5; ++i) xr[i] = ct + tr[i];
-                    sacc = tadd(sacc, dd_table_entry<R>(xr, zr));
+                        for (int i = 0; i < 5; ++i) xr[i] = xa[i] - d0;
+                    }
+                    acc[fi] = tadd(acc[fi], dd_table_entry<R>(xr, zr[fi][side]));
                 }
             }
-            acc.x += (double)sacc.x;
-            acc.y += (double)sacc.y;
         }
-        wout[(size_t)f * K + t] = make_double2(acc.x * pref / 6.0, acc.y * pref / 6.0);
+#pragma unroll
+        for (int fi = 0; fi < TT_FC; ++fi)
+            if (f0 + fi < fend)
+                wout[(size_t)(f0 + fi) * K + t] =
+                    make_double2((double)acc[fi].x * pref / 6.0, (double)acc[fi].y * pref / 6.0);
     }
 }
 
@@ -541,7 +577,7 @@ cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double
         if (e != cudaSuccess) return e;
     }
     const long long K = (long long)c->nk * c->nemp * c->nocc;
-    const int bs = 128;
+    const int bs = 64;
     // frequencies per grid row: all of them when the pairs alone fill the GPU
     const int fch = K >= 4LL * 152 * bs ? nf : std::max(1, (int)((nf * K + 4LL * 152 * bs - 1) / (4LL * 152 * bs)));
     dim3 grid((unsigned)((K + bs - 1) / bs), (unsigned)((nf + fch - 1) / fch));
