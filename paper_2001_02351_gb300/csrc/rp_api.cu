@@ -173,21 +173,12 @@ int plan_q(rp_ctx* c, const double q[3]) {
         st = upload(c, P.d_efwd32[a], e32.data(), e32.size() * sizeof(float));
         if (st) return st;
     }
-    // twiddle tables and residue maps of the fused line transforms
+    // residue maps of the line transforms (sphere index of each transform output, or -1)
     P.fused = true;
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 1; a < 3; ++a) {
         const int N = c->fft[a];
-        std::vector<double> t(2 * N);
-        std::vector<float> t32(2 * N);
-        for (int e = 0; e < N; ++e) {
-            double ang = 2.0 * M_PI * (double)e / (double)N;
-            t[2 * e] = std::cos(ang); t[2 * e + 1] = std::sin(ang);
-            t32[2 * e] = (float)t[2 * e]; t32[2 * e + 1] = (float)t[2 * e + 1];
-        }
-        int st_ = upload(c, P.d_tw[a], t.data(), t.size() * sizeof(double));
-        if (st_) return st_;
-        if ((st_ = upload(c, P.d_tw32[a], t32.data(), t32.size() * sizeof(float)))) return st_;
-        if (a > 0) {
+        int st_;
+        {
             std::vector<int> map(N, -1);
             for (int s_ = 0; s_ < P.nset[a]; ++s_) {
                 int r = ((P.setv[a][s_] % N) + N) % N;
@@ -704,9 +695,7 @@ void rp_destroy(rp_ctx* c) {
                       &c->s_u, &c->s_p, &c->s_t1, &c->s_t2, &c->s_m, &c->s_w, &c->s_chi, &c->s_io1, &c->s_io2,
                       &c->s_io3, &c->s_hi, &c->s_lo, &c->s_w32, &c->s_queue, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
-                      &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_tw[0], &c->plan.d_tw[1],
-                      &c->plan.d_tw[2], &c->plan.d_tw32[0], &c->plan.d_tw32[1], &c->plan.d_tw32[2],
-                      &c->plan.d_zmap, &c->plan.d_ymap};
+                      &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_zmap, &c->plan.d_ymap};
     for (DevBuf* b : bufs) release(*b);
     for (int i = 0; i < RP_NSTAGE; ++i)
         for (cudaEvent_t e : c->prof_ev[i]) cudaEventDestroy(e);

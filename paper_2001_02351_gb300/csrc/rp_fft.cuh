@@ -1,7 +1,8 @@
 // In-register mixed-radix (4, 3, 2) Fourier transform of one line of N complex values,
 // sign +1:  X[k] = sum_j x[j] exp(+2 pi i j k / N).
-// Decimation in time; the twiddles W_N^e = exp(2 pi i e / N) come from a table tw[e],
-// e = 0 .. NF-1, of the full line length NF (sub-transforms read it with stride NF/N).
+// Decimation in time; the twiddles W_N^e = exp(2 pi i e / N) are compile-time constants
+// (cos and sin of the reduced angle by their Taylor series in double, rounded once to the
+// line's precision), so a transform issues no loads.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,6 +34,60 @@ __device__ __forceinline__ C c_conjmul(C a, C b) { return Cx<C>::mk(a.x * b.x + 
 // i * a
 template <typename C>
 __device__ __forceinline__ C c_i(C a) { return Cx<C>::mk(-a.y, a.x); }
+
+// cos and sin of 2 pi p / q at compile time: quarter turns exact, otherwise the angle is reduced
+// to |x| <= pi/2 and summed from the Taylor series (terms to x^41 / 41!, far below double
+// roundoff there)
+__host__ __device__ constexpr double ct_cos_series(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int n = 1; n <= 20; ++n) {
+        term *= -x * x / ((double)(2 * n - 1) * (double)(2 * n));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double ct_sin_series(double x) {
+    double term = x, sum = x;
+    for (int n = 1; n <= 20; ++n) {
+        term *= -x * x / ((double)(2 * n) * (double)(2 * n + 1));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double kCtPi = 3.14159265358979323846264338327950288;
+__host__ __device__ constexpr double ct_angle(int p, int q) {   // 2 pi p / q in (-pi, pi]
+    const int r = ((p % q) + q) % q;
+    return 2.0 * r > q ? 2.0 * kCtPi * (double)(r - q) / (double)q : 2.0 * kCtPi * (double)r / (double)q;
+}
+__host__ __device__ constexpr double ct_cos2pi(int p, int q) {
+    const int r = ((p % q) + q) % q;
+    if ((4 * r) % q == 0) {
+        const int quarter = 4 * r / q;
+        return quarter == 0 ? 1.0 : (quarter == 2 ? -1.0 : 0.0);
+    }
+    const double x = ct_angle(p, q);
+    const double ax = x < 0 ? -x : x;
+    return ax > kCtPi / 2 ? -ct_cos_series(kCtPi - ax) : ct_cos_series(x);
+}
+__host__ __device__ constexpr double ct_sin2pi(int p, int q) {
+    const int r = ((p % q) + q) % q;
+    if ((4 * r) % q == 0) {
+        const int quarter = 4 * r / q;
+        return quarter == 1 ? 1.0 : (quarter == 3 ? -1.0 : 0.0);
+    }
+    const double x = ct_angle(p, q);
+    if (x > kCtPi / 2) return ct_sin_series(kCtPi - x);
+    if (x < -kCtPi / 2) return -ct_sin_series(kCtPi + x);
+    return ct_sin_series(x);
+}
+
+// W_N^E = exp(2 pi i E / N) as a constant of the line's precision
+template <typename C, int N, int E>
+__device__ __forceinline__ C twiddle() {
+    using R = typename Cx<C>::R;
+    constexpr double c = ct_cos2pi(E, N), s = ct_sin2pi(E, N);
+    return Cx<C>::mk((R)c, (R)s);
+}
 
 template <int N>
 struct Radix {
@@ -69,11 +124,26 @@ __device__ __forceinline__ void small_dft(C (&t)[3]) {
     t[2] = c_sub(m, rd);
 }
 
-template <typename C, int N, int STRIDE>
+template <typename C, int N>
 struct LineFFT {
     static constexpr int R = Radix<N>::value;
     static constexpr int M = N / R;
-    static __device__ __forceinline__ void run(C (&x)[N], const C* __restrict__ tw) {
+    // butterflies k .. M-1 of the last stage: t_s = W_N^{s k} sub[s][k], R-point DFT, scatter
+    template <int K>
+    static __device__ __forceinline__ void butterflies(C (&x)[N], C (&sub)[R][M]) {
+        if constexpr (K < M) {
+            C t[R];
+            t[0] = sub[0][K];
+            t[1] = c_mul(sub[1][K], twiddle<C, N, K>());
+            if constexpr (R > 2) t[2] = c_mul(sub[2][K], twiddle<C, N, 2 * K>());
+            if constexpr (R > 3) t[3] = c_mul(sub[3][K], twiddle<C, N, 3 * K>());
+            small_dft<C>(t);
+#pragma unroll
+            for (int q = 0; q < R; ++q) x[K + M * q] = t[q];
+            butterflies<K + 1>(x, sub);
+        }
+    }
+    static __device__ __forceinline__ void run(C (&x)[N]) {
         if constexpr (N == 1) {
             return;
         } else if constexpr (M == 1) {
@@ -85,17 +155,8 @@ struct LineFFT {
 #pragma unroll
                 for (int j = 0; j < M; ++j) sub[s][j] = x[j * R + s];
 #pragma unroll
-            for (int s = 0; s < R; ++s) LineFFT<C, M, STRIDE * R>::run(sub[s], tw);
-#pragma unroll
-            for (int k = 0; k < M; ++k) {
-                C t[R];
-                t[0] = sub[0][k];
-#pragma unroll
-                for (int s = 1; s < R; ++s) t[s] = c_mul(sub[s][k], tw[s * k * STRIDE]);
-                small_dft<C>(t);
-#pragma unroll
-                for (int q = 0; q < R; ++q) x[k + M * q] = t[q];
-            }
+            for (int s = 0; s < R; ++s) LineFFT<C, M>::run(sub[s]);
+            butterflies<0>(x, sub);
         }
     }
 };

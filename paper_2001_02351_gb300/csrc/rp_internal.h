@@ -34,10 +34,10 @@ struct QPlan {
     std::vector<int> setv[3];        // the values
     std::vector<int> gpos;           // [ng][3] position of each G's components in the sets
     DevBuf d_gpos, d_efwd[3], d_efwd32[3], d_kp, d_g0, d_vs;
-    // line-transform twiddles exp(2 pi i e / N_axis), e = 0..N_axis-1, and residue maps
-    // (grid index -> position in the axis set, -1 if absent) for the fused pair kernels
+    // residue maps (grid index -> position in the axis set, -1 if absent) of the y and z axes for
+    // the fused pair kernels; fused is false when two set values share a residue
     bool fused = false;
-    DevBuf d_tw[3], d_tw32[3], d_zmap, d_ymap;
+    DevBuf d_zmap, d_ymap;
 };
 
 }  // namespace rp

@@ -131,7 +131,7 @@ template <typename C, int N>
 __global__ void __launch_bounds__(256) k_gather_fft(const double2* __restrict__ coef, const int* __restrict__ miller,
                                                     const int* __restrict__ npw, int npw_max, int nband, int nocc,
                                                     const int* __restrict__ kp, const int* __restrict__ g0, int k0,
-                                                    int lb, const C* __restrict__ tw, C* __restrict__ u) {
+                                                    int lb, C* __restrict__ u) {
     using R = typename CT<C>::R;
     constexpr int XG = 256 / N;
     const int B = 2 * lb + 1, BB = B * B;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_gather_fft(const double2* __restrict__ 
             const int m = slot(n);
             v[n] = m >= 0 ? T[m * BB + l] : CT<C>::make(0, 0);
         }
-        LineFFT<C, N, 1>::run(v, tw);
+        LineFFT<C, N>::run(v);
 #pragma unroll
         for (int x = 0; x < N; ++x) T[x * BB + l] = v[x];
     }
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256) k_gather_fft(const double2* __restrict__ 
                 const int m = slot(n);
                 v[n] = m >= 0 ? src[m * B] : CT<C>::make(0, 0);
             }
-            LineFFT<C, N, 1>::run(v, tw);
+            LineFFT<C, N>::run(v);
 #pragma unroll
             for (int y = 0; y < N; ++y) U[(xl * N + y) * B + m3] = v[y];
         }
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) k_gather_fft(const double2* __restrict__ 
                 const int m = slot(n);
                 v[n] = m >= 0 ? src[m] : CT<C>::make(0, 0);
             }
-            LineFFT<C, N, 1>::run(v, tw);
+            LineFFT<C, N>::run(v);
             C* d = dst + ((size_t)x0 * N + l) * N;
 #pragma unroll
             for (int z = 0; z < N; ++z) d[z] = v[z];
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256) k_gather_grid(const double2* __restrict__
 template <typename C, int N3>
 __global__ void __launch_bounds__(128) k_pair_z(const C* __restrict__ u, int nband, int nocc, int a0, int nab,
                                                 int nlines, const int* __restrict__ zmap, int nz,
-                                                const C* __restrict__ tw, C* __restrict__ T1) {
+                                                C* __restrict__ T1) {
     constexpr int LD = N3 + 1;
     extern __shared__ __align__(16) unsigned char sm_z[];
     C* sa = reinterpret_cast<C*>(sm_z);              // [32][LD]
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(128) k_pair_z(const C* __restrict__ u, int nba
         C x[N3];
 #pragma unroll
         for (int z = 0; z < N3; ++z) x[z] = c_conjmul(sa[li * LD + z], so[oi * 32 * LD + li * LD + z]);
-        LineFFT<C, N3, 1>::run(x, tw);
+        LineFFT<C, N3>::run(x);
         C* dst = T1 + ((size_t)(blockIdx.y * nocc + o) * nlines + l0 + li) * nz;
 #pragma unroll
         for (int z = 0; z < N3; ++z) {
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(128) k_pair_z(const C* __restrict__ u, int nba
 // y transform (pruned) of PPC pairs per CTA into shared memory, then the x sum on the sphere points
 template <typename C, int N2, int PPC, typename CO>
 __global__ void __launch_bounds__(256) k_pair_yx(const C* __restrict__ T1, int npair, int N1, int nz,
-                                                 const int* __restrict__ ymap, int ny, const C* __restrict__ tw,
+                                                 const int* __restrict__ ymap, int ny,
                                                  const C* __restrict__ Ex, const int* __restrict__ gpos, int ng,
                                                  typename Cx<C>::R scale, CO* __restrict__ M, long long ldm,
                                                  long long col0) {
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(256) k_pair_yx(const C* __restrict__ T1, int n
         C v[N2];
 #pragma unroll
         for (int y = 0; y < N2; ++y) v[y] = src[(size_t)y * nz];
-        LineFFT<C, N2, 1>::run(v, tw);
+        LineFFT<C, N2>::run(v);
 #pragma unroll
         for (int y = 0; y < N2; ++y) {
             const int iy = ymap[y];
@@ -377,7 +377,6 @@ template <typename C, int N3, int N2>
 __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const C* __restrict__ u, int nband, int nocc, int nemp, int N1,
                                                  const int* __restrict__ zmap, int nz,
                                                  const int* __restrict__ ymap, int ny,
-                                                 const C* __restrict__ twz, const C* __restrict__ twy,
                                                  C* __restrict__ T2) {
     constexpr int A = 128 / N2;
     constexpr int LD = N3 + 1;
@@ -416,7 +415,7 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
             C v[N3];
 #pragma unroll
             for (int z = 0; z < N3; ++z) v[z] = c_conjmul(sa[(ai * N2 + y) * LD + z], sb[y * LD + z]);
-            LineFFT<C, N3, 1>::run(v, twz);
+            LineFFT<C, N3>::run(v);
 #pragma unroll
             for (int z = 0; z < N3; ++z) {
                 const int iz = zmap[z];
@@ -439,7 +438,7 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
             C v[N2];
 #pragma unroll
             for (int yy = 0; yy < N2; ++yy) v[yy] = tb[(q * N2 + yy) * nz + iz];
-            LineFFT<C, N2, 1>::run(v, twy);
+            LineFFT<C, N2>::run(v);
             const size_t pair = ((size_t)kl * nemp + a0 + q) * nocc + o;
             C* dst = T2 + (pair * N1 + x) * nyz + iz;
 #pragma unroll
@@ -502,84 +501,84 @@ __global__ void __launch_bounds__(256) k_pair_x(const C* __restrict__ T2, long l
 
 template <typename C, int N>
 static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int N1, const int* zmap, int nz,
-                        const int* ymap, int ny, const C* twz, const C* twy, C* T2, cudaStream_t st) {
+                        const int* ymap, int ny, C* T2, cudaStream_t st) {
     constexpr int A = 128 / N;
     const size_t smem = sizeof(C) * ((size_t)(A + 2) * N * (N + 1) + (size_t)2 * A * N * nz);
     if (smem > 200 * 1024) return false;
     if (cudaFuncSetAttribute(k_pair_zy<C, N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return false;
     dim3 grid(N1, (nemp + A - 1) / A, nkb);
-    k_pair_zy<C, N, N><<<grid, 128, smem, st>>>(u, nband, nocc, nemp, N1, zmap, nz, ymap, ny, twz, twy, T2);
+    k_pair_zy<C, N, N><<<grid, 128, smem, st>>>(u, nband, nocc, nemp, N1, zmap, nz, ymap, ny, T2);
     return true;
 }
 
 // plane-wise path for square planes N2 == N3 of a supported length
 template <typename C>
 static bool launch_zy(int n2, int n3, const C* u, int nkb, int nband, int nocc, int nemp, int N1, const int* zmap,
-                      int nz, const int* ymap, int ny, const C* twz, const C* twy, C* T2, cudaStream_t st) {
+                      int nz, const int* ymap, int ny, C* T2, cudaStream_t st) {
     if (n2 != n3) return false;
     switch (n3) {
-        case 16: return launch_zy_n<C, 16>(u, nkb, nband, nocc, nemp, N1, zmap, nz, ymap, ny, twz, twy, T2, st);
-        case 32: return launch_zy_n<C, 32>(u, nkb, nband, nocc, nemp, N1, zmap, nz, ymap, ny, twz, twy, T2, st);
+        case 16: return launch_zy_n<C, 16>(u, nkb, nband, nocc, nemp, N1, zmap, nz, ymap, ny, T2, st);
+        case 32: return launch_zy_n<C, 32>(u, nkb, nband, nocc, nemp, N1, zmap, nz, ymap, ny, T2, st);
         default: return false;
     }
 }
 
 template <typename C, int N3>
 static void launch_z(const C* u, int nkb, int nband, int nocc, int a0, int nab, int nlines, const int* zmap, int nz,
-                     const C* tw, C* T1, cudaStream_t st) {
+                     C* T1, cudaStream_t st) {
     dim3 grid((nlines + 31) / 32, nkb * nab);
     const size_t smem = (size_t)5 * 32 * (N3 + 1) * sizeof(C);
     cudaFuncSetAttribute(k_pair_z<C, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pair_z<C, N3><<<grid, 128, smem, st>>>(u, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1);
+    k_pair_z<C, N3><<<grid, 128, smem, st>>>(u, nband, nocc, a0, nab, nlines, zmap, nz, T1);
 }
 
 template <typename C, int N2, typename CO>
-static void launch_yx(const C* T1, int npair, int N1, int nz, const int* ymap, int ny, const C* tw, const C* Ex,
+static void launch_yx(const C* T1, int npair, int N1, int nz, const int* ymap, int ny, const C* Ex,
                       const int* gpos, int ng, typename Cx<C>::R scale, CO* M, long long ldm, long long col0,
                       cudaStream_t st) {
     constexpr int PPC = sizeof(C) == 8 ? 4 : 2;
     const size_t smem = (size_t)PPC * N1 * ny * nz * sizeof(C);
     cudaFuncSetAttribute(k_pair_yx<C, N2, PPC, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pair_yx<C, N2, PPC, CO><<<(npair + PPC - 1) / PPC, 256, smem, st>>>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos,
+    k_pair_yx<C, N2, PPC, CO><<<(npair + PPC - 1) / PPC, 256, smem, st>>>(T1, npair, N1, nz, ymap, ny, Ex, gpos,
                                                                          ng, scale, M, ldm, col0);
 }
 
 // dispatch on the compile-time line lengths this build instantiates; false if not available
 template <typename C>
 static bool fused_z(int n, const C* u, int nkb, int nband, int nocc, int a0, int nab, int nlines, const int* zmap,
-                    int nz, const C* tw, C* T1, cudaStream_t st) {
+                    int nz, C* T1, cudaStream_t st) {
     switch (n) {
-        case 8: launch_z<C, 8>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
-        case 12: launch_z<C, 12>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
-        case 16: launch_z<C, 16>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
-        case 24: launch_z<C, 24>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
-        case 32: launch_z<C, 32>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
-        case 48: launch_z<C, 48>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, tw, T1, st); return true;
+        case 8: launch_z<C, 8>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, T1, st); return true;
+        case 12: launch_z<C, 12>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, T1, st); return true;
+        case 16: launch_z<C, 16>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, T1, st); return true;
+        case 24: launch_z<C, 24>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, T1, st); return true;
+        case 32: launch_z<C, 32>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, T1, st); return true;
+        case 48: launch_z<C, 48>(u, nkb, nband, nocc, a0, nab, nlines, zmap, nz, T1, st); return true;
         default: return false;
     }
 }
 
 template <typename C, typename CO>
-static bool fused_yx(int n, const C* T1, int npair, int N1, int nz, const int* ymap, int ny, const C* tw,
+static bool fused_yx(int n, const C* T1, int npair, int N1, int nz, const int* ymap, int ny,
                      const C* Ex, const int* gpos, int ng, typename Cx<C>::R scale, CO* M, long long ldm,
                      long long col0, cudaStream_t st) {
     constexpr int PPC = sizeof(C) == 8 ? 4 : 2;
     if ((size_t)PPC * N1 * ny * nz * sizeof(C) > 200 * 1024) return false;
     switch (n) {
-        case 8: launch_yx<C, 8, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
-        case 12: launch_yx<C, 12, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
-        case 16: launch_yx<C, 16, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
-        case 24: launch_yx<C, 24, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
-        case 32: launch_yx<C, 32, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
-        case 48: launch_yx<C, 48, CO>(T1, npair, N1, nz, ymap, ny, tw, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 8: launch_yx<C, 8, CO>(T1, npair, N1, nz, ymap, ny, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 12: launch_yx<C, 12, CO>(T1, npair, N1, nz, ymap, ny, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 16: launch_yx<C, 16, CO>(T1, npair, N1, nz, ymap, ny, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 24: launch_yx<C, 24, CO>(T1, npair, N1, nz, ymap, ny, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 32: launch_yx<C, 32, CO>(T1, npair, N1, nz, ymap, ny, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
+        case 48: launch_yx<C, 48, CO>(T1, npair, N1, nz, ymap, ny, Ex, gpos, ng, scale, M, ldm, col0, st); return true;
         default: return false;
     }
 }
 
 
 template <typename C, int N>
-static bool gather_fft_n(rp_ctx* c, int k0, long long nbands, const C* tw, cudaStream_t st) {
+static bool gather_fft_n(rp_ctx* c, int k0, long long nbands, cudaStream_t st) {
     const int B = 2 * c->lb + 1;
     const size_t smem = sizeof(C) * ((size_t)N * B * B + (size_t)256 * B);
     if (B > N || smem > 200 * 1024) return false;
@@ -588,21 +587,21 @@ static bool gather_fft_n(rp_ctx* c, int k0, long long nbands, const C* tw, cudaS
         return false;
     k_gather_fft<C, N><<<(unsigned)nbands, 256, smem, st>>>(
         (const double2*)c->d_coef.p, (const int*)c->d_miller.p, (const int*)c->d_npw.p, c->npw_max, c->nband, c->nocc,
-        (const int*)c->plan.d_kp.p, (const int*)c->plan.d_g0.p, k0, c->lb, tw, (C*)c->s_u.p);
+        (const int*)c->plan.d_kp.p, (const int*)c->plan.d_g0.p, k0, c->lb, (C*)c->s_u.p);
     return true;
 }
 
 template <typename C>
-static cudaError_t gather_inverse_t(rp_ctx* c, int k0, int nkb, const C* const einv[3], const C* tw,
+static cudaError_t gather_inverse_t(rp_ctx* c, int k0, int nkb, const C* const einv[3],
                                     cudaStream_t st) {
     const int B = 2 * c->lb + 1;
     const int N1 = c->fft[0], N2 = c->fft[1], N3 = c->fft[2];
     const long long nbands = (long long)nkb * c->nband;
     // line-FFT path on cubic grids of a supported length
-    if (tw && N1 == N2 && N2 == N3) {
+    if (N1 == N2 && N2 == N3) {
         bool done = false;
-        if (N1 == 16) done = gather_fft_n<C, 16>(c, k0, nbands, tw, st);
-        else if (N1 == 32) done = gather_fft_n<C, 32>(c, k0, nbands, tw, st);
+        if (N1 == 16) done = gather_fft_n<C, 16>(c, k0, nbands, st);
+        else if (N1 == 32) done = gather_fft_n<C, 32>(c, k0, nbands, st);
         if (done) return cudaGetLastError();
     }
     {   // one CTA per band with the Miller box in shared memory
@@ -650,7 +649,7 @@ static cudaError_t gather_inverse_t(rp_ctx* c, int k0, int nkb, const C* const e
 
 template <typename C, typename CO>
 static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long long col0, const C* const efwd[3],
-                                  const C* const twz, const C* const twy, cudaStream_t st, int* nlaunch) {
+                                  cudaStream_t st, int* nlaunch) {
     const QPlan& P = c->plan;
     const int N1 = c->fft[0], N2 = c->fft[1], N3 = c->fft[2];
     const int ny = P.nset[1], nz = P.nset[2];
@@ -661,9 +660,9 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
         const long long npair = (long long)nkb * c->nemp * c->nocc;
         const size_t t2 = (size_t)npair * N1 * ny * nz * sizeof(C);
         const size_t xsm = ((size_t)P.nset[0] * N1 + (size_t)P.ng * PX_PB) * sizeof(C);
-        if (P.fused && twz && twy && xsm <= 200 * 1024 && t2 <= (size_t)16 << 30 && ensure(c, c->s_t2, t2) == RP_OK &&
+        if (P.fused && xsm <= 200 * 1024 && t2 <= (size_t)16 << 30 && ensure(c, c->s_t2, t2) == RP_OK &&
             launch_zy<C>(N2, N3, (const C*)c->s_u.p, nkb, c->nband, c->nocc, c->nemp, N1, (const int*)P.d_zmap.p,
-                         nz, (const int*)P.d_ymap.p, ny, twz, twy, (C*)c->s_t2.p, st)) {
+                         nz, (const int*)P.d_ymap.p, ny, (C*)c->s_t2.p, st)) {
             cudaError_t e = cudaFuncSetAttribute(k_pair_x<C, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
             if (e != cudaSuccess) return e;
             k_pair_x<C, CO><<<(unsigned)((npair + PX_PB - 1) / PX_PB), 256, xsm, st>>>(
@@ -677,10 +676,10 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
     {
         const long long npair = (long long)nkb * c->nemp * c->nocc;
         const size_t t1 = (size_t)npair * N1 * N2 * nz * sizeof(C);
-        if (P.fused && twz && twy && t1 <= (size_t)12 << 30 && ensure(c, c->s_t1, t1) == RP_OK &&
+        if (P.fused && t1 <= (size_t)12 << 30 && ensure(c, c->s_t1, t1) == RP_OK &&
             fused_z<C>(N3, (const C*)c->s_u.p, nkb, c->nband, c->nocc, 0, c->nemp, N1 * N2, (const int*)P.d_zmap.p,
-                       nz, twz, (C*)c->s_t1.p, st)) {
-            if (fused_yx<C, CO>(N2, (const C*)c->s_t1.p, (int)npair, N1, nz, (const int*)P.d_ymap.p, ny, twy, efwd[0],
+                       nz, (C*)c->s_t1.p, st)) {
+            if (fused_yx<C, CO>(N2, (const C*)c->s_t1.p, (int)npair, N1, nz, (const int*)P.d_ymap.p, ny, efwd[0],
                                 (const int*)P.d_gpos.p, P.ng, (typename CT<C>::R)(1.0 / (double)nr), M, ldm, col0,
                                 st)) {
                 *nlaunch += 2;
@@ -739,11 +738,11 @@ cudaError_t launch_gather_inverse(rp_ctx* c, int k0, int nkb, bool fp32, cudaStr
     if (fp32) {
         const float2* e[3] = {(const float2*)c->d_einv32[0].p, (const float2*)c->d_einv32[1].p,
                               (const float2*)c->d_einv32[2].p};
-        return gather_inverse_t<float2>(c, k0, nkb, e, (const float2*)c->plan.d_tw32[0].p, st);
+        return gather_inverse_t<float2>(c, k0, nkb, e, st);
     }
     const double2* e[3] = {(const double2*)c->d_einv[0].p, (const double2*)c->d_einv[1].p,
                            (const double2*)c->d_einv[2].p};
-    return gather_inverse_t<double2>(c, k0, nkb, e, (const double2*)c->plan.d_tw[0].p, st);
+    return gather_inverse_t<double2>(c, k0, nkb, e, st);
 }
 
 cudaError_t launch_pair_forward(rp_ctx* c, int nkb, double2* M, long long ldm, long long col0, cudaStream_t st,
@@ -751,8 +750,7 @@ cudaError_t launch_pair_forward(rp_ctx* c, int nkb, double2* M, long long ldm, l
     const QPlan& P = c->plan;
     const double2* e[3] = {(const double2*)P.d_efwd[0].p, (const double2*)P.d_efwd[1].p,
                            (const double2*)P.d_efwd[2].p};
-    return pair_forward_t<double2, double2>(c, nkb, M, ldm, col0, e, (const double2*)P.d_tw[2].p,
-                                            (const double2*)P.d_tw[1].p, st, nlaunch);
+    return pair_forward_t<double2, double2>(c, nkb, M, ldm, col0, e, st, nlaunch);
 }
 
 cudaError_t launch_pair_forward32(rp_ctx* c, int nkb, float2* M, long long ldm, long long col0, cudaStream_t st,
@@ -760,8 +758,7 @@ cudaError_t launch_pair_forward32(rp_ctx* c, int nkb, float2* M, long long ldm, 
     const QPlan& P = c->plan;
     const float2* e[3] = {(const float2*)P.d_efwd32[0].p, (const float2*)P.d_efwd32[1].p,
                           (const float2*)P.d_efwd32[2].p};
-    return pair_forward_t<float2, float2>(c, nkb, M, ldm, col0, e, (const float2*)P.d_tw32[2].p,
-                                          (const float2*)P.d_tw32[1].p, st, nlaunch);
+    return pair_forward_t<float2, float2>(c, nkb, M, ldm, col0, e, st, nlaunch);
 }
 
 }  // namespace rp
