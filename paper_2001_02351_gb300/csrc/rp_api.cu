@@ -188,7 +188,24 @@ int plan_q(rp_ctx* c, const double q[3]) {
             if ((st_ = upload(c, a == 2 ? P.d_zmap : P.d_ymap, map.data(), N * sizeof(int)))) return st_;
         }
     }
+    // residue masks and residue-ordered sphere positions (plane-wise pair kernels)
+    P.masks = P.fused && c->fft[1] <= 32 && c->fft[2] <= 32;
+    P.ymask = P.zmask = 0;
+    std::vector<int> gpos_r(P.gpos);
+    if (P.masks) {
+        for (int a = 1; a < 3; ++a) {
+            const int N = c->fft[a];
+            unsigned m = 0;
+            for (int s_ = 0; s_ < P.nset[a]; ++s_) m |= 1u << (((P.setv[a][s_] % N) + N) % N);
+            (a == 1 ? P.ymask : P.zmask) = m;
+            for (int g = 0; g < P.ng; ++g) {
+                const int r = ((P.gm[3 * g + a] % N) + N) % N;
+                gpos_r[3 * g + a] = __builtin_popcount(m & ((1u << r) - 1u));
+            }
+        }
+    }
     int st;
+    if ((st = upload(c, P.d_gpos_r, gpos_r.data(), gpos_r.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_gpos, P.gpos.data(), P.gpos.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_kp, P.kp.data(), P.kp.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_g0, P.g0.data(), P.g0.size() * sizeof(int)))) return st;
@@ -695,7 +712,8 @@ void rp_destroy(rp_ctx* c) {
                       &c->s_u, &c->s_p, &c->s_t1, &c->s_t2, &c->s_m, &c->s_w, &c->s_chi, &c->s_io1, &c->s_io2,
                       &c->s_io3, &c->s_hi, &c->s_lo, &c->s_w32, &c->s_queue, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
-                      &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_zmap, &c->plan.d_ymap};
+                      &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_zmap, &c->plan.d_ymap,
+                      &c->plan.d_gpos_r};
     for (DevBuf* b : bufs) release(*b);
     for (int i = 0; i < RP_NSTAGE; ++i)
         for (cudaEvent_t e : c->prof_ev[i]) cudaEventDestroy(e);

@@ -38,6 +38,12 @@ struct QPlan {
     // the fused pair kernels; fused is false when two set values share a residue
     bool fused = false;
     DevBuf d_zmap, d_ymap;
+    // residue masks of the y and z axes (bit r: residue r present; axes of length <= 32 only) and
+    // the sphere positions with the y and z components in ascending residue order, for the
+    // plane-wise pair kernels
+    bool masks = false;
+    unsigned ymask = 0, zmask = 0;
+    DevBuf d_gpos_r;
 };
 
 }  // namespace rp

@@ -368,15 +368,16 @@ __global__ void __launch_bounds__(256) k_pair_yx(const C* __restrict__ T1, int n
 // stay in shared memory while the occupied bands stream through, one plane per step: the plane
 // of band o + 1 is fetched with coalesced 16-byte loads into registers while thread (a, y) forms
 // conj(u_a) u_o on its z line of band o, transforms it in registers (pruned to the sphere's z
-// values) and parks it in a double-buffered tile.  Then one thread per (a, sphere z) column
-// transforms along y in registers and writes the sphere's y values to T2[pair][x][iy][iz]; the
-// warps without a column go straight on to the next band.  One barrier per occupied band.
+// residues) and parks it in a double-buffered tile.  Then one thread per (a, sphere z) column
+// transforms along y in registers and writes the sphere's y residues to T2[pair][x][iy][iz]; the
+// warps without a column go straight on to the next band.  One barrier per occupied band.  The
+// y and z axes of T2 hold the residues present on the sphere in ascending order: residue r of
+// an axis is kept when bit r of its mask is set, at position popc(mask & (2^r - 1)).
 // k_pair_x: the x sum on the sphere points, M[g][col0 + pair] = scale * sum_x Ex[gx][x] T2[...],
-// one thread per sphere point with all of the CTA's pairs in flight.
+// with T2 streamed through shared memory a few pairs at a time (double-buffered cp.async).
 template <typename C, int N3, int N2>
 __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const C* __restrict__ u, int nband, int nocc, int nemp, int N1,
-                                                 const int* __restrict__ zmap, int nz,
-                                                 const int* __restrict__ ymap, int ny,
+                                                 unsigned zmask, int nz, unsigned ymask, int ny,
                                                  C* __restrict__ T2) {
     constexpr int A = 128 / N2;
     constexpr int LD = N3 + 1;
@@ -417,10 +418,8 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
             for (int z = 0; z < N3; ++z) v[z] = c_conjmul(sa[(ai * N2 + y) * LD + z], sb[y * LD + z]);
             LineFFT<C, N3>::run(v);
 #pragma unroll
-            for (int z = 0; z < N3; ++z) {
-                const int iz = zmap[z];
-                if (iz >= 0) tb[(ai * N2 + y) * nz + iz] = v[z];
-            }
+            for (int z = 0; z < N3; ++z)
+                if ((zmask >> z) & 1u) tb[(ai * N2 + y) * nz + __popc(zmask & ((1u << z) - 1u))] = v[z];
         }
         if (more) {
             C* dst = so + ((o + 1) & 1) * N2 * LD;
@@ -442,84 +441,111 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
             const size_t pair = ((size_t)kl * nemp + a0 + q) * nocc + o;
             C* dst = T2 + (pair * N1 + x) * nyz + iz;
 #pragma unroll
-            for (int yy = 0; yy < N2; ++yy) {
-                const int iy = ymap[yy];
-                if (iy >= 0) dst[iy * nz] = v[yy];
-            }
+            for (int yy = 0; yy < N2; ++yy)
+                if ((ymask >> yy) & 1u) dst[__popc(ymask & ((1u << yy) - 1u)) * nz] = v[yy];
         }
     }
 }
 
-// pairs per read-out CTA; a thread takes two of them for one sphere point
-#define PX_PB 4
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// pairs per stage of the x read-out (one stage is PB * N1 * nyz complex values)
+template <typename C>
+struct PairX { static constexpr int PB = sizeof(C) == 8 ? 2 : 1; };
+#define PX_THREADS 256
+
+// persistent: each CTA takes chunks of PB pairs (chunk c, c + gridDim.x, ...); the next chunk's
+// slab is copied while the current one is summed
 template <typename C, typename CO>
-__global__ void __launch_bounds__(256) k_pair_x(const C* __restrict__ T2, long long npair, int N1, int nyz, int nz,
-                                                const C* __restrict__ Ex, int nx, const int* __restrict__ gpos, int ng,
-                                                typename Cx<C>::R scale, CO* __restrict__ M, long long ldm,
-                                                long long col0) {
+__global__ void __launch_bounds__(PX_THREADS) k_pair_x(const C* __restrict__ T2, long long npair, int N1, int nyz,
+                                                       int nz, const C* __restrict__ Ex, int nx,
+                                                       const int* __restrict__ gpos, int ng,
+                                                       typename Cx<C>::R scale, CO* __restrict__ M, long long ldm,
+                                                       long long col0) {
     using R = typename Cx<C>::R;
+    constexpr int PB = PairX<C>::PB;
     extern __shared__ __align__(16) unsigned char sm_x[];
-    C* ex = reinterpret_cast<C*>(sm_x);           // [nx][N1]
-    C* out = ex + nx * N1;                        // [ng][PX_PB]
-    const long long p0 = (long long)blockIdx.x * PX_PB;
-    const int np = (int)min((long long)PX_PB, npair - p0);
     const size_t per = (size_t)N1 * nyz;
-    for (int e = threadIdx.x; e < nx * N1; e += 256) ex[e] = Ex[e];
-    __syncthreads();
-    // consecutive threads take consecutive sphere points of the same pairs: their loads fall in
-    // one nyz-long row of T2 per x
-    for (int e = threadIdx.x; e < ng * (PX_PB / 2); e += 256) {
-        const int g = e % ng, h = e / ng;
-        const int j0 = 2 * h;
-        if (j0 >= np) continue;
-        const bool two = j0 + 1 < np;
-        const int gx = gpos[3 * g], gyz = gpos[3 * g + 1] * nz + gpos[3 * g + 2];
-        const C* s0 = T2 + (size_t)(p0 + j0) * per + gyz;
-        const C* s1 = two ? s0 + per : s0;
-        const C* w = ex + gx * N1;
-        R r0 = 0, i0 = 0, r1 = 0, i1 = 0;
-#pragma unroll 4
-        for (int xx = 0; xx < N1; ++xx) {
-            const C c = w[xx];
-            const C v0 = __ldg(s0 + (size_t)xx * nyz), v1 = __ldg(s1 + (size_t)xx * nyz);
-            r0 += c.x * v0.x - c.y * v0.y;
-            i0 += c.x * v0.y + c.y * v0.x;
-            r1 += c.x * v1.x - c.y * v1.y;
-            i1 += c.x * v1.y + c.y * v1.x;
+    C* slab = reinterpret_cast<C*>(sm_x);         // [2][PB][N1][nyz]
+    C* ex = slab + 2 * PB * per;                  // [nx][N1]
+    C* out = ex + nx * N1;                        // [ng][PB]
+    for (int e = threadIdx.x; e < nx * N1; e += PX_THREADS) ex[e] = Ex[e];
+    const long long nchunk = (npair + PB - 1) / PB;
+    auto issue = [&](long long c, int b) {
+        const long long p0 = c * PB;
+        const size_t nbytes = (size_t)min((long long)PB, npair - p0) * per * sizeof(C);   // multiple of 16
+        const char* src = reinterpret_cast<const char*>(T2 + (size_t)p0 * per);
+        char* dst = reinterpret_cast<char*>(slab + (size_t)b * PB * per);
+        for (size_t off = (size_t)threadIdx.x * 16; off < nbytes; off += PX_THREADS * 16) cp_async16(dst + off, src + off);
+        cp_async_commit();
+    };
+    long long c = blockIdx.x;
+    if (c < nchunk) issue(c, 0);
+    for (int b = 0; c < nchunk; c += gridDim.x, b ^= 1) {
+        if (c + gridDim.x < nchunk) issue(c + gridDim.x, b ^ 1);
+        else cp_async_commit();                   // an empty group keeps the count uniform
+        cp_async_wait<1>();                       // the current chunk's group has landed
+        __syncthreads();
+        const long long p0 = c * PB;
+        const int np = (int)min((long long)PB, npair - p0);
+        const C* t = slab + (size_t)b * PB * per;
+        for (int g = threadIdx.x; g < ng; g += PX_THREADS) {
+            const int gx = gpos[3 * g], gyz = gpos[3 * g + 1] * nz + gpos[3 * g + 2];
+            const C* w = ex + gx * N1;
+            R re[PB], im[PB];
+#pragma unroll
+            for (int j = 0; j < PB; ++j) re[j] = im[j] = 0;
+#pragma unroll 8
+            for (int xx = 0; xx < N1; ++xx) {
+                const C cw = w[xx];
+#pragma unroll
+                for (int j = 0; j < PB; ++j) {
+                    const C v = t[j * per + xx * nyz + gyz];
+                    re[j] += cw.x * v.x - cw.y * v.y;
+                    im[j] += cw.x * v.y + cw.y * v.x;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < PB; ++j) out[g * PB + j] = Cx<C>::mk(re[j] * scale, im[j] * scale);
         }
-        out[g * PX_PB + j0] = Cx<C>::mk(r0 * scale, i0 * scale);
-        out[g * PX_PB + j0 + 1] = Cx<C>::mk(r1 * scale, i1 * scale);
+        __syncthreads();                          // slab b and out are free after this
+        for (int e = threadIdx.x; e < ng * np; e += PX_THREADS) {
+            const int g = e / np, j = e % np;
+            const C v = out[g * PB + j];
+            M[(size_t)g * ldm + col0 + p0 + j] = CT<CO>::make((typename CT<CO>::R)v.x, (typename CT<CO>::R)v.y);
+        }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < ng * np; e += 256) {
-        const int g = e / np, j = e % np;
-        const C v = out[g * PX_PB + j];
-        M[(size_t)g * ldm + col0 + p0 + j] = CT<CO>::make((typename CT<CO>::R)v.x, (typename CT<CO>::R)v.y);
-    }
+    cp_async_wait<0>();
 }
 
 template <typename C, int N>
-static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int N1, const int* zmap, int nz,
-                        const int* ymap, int ny, C* T2, cudaStream_t st) {
+static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int N1, unsigned zmask, int nz,
+                        unsigned ymask, int ny, C* T2, cudaStream_t st) {
     constexpr int A = 128 / N;
     const size_t smem = sizeof(C) * ((size_t)(A + 2) * N * (N + 1) + (size_t)2 * A * N * nz);
     if (smem > 200 * 1024) return false;
     if (cudaFuncSetAttribute(k_pair_zy<C, N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return false;
     dim3 grid(N1, (nemp + A - 1) / A, nkb);
-    k_pair_zy<C, N, N><<<grid, 128, smem, st>>>(u, nband, nocc, nemp, N1, zmap, nz, ymap, ny, T2);
+    k_pair_zy<C, N, N><<<grid, 128, smem, st>>>(u, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2);
     return true;
 }
 
 // plane-wise path for square planes N2 == N3 of a supported length
 template <typename C>
-static bool launch_zy(int n2, int n3, const C* u, int nkb, int nband, int nocc, int nemp, int N1, const int* zmap,
-                      int nz, const int* ymap, int ny, C* T2, cudaStream_t st) {
+static bool launch_zy(int n2, int n3, const C* u, int nkb, int nband, int nocc, int nemp, int N1, unsigned zmask,
+                      int nz, unsigned ymask, int ny, C* T2, cudaStream_t st) {
     if (n2 != n3) return false;
     switch (n3) {
-        case 16: return launch_zy_n<C, 16>(u, nkb, nband, nocc, nemp, N1, zmap, nz, ymap, ny, T2, st);
-        case 32: return launch_zy_n<C, 32>(u, nkb, nband, nocc, nemp, N1, zmap, nz, ymap, ny, T2, st);
+        case 16: return launch_zy_n<C, 16>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
+        case 32: return launch_zy_n<C, 32>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
         default: return false;
     }
 }
@@ -659,14 +685,17 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
     {
         const long long npair = (long long)nkb * c->nemp * c->nocc;
         const size_t t2 = (size_t)npair * N1 * ny * nz * sizeof(C);
-        const size_t xsm = ((size_t)P.nset[0] * N1 + (size_t)P.ng * PX_PB) * sizeof(C);
-        if (P.fused && xsm <= 200 * 1024 && t2 <= (size_t)16 << 30 && ensure(c, c->s_t2, t2) == RP_OK &&
-            launch_zy<C>(N2, N3, (const C*)c->s_u.p, nkb, c->nband, c->nocc, c->nemp, N1, (const int*)P.d_zmap.p,
-                         nz, (const int*)P.d_ymap.p, ny, (C*)c->s_t2.p, st)) {
+        constexpr int PB = PairX<C>::PB;
+        const size_t xsm = ((size_t)2 * PB * N1 * ny * nz + (size_t)P.nset[0] * N1 + (size_t)P.ng * PB) * sizeof(C);
+        if (P.fused && P.masks && xsm <= 200 * 1024 && t2 <= (size_t)16 << 30 && ensure(c, c->s_t2, t2) == RP_OK &&
+            launch_zy<C>(N2, N3, (const C*)c->s_u.p, nkb, c->nband, c->nocc, c->nemp, N1, P.zmask, nz, P.ymask, ny,
+                         (C*)c->s_t2.p, st)) {
             cudaError_t e = cudaFuncSetAttribute(k_pair_x<C, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
             if (e != cudaSuccess) return e;
-            k_pair_x<C, CO><<<(unsigned)((npair + PX_PB - 1) / PX_PB), 256, xsm, st>>>(
-                (const C*)c->s_t2.p, npair, N1, ny * nz, nz, efwd[0], P.nset[0], (const int*)P.d_gpos.p, P.ng,
+            const long long nchunk = (npair + PB - 1) / PB;
+            const unsigned grid = (unsigned)std::min<long long>(nchunk, c->num_sms);
+            k_pair_x<C, CO><<<grid, PX_THREADS, xsm, st>>>(
+                (const C*)c->s_t2.p, npair, N1, ny * nz, nz, efwd[0], P.nset[0], (const int*)P.d_gpos_r.p, P.ng,
                 (typename CT<C>::R)(1.0 / (double)nr), M, ldm, col0);
             *nlaunch += 2;
             return cudaGetLastError();
