@@ -24,7 +24,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "chi0 build TFLOP/s & %tensor-pipe peak, split-precision vs FP64, at stated error"
-STAGES = ["gather_inverse", "pair_forward", "tetra_weights", "contraction", "dyson"]
+STAGES = ["gather_inverse", "pair_forward", "tetra_weights", "contraction", "dyson", "operands"]
+# DRAM traffic of one contraction launch (ncu), valid only for the source it was measured on
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "contraction_medium_bf16x3.md")
+CONTRACT_SRC = os.path.join(ROOT, "paper_2001_02351_gb300", "csrc", "rp_contract_tc.cu")
+
+
+def measured_traffic(workload, precision):
+    """(bytes per launch, note) from the committed ncu summary if it matches this run, else (None, why)."""
+    import hashlib
+    import re
+    if workload != "medium" or precision != "bf16x3":
+        return None, "no ncu capture for this workload"
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+        src = hashlib.sha256(open(CONTRACT_SRC, "rb").read()).hexdigest()
+    except OSError:
+        return None, "ncu summary missing"
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h:
+        return None, "ncu summary without traffic"
+    if not src.startswith(h.group(1)):
+        return None, "kernel changed since the ncu capture"
+    return int(m.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of K = 64000 pairs"
 
 
 def peaks():
@@ -237,10 +260,13 @@ def main():
     else:
         peak = pk.get("bf16_tflops_sustained", 1700.0)
         peak_note = "measured bf16 sustained"
+    # algorithmic flops of the timed steps / summed duration of the contraction kernel's launches
     achieved = F / t_con / 1e12 if t_con > 0 else None
+    traffic, traffic_note = measured_traffic(args.workload, args.precision)
     roof = {"bound": "tensor", "kernel": "chi0 contraction", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "peak_source": peak_note}
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_note": traffic_note, "launches_per_step": int(launches[3]) // args.steps,
+            "ms_per_launch": float(stage_ms[3]) / max(1, int(launches[3])), "peak_source": peak_note}
 
     res = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -183,7 +183,8 @@ int rp_contract_chi0_static(int ng, long long K, int nfreq, const double* M, con
  * rp_profile_read -- synchronises the context's last stream and returns, per stage,
  *   the summed device time (ms) and the number of kernels launched since the last reset.
  *   Stages: 0 gather + inverse transform, 1 pair product + forward transform + read-back,
- *   2 tetrahedron weights, 3 chi0 contraction, 4 Dyson solve.  ms[5], launches[5] (host). */
+ *   2 tetrahedron weights, 3 chi0 contraction kernel, 4 Dyson solve, 5 operands of the split
+ *   contraction (bf16 split of M and float weights of each block).  ms[6], launches[6] (host). */
 int rp_profile_enable(rp_ctx* ctx, int enable);
 int rp_profile_read(rp_ctx* ctx, double* ms, long long* launches);
 

@@ -230,9 +230,10 @@ class Context:
         self._check(self._lib.rp_profile_enable(self._h, 1 if enable else 0))
 
     def rp_profile_read(self):
-        """(ms[5], launches[5]) per stage: gather+inverse, pair forward, weights, contraction, Dyson."""
-        ms = np.zeros(5)
-        nl = np.zeros(5, dtype=np.int64)
+        """(ms[6], launches[6]) per stage: gather+inverse, pair forward, weights, contraction kernel,
+        Dyson, split-contraction operands (bf16 split of M, float weights)."""
+        ms = np.zeros(6)
+        nl = np.zeros(6, dtype=np.int64)
         self._check(self._lib.rp_profile_read(self._h, ms.ctypes.data_as(ctypes.c_void_p),
                                               nl.ctypes.data_as(ctypes.c_void_p)))
         return ms, nl

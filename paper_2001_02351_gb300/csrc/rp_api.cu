@@ -154,8 +154,32 @@ int plan_q(rp_ctx* c, const double q[3]) {
         P.nset[a] = (int)P.setv[a].size();
         for (int g = 0; g < P.ng; ++g)
             P.gpos[3 * g + a] = (int)(std::lower_bound(P.setv[a].begin(), P.setv[a].end(), P.gm[3 * g + a]) - P.setv[a].begin());
+    }
+    // Transform grid.  The product conj(u_a) u_o has Miller components within
+    // +-(2 mu + 1) per axis (mu: largest |m| of the bands; the empty band is shifted by -G0, |G0_i|
+    // <= 1) and is read back at |g| <= Lg; on any grid with N >= 2 mu + 2 + Lg no other component
+    // of the product folds onto a sphere value, so the transforms give the convolution of Eq. ism
+    // exactly.  A cubic requested grid larger than that is replaced by the smallest of the
+    // transform sizes with dedicated kernels that qualifies; otherwise (including a requested
+    // grid that folds) the requested grid is used as given.
+    for (int a = 0; a < 3; ++a) P.nfft[a] = c->fft[a];
+    if (c->lb > 0 && c->fft[0] == c->fft[1] && c->fft[1] == c->fft[2]) {
+        int need = 0;
+        for (int a = 0; a < 3; ++a) {
+            int lg = 0;
+            for (int v : P.setv[a]) lg = std::max(lg, std::abs(v));
+            need = std::max(need, 2 * c->mu[a] + 2 + lg);
+        }
+        for (int cand : {16, 24, 32})
+            if (cand >= need && cand < c->fft[0]) {
+                for (int a = 0; a < 3; ++a) P.nfft[a] = cand;
+                break;
+            }
+    }
+    P.nr = (long long)P.nfft[0] * P.nfft[1] * P.nfft[2];
+    for (int a = 0; a < 3; ++a) {
         // forward phases exp(+2 pi i g x / N): the matrix element of Eq. ism carries e^{+iG.r}
-        const int N = c->fft[a];
+        const int N = P.nfft[a];
         std::vector<double> e(2 * P.nset[a] * N);
         std::vector<float> e32(2 * P.nset[a] * N);
         for (int s_ = 0; s_ < P.nset[a]; ++s_)
@@ -176,7 +200,7 @@ int plan_q(rp_ctx* c, const double q[3]) {
     // residue maps of the line transforms (sphere index of each transform output, or -1)
     P.fused = true;
     for (int a = 1; a < 3; ++a) {
-        const int N = c->fft[a];
+        const int N = P.nfft[a];
         int st_;
         {
             std::vector<int> map(N, -1);
@@ -189,12 +213,12 @@ int plan_q(rp_ctx* c, const double q[3]) {
         }
     }
     // residue masks and residue-ordered sphere positions (plane-wise pair kernels)
-    P.masks = P.fused && c->fft[1] <= 32 && c->fft[2] <= 32;
+    P.masks = P.fused && P.nfft[1] <= 32 && P.nfft[2] <= 32;
     P.ymask = P.zmask = 0;
     std::vector<int> gpos_r(P.gpos);
     if (P.masks) {
         for (int a = 1; a < 3; ++a) {
-            const int N = c->fft[a];
+            const int N = P.nfft[a];
             unsigned m = 0;
             for (int s_ = 0; s_ < P.nset[a]; ++s_) m |= 1u << (((P.setv[a][s_] % N) + N) % N);
             (a == 1 ? P.ymask : P.zmask) = m;
@@ -205,6 +229,27 @@ int plan_q(rp_ctx* c, const double q[3]) {
         }
     }
     int st;
+    // inverse-transform phases exp(+2 pi i m x / N) for m = -lb..lb (Eq. pak on the grid)
+    if (c->lb > 0) {
+        const int B = 2 * c->lb + 1;
+        for (int a = 0; a < 3; ++a) {
+            const int N = P.nfft[a];
+            std::vector<double> e(2 * (size_t)N * B);
+            std::vector<float> e32(2 * (size_t)N * B);
+            for (int x = 0; x < N; ++x)
+                for (int mi = 0; mi < B; ++mi) {
+                    long long ph = ((long long)(mi - c->lb) * x) % N;
+                    if (ph < 0) ph += N;
+                    double ang = 2.0 * M_PI * (double)ph / (double)N;
+                    e[2 * ((size_t)x * B + mi)] = std::cos(ang);
+                    e[2 * ((size_t)x * B + mi) + 1] = std::sin(ang);
+                    e32[2 * ((size_t)x * B + mi)] = (float)std::cos(ang);
+                    e32[2 * ((size_t)x * B + mi) + 1] = (float)std::sin(ang);
+                }
+            if ((st = upload(c, P.d_einv[a], e.data(), e.size() * sizeof(double)))) return st;
+            if ((st = upload(c, P.d_einv32[a], e32.data(), e32.size() * sizeof(float)))) return st;
+        }
+    }
     if ((st = upload(c, P.d_gpos_r, gpos_r.data(), gpos_r.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_gpos, P.gpos.data(), P.gpos.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_kp, P.kp.data(), P.kp.size() * sizeof(int)))) return st;
@@ -311,7 +356,7 @@ int rp_load_bands(rp_ctx* c, int nk, int nband, int nocc, const int* npw, int np
     if (nk != c->nk) return fail(c, RP_ERR_ARG, "nk does not match the k mesh");
     if (nocc < 1 || nband <= nocc) return fail(c, RP_ERR_ARG, "need 1 <= nocc < nband");
     if (!npw || !miller || !coef || !energy_ha || npw_max < nband) return fail(c, RP_ERR_ARG, "bad band arrays");
-    int maxm = 0;
+    int maxm = 0, mu[3] = {0, 0, 0};
     std::vector<unsigned char> mark((size_t)c->nr);
     for (int k = 0; k < nk; ++k) {
         if (npw[k] < nband || npw[k] > npw_max) return fail(c, RP_ERR_ARG, "npw out of range");
@@ -321,6 +366,7 @@ int rp_load_bands(rp_ctx* c, int nk, int nband, int nocc, const int* npw, int np
             for (int a = 0; a < 3; ++a) {
                 int m = miller[((size_t)k * npw_max + p) * 3 + a];
                 maxm = std::max(maxm, std::abs(m));
+                mu[a] = std::max(mu[a], std::abs(m));
                 int w = ((m % c->fft[a]) + c->fft[a]) % c->fft[a];
                 idx = idx * c->fft[a] + w;
             }
@@ -336,6 +382,7 @@ int rp_load_bands(rp_ctx* c, int nk, int nband, int nocc, const int* npw, int np
     c->plan.valid = false;
     c->nband = nband; c->nocc = nocc; c->nemp = nband - nocc; c->npw_max = npw_max;
     c->lb = maxm + 1;
+    for (int a = 0; a < 3; ++a) c->mu[a] = mu[a];
     if (2 * c->lb + 1 > 4 * std::max(c->fft[0], std::max(c->fft[1], c->fft[2])))
         return fail(c, RP_ERR_ARG, "Miller indices too large for the grid");
     c->npw.assign(npw, npw + nk);
@@ -351,25 +398,6 @@ int rp_load_bands(rp_ctx* c, int nk, int nband, int nocc, const int* npw, int np
     build_tetrahedra(c);
     if ((st = upload(c, c->d_tets, c->tets.data(), c->tets.size() * sizeof(int)))) return st;
     if ((st = upload(c, c->d_tetk, c->tetk.data(), c->tetk.size() * sizeof(int)))) return st;
-    // inverse-transform phases exp(+2 pi i m x / N) for m = -lb..lb (Eq. pak on the grid)
-    const int B = 2 * c->lb + 1;
-    for (int a = 0; a < 3; ++a) {
-        const int N = c->fft[a];
-        std::vector<double> e(2 * (size_t)N * B);
-        std::vector<float> e32(2 * (size_t)N * B);
-        for (int x = 0; x < N; ++x)
-            for (int mi = 0; mi < B; ++mi) {
-                long long ph = ((long long)(mi - c->lb) * x) % N;
-                if (ph < 0) ph += N;
-                double ang = 2.0 * M_PI * (double)ph / (double)N;
-                e[2 * ((size_t)x * B + mi)] = std::cos(ang);
-                e[2 * ((size_t)x * B + mi) + 1] = std::sin(ang);
-                e32[2 * ((size_t)x * B + mi)] = (float)std::cos(ang);
-                e32[2 * ((size_t)x * B + mi) + 1] = (float)std::sin(ang);
-            }
-        if ((st = upload(c, c->d_einv[a], e.data(), e.size() * sizeof(double)))) return st;
-        if ((st = upload(c, c->d_einv32[a], e32.data(), e32.size() * sizeof(float)))) return st;
-    }
     c->loaded = true;
     return RP_OK;
 }
@@ -408,7 +436,7 @@ static int finish(rp_ctx* c, cudaStream_t st, int on_device) {
 // taken in sub-blocks whose real-space grids stay within a scratch budget.
 static int pair_density_device(rp_ctx* c, int k0, int k1, void* M, bool fp32, long long ldm, long long col0,
                                cudaStream_t st) {
-    const size_t per_k = (size_t)c->nband * c->nr * (fp32 ? sizeof(float2) : sizeof(double2));
+    const size_t per_k = (size_t)c->nband * c->plan.nr * (fp32 ? sizeof(float2) : sizeof(double2));
     const int kb = (int)std::max<size_t>(1, std::min<size_t>((size_t)(k1 - k0), ((size_t)2 << 30) / (3 * per_k)));
     for (int k = k0; k < k1; k += kb) {
         const int nkb = std::min(kb, k1 - k);
@@ -518,12 +546,16 @@ static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, lon
     if ((s = ensure(c, c->s_hi, sb)) || (s = ensure(c, c->s_lo, sb)) ||
         (s = ensure(c, c->s_w32, (size_t)((nfreq + 1) / 2 * 2) * (tc_kp2(K) / 2) * sizeof(float2))))
         return s;
-    prof_begin(c, 3, st);
+    prof_begin(c, 5, st);
     e = launch_split_bf16(M, m32, ldm, col0m, K, ng, c->s_hi.p, c->s_lo.p, st);
-    if (e == cudaSuccess)
-        e = launch_contract_bf16x3(c->s_hi.p, c->s_lo.p, K, ng, w, ldw, col0w, nfreq, c->s_w32.p, chi,
-                                   (int*)c->d_err.p + 1, c->num_sms, st);
-    prof_end(c, 3, st, 3);
+    if (e == cudaSuccess) e = launch_weights32(K, w, ldw, col0w, nfreq, c->s_w32.p, st);
+    prof_end(c, 5, st, 2);
+    if (e == cudaSuccess) {
+        prof_begin(c, 3, st);
+        e = launch_contract_bf16x3_core(c->s_hi.p, c->s_lo.p, K, ng, nfreq, c->s_w32.p, chi, (int*)c->d_err.p + 1,
+                                        c->num_sms, st);
+        prof_end(c, 3, st, 1);
+    }
     return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "bf16x3 contraction");
 }
 
@@ -707,8 +739,8 @@ const char* rp_last_error(const rp_ctx* c) {
 void rp_destroy(rp_ctx* c) {
     if (!c) return;
     DevBuf* bufs[] = {&c->d_coef, &c->d_miller, &c->d_npw, &c->d_energy, &c->d_T, &c->d_tets, &c->d_tetk,
-                      &c->d_einv[0], &c->d_einv[1], &c->d_einv[2], &c->d_einv32[0], &c->d_einv32[1],
-                      &c->d_einv32[2], &c->d_err, &c->s_box, &c->s_u1, &c->s_u2,
+                      &c->plan.d_einv[0], &c->plan.d_einv[1], &c->plan.d_einv[2], &c->plan.d_einv32[0],
+                      &c->plan.d_einv32[1], &c->plan.d_einv32[2], &c->d_err, &c->s_box, &c->s_u1, &c->s_u2,
                       &c->s_u, &c->s_p, &c->s_t1, &c->s_t2, &c->s_m, &c->s_w, &c->s_chi, &c->s_io1, &c->s_io2,
                       &c->s_io3, &c->s_hi, &c->s_lo, &c->s_w32, &c->s_queue, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],

@@ -522,11 +522,26 @@ cudaError_t launch_split_bf16(const void* M, bool m32, long long ldm, long long 
 
 // chi (+)= ... over the K pairs whose bf16 split is in hi/lo ([ng][kp2]); chi must be zeroed by
 // the caller before the first accumulation
+cudaError_t launch_weights32(long long K, const double2* w, long long ldw, long long col0, int nf, void* w32,
+                             cudaStream_t st) {
+    const long long kpad = tc_kp2(K) / 2;
+    const int nfp = (nf + 1) / 2;
+    const long long nw = (long long)2 * nfp * kpad;
+    k_weights32<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(w, ldw, col0, K, nf, 2 * nfp, kpad, (float2*)w32);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, int ng, const double2* w,
                                    long long ldw, long long col0, int nf, void* w32, double2* chi, int* err,
                                    int num_sms, cudaStream_t st) {
+    cudaError_t e = launch_weights32(K, w, ldw, col0, nf, w32, st);
+    if (e != cudaSuccess) return e;
+    return launch_contract_bf16x3_core(hi, lo, K, ng, nf, w32, chi, err, num_sms, st);
+}
+
+cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long long K, int ng, int nf,
+                                        const void* w32, double2* chi, int* err, int num_sms, cudaStream_t st) {
     const long long kp2 = tc_kp2(K);
-    const long long kpad = kp2 / 2;
     CUtensorMap mraw_hi, mraw_lo, mrow_hi, mrow_lo;
     if (!make_map(&mraw_hi, const_cast<void*>(hi), ng, kp2, TC_BN) ||
         !make_map(&mraw_lo, const_cast<void*>(lo), ng, kp2, TC_BN) ||
@@ -534,8 +549,6 @@ cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, 
         !make_map(&mrow_lo, const_cast<void*>(lo), ng, kp2, TC_GN))
         return cudaErrorInvalidValue;
     const int nfp = (nf + 1) / 2;
-    const long long nw = (long long)2 * nfp * kpad;
-    k_weights32<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(w, ldw, col0, K, nf, 2 * nfp, kpad, (float2*)w32);
     TcArgs a;
     a.w32 = (const float2*)w32; a.K = K;
     a.ng = ng; a.nf = nf; a.nfp = nfp;

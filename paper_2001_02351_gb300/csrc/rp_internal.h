@@ -8,7 +8,7 @@
 
 #include "respack_gb300.h"
 
-#define RP_NSTAGE 5
+#define RP_NSTAGE 6
 
 namespace rp {
 
@@ -44,6 +44,12 @@ struct QPlan {
     bool masks = false;
     unsigned ymask = 0, zmask = 0;
     DevBuf d_gpos_r;
+    // grid of the pair-density transforms: the requested grid, or a smaller cubic one on which
+    // the transforms are still exact for this sphere (see plan_q), with its inverse-transform
+    // phases exp(+2 pi i m x / N) for m = -lb..lb, [N_axis][2 lb + 1] (FP64 and FP32)
+    int nfft[3] = {0, 0, 0};
+    long long nr = 0;
+    DevBuf d_einv[3], d_einv32[3];
 };
 
 }  // namespace rp
@@ -58,6 +64,7 @@ struct rp_ctx {
     bool loaded = false;
     int nband = 0, nocc = 0, nemp = 0, npw_max = 0;
     int lb = 0;                       // half width of the Miller box used by the gather
+    int mu[3] = {0, 0, 0};            // largest |Miller index| of the bands per axis
     std::vector<int> npw;             // [nk]
     std::vector<int> miller;          // [nk][npw_max][3]
     std::vector<double> energy;       // [nk][nband]
@@ -66,8 +73,6 @@ struct rp_ctx {
     std::vector<int> tetk;            // [nk][24]: 4 * tetra + vertex position
 
     rp::DevBuf d_coef, d_miller, d_npw, d_energy, d_T, d_tets, d_tetk;
-    rp::DevBuf d_einv[3];             // inverse-transform phases [N_axis][2 lb + 1]
-    rp::DevBuf d_einv32[3];           // the same in FP32
     rp::DevBuf d_err;                 // int error flags written by kernels
     // scratch (grow-only)
     rp::DevBuf s_box, s_u1, s_u2, s_u, s_p, s_t1, s_t2, s_m, s_w, s_chi, s_io1, s_io2, s_io3;
@@ -122,6 +127,11 @@ cudaError_t launch_split_bf16(const void* M, bool m32, long long ldm, long long 
 cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, int ng, const double2* w,
                                    long long ldw, long long col0, int nf, void* w32, double2* chi, int* err,
                                    int num_sms, cudaStream_t st);
+// the two halves of launch_contract_bf16x3: float copy of the weights, then the tensor-core kernel
+cudaError_t launch_weights32(long long K, const double2* w, long long ldw, long long col0, int nf, void* w32,
+                             cudaStream_t st);
+cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long long K, int ng, int nf,
+                                        const void* w32, double2* chi, int* err, int num_sms, cudaStream_t st);
 // Dyson step
 cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W,
                          int* err_flag, cudaStream_t st);

@@ -168,9 +168,10 @@ __global__ void __launch_bounds__(256) k_gather_fft(const double2* __restrict__ 
     }
     C* dst = u + (size_t)band * N * N * N;
     for (int x0 = 0; x0 < N; x0 += XG) {
+        const int xg = min(XG, N - x0);
         __syncthreads();
-        // y: m2 -> y on the (x, m3) lines of XG planes
-        for (int l = threadIdx.x; l < XG * B; l += 256) {
+        // y: m2 -> y on the (x, m3) lines of xg planes
+        for (int l = threadIdx.x; l < xg * B; l += 256) {
             const int xl = l / B, m3 = l % B;
             const C* src = T + (size_t)(x0 + xl) * BB + m3;
             C v[N];
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(256) k_gather_fft(const double2* __restrict__ 
         }
         __syncthreads();
         // z: m3 -> z on the (x, y) lines, written to the grid
-        for (int l = threadIdx.x; l < XG * N; l += 256) {
+        for (int l = threadIdx.x; l < xg * N; l += 256) {
             const C* src = U + (size_t)l * B;
             C v[N];
 #pragma unroll
@@ -382,8 +383,9 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
     constexpr int A = 128 / N2;
     constexpr int LD = N3 + 1;
     constexpr int PER = 16 / sizeof(C);                 // complex values per 16-byte load
-    constexpr int NV = N2 * N3 / (128 * PER);           // 16-byte loads per thread per plane
-    static_assert(NV * 128 * PER == N2 * N3, "plane must split evenly into 16-byte loads");
+    constexpr int NE = N2 * N3 / PER;                   // 16-byte pieces of a plane
+    constexpr int NV = (NE + 127) / 128;                // pieces per thread (the last one guarded)
+    static_assert(NE * PER == N2 * N3, "plane must split into 16-byte pieces");
     extern __shared__ __align__(16) unsigned char sm_zy[];
     C* sa = reinterpret_cast<C*>(sm_zy);          // [A][N2][LD]
     C* so = sa + A * N2 * LD;                     // [2][N2][LD]
@@ -410,7 +412,8 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
         if (more) {
             const float4* src = reinterpret_cast<const float4*>(uk + (size_t)(o + 1) * N1 * plane);
 #pragma unroll
-            for (int i = 0; i < NV; ++i) pf[i] = __ldg(src + i * 128 + threadIdx.x);
+            for (int i = 0; i < NV; ++i)
+                if (i * 128 + (int)threadIdx.x < NE) pf[i] = __ldg(src + i * 128 + threadIdx.x);
         }
         if (ai < na) {
             C v[N3];
@@ -425,6 +428,7 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
             C* dst = so + ((o + 1) & 1) * N2 * LD;
 #pragma unroll
             for (int i = 0; i < NV; ++i) {
+                if (i * 128 + (int)threadIdx.x >= NE) break;
                 const C* c = reinterpret_cast<const C*>(&pf[i]);
                 const int e0 = (i * 128 + threadIdx.x) * PER;
 #pragma unroll
@@ -545,6 +549,7 @@ static bool launch_zy(int n2, int n3, const C* u, int nkb, int nband, int nocc, 
     if (n2 != n3) return false;
     switch (n3) {
         case 16: return launch_zy_n<C, 16>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
+        case 24: return launch_zy_n<C, 24>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
         case 32: return launch_zy_n<C, 32>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
         default: return false;
     }
@@ -608,7 +613,7 @@ static bool gather_fft_n(rp_ctx* c, int k0, long long nbands, cudaStream_t st) {
     const int B = 2 * c->lb + 1;
     const size_t smem = sizeof(C) * ((size_t)N * B * B + (size_t)256 * B);
     if (B > N || smem > 200 * 1024) return false;
-    if (ensure(c, c->s_u, (size_t)nbands * c->nr * sizeof(C))) return false;
+    if (ensure(c, c->s_u, (size_t)nbands * c->plan.nr * sizeof(C))) return false;
     if (cudaFuncSetAttribute(k_gather_fft<C, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return false;
     k_gather_fft<C, N><<<(unsigned)nbands, 256, smem, st>>>(
@@ -621,19 +626,20 @@ template <typename C>
 static cudaError_t gather_inverse_t(rp_ctx* c, int k0, int nkb, const C* const einv[3],
                                     cudaStream_t st) {
     const int B = 2 * c->lb + 1;
-    const int N1 = c->fft[0], N2 = c->fft[1], N3 = c->fft[2];
+    const int N1 = c->plan.nfft[0], N2 = c->plan.nfft[1], N3 = c->plan.nfft[2];
     const long long nbands = (long long)nkb * c->nband;
     // line-FFT path on cubic grids of a supported length
     if (N1 == N2 && N2 == N3) {
         bool done = false;
         if (N1 == 16) done = gather_fft_n<C, 16>(c, k0, nbands, st);
+        else if (N1 == 24) done = gather_fft_n<C, 24>(c, k0, nbands, st);
         else if (N1 == 32) done = gather_fft_n<C, 32>(c, k0, nbands, st);
         if (done) return cudaGetLastError();
     }
     {   // one CTA per band with the Miller box in shared memory
         const size_t smem = sizeof(C) * ((size_t)B * B * B + (size_t)B * B + (size_t)N2 * B);
         if (smem <= 200 * 1024) {
-            if (ensure(c, c->s_u, (size_t)nbands * c->nr * sizeof(C))) return cudaErrorMemoryAllocation;
+            if (ensure(c, c->s_u, (size_t)nbands * c->plan.nr * sizeof(C))) return cudaErrorMemoryAllocation;
             cudaError_t e = cudaFuncSetAttribute(k_gather_grid<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             k_gather_grid<C><<<(unsigned)nbands, 256, smem, st>>>(
@@ -644,7 +650,7 @@ static cudaError_t gather_inverse_t(rp_ctx* c, int k0, int nkb, const C* const e
         }
     }
     const size_t box = (size_t)nbands * B * B * B, u1 = (size_t)nbands * N1 * B * B,
-                 u2 = (size_t)nbands * N1 * N2 * B, uu = (size_t)nbands * c->nr;
+                 u2 = (size_t)nbands * N1 * N2 * B, uu = (size_t)nbands * c->plan.nr;
     if (ensure(c, c->s_box, box * sizeof(C)) || ensure(c, c->s_u1, u1 * sizeof(C)) ||
         ensure(c, c->s_u2, u2 * sizeof(C)) || ensure(c, c->s_u, uu * sizeof(C)))
         return cudaErrorMemoryAllocation;
@@ -677,9 +683,9 @@ template <typename C, typename CO>
 static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long long col0, const C* const efwd[3],
                                   cudaStream_t st, int* nlaunch) {
     const QPlan& P = c->plan;
-    const int N1 = c->fft[0], N2 = c->fft[1], N3 = c->fft[2];
+    const int N1 = c->plan.nfft[0], N2 = c->plan.nfft[1], N3 = c->plan.nfft[2];
     const int ny = P.nset[1], nz = P.nset[2];
-    const long long nr = c->nr;
+    const long long nr = c->plan.nr;
     const int bs = 256;
     // plane-wise path: z and y transforms on chip, then the x sum on the sphere points
     {
@@ -765,12 +771,12 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
 
 cudaError_t launch_gather_inverse(rp_ctx* c, int k0, int nkb, bool fp32, cudaStream_t st) {
     if (fp32) {
-        const float2* e[3] = {(const float2*)c->d_einv32[0].p, (const float2*)c->d_einv32[1].p,
-                              (const float2*)c->d_einv32[2].p};
+        const float2* e[3] = {(const float2*)c->plan.d_einv32[0].p, (const float2*)c->plan.d_einv32[1].p,
+                              (const float2*)c->plan.d_einv32[2].p};
         return gather_inverse_t<float2>(c, k0, nkb, e, st);
     }
-    const double2* e[3] = {(const double2*)c->d_einv[0].p, (const double2*)c->d_einv[1].p,
-                           (const double2*)c->d_einv[2].p};
+    const double2* e[3] = {(const double2*)c->plan.d_einv[0].p, (const double2*)c->plan.d_einv[1].p,
+                           (const double2*)c->plan.d_einv[2].p};
     return gather_inverse_t<double2>(c, k0, nkb, e, st);
 }
 

@@ -61,6 +61,26 @@ def test_pair_density(name, krange):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("name,fft", [("tiny", (32, 32, 32)), ("small", (24, 24, 24))])
+def test_pair_density_on_a_smaller_exact_grid(name, fft):
+    """A requested grid larger than the product and the sphere need: the library transforms on
+    a smaller grid on which nothing folds onto the sphere, so M is the oracle's convolution over
+    the requested grid (both are the exact convolution of Eq. ism)."""
+    from dataclasses import replace
+    wl = replace(workload(name), fft=fft)
+    ctx = _ctx(wl)
+    q = wl.q[0]
+    G = OL.eps_sphere(wl.cell.lat, q, wl.ecut_eps[0])
+    ref = OP.pair_density(wl.bands, wl.nocc, wl.nemp, q, G, fft=wl.fft, k_list=range(0, 5))
+    got = ctx.rp_pair_density(q, 0, 5)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    # the split-precision path (FP32 transforms) on the same grid choice
+    M = OP.pair_density(wl.bands, wl.nocc, wl.nemp, q, G, fft=wl.fft)
+    chi_ref = OC.chi0(M, OC.pair_weights(wl, q))
+    chi = ctx.rp_build_chi0(q, _axis(wl), _ordering(wl), wl.freq, wl.delta, rp.RP_BF16X3)
+    assert np.all(_rel_fro(chi, chi_ref) < BF16X3_TOL)
+
+
 @pytest.mark.parametrize("name", ["micro", "small"])
 def test_tetra_weights(name):
     wl = workload(name)
