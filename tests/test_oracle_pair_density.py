@@ -108,3 +108,31 @@ def test_grid_and_free_agree(micro):
     Mg = pd.pair_density(b, wl.nocc, wl.nemp, q, G, fft=wl.fft, wrap=True)
     Mf = pd.pair_density(b, wl.nocc, wl.nemp, q, G, wrap=False)
     assert np.abs(Mg - Mf).max() < 1e-14
+
+
+def test_completeness_free_variant():
+    """With the complete set of bands at k' (Gamma only, q = 0, all N_pw eigenvectors), the
+    squared pair densities of an occupied band b summed over every band a equal the weight of
+    C_b that the shift by G keeps inside the sphere:  sum_a |M^G_ab|^2 = sum_{G1: G1+G in sphere}
+    |C_b[G1]|^2  (Parseval in the orthonormal eigenbasis of H_Gamma)."""
+    from dataclasses import replace
+    from synth.epm import make_bands, psi_sphere
+    cell = fcc_cell(10.2)
+    ecut = 2.0
+    npw = len(psi_sphere(cell.recip, np.zeros(3), ecut))
+    pot = {"kind": "shells", "nshell": 6, "vmin": 0.1, "vmax": 0.3}
+    full = make_bands(cell, (1, 1, 1), ecut, npw, pot, seed=7, workers=1)
+    ob = 2                                               # the occupied band b
+    # band 0 = b (the "occupied" slot), bands 1..npw = all eigenvectors (the "empty" slots)
+    coef = np.concatenate([full.coef[:, ob:ob + 1], full.coef], axis=1)
+    energy = np.concatenate([full.energy[:, ob:ob + 1], full.energy], axis=1)
+    b2 = replace(full, coef=coef, energy=energy)
+    G = lattice.eps_sphere(cell.lat, np.zeros(3), 0.6)
+    M = pd.pair_density(b2, 1, npw, np.zeros(3), G, wrap=False)          # [NG, npw]
+    lhs = np.sum(np.abs(M) ** 2, axis=1)
+    m = full.miller[0, :npw].astype(np.int64)
+    inside = {tuple(r) for r in m}
+    cb = full.coef[0, ob, :npw]
+    rhs = np.array([sum(abs(cb[i]) ** 2 for i in range(npw) if tuple(m[i] + g) in inside) for g in G])
+    assert len(G) > 4 and np.all(rhs < 1.0 + 1e-12)
+    assert np.allclose(lhs, rhs, rtol=0, atol=1e-12)
