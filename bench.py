@@ -193,7 +193,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="medium")
-    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -215,7 +215,7 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     q = wl.q[0]
-    prec = rp.RP_FP64_NATIVE if args.precision == "fp64" else rp.RP_BF16X3
+    prec = {"fp64": rp.RP_FP64_NATIVE, "bf16x3": rp.RP_BF16X3, "tf32x3": rp.RP_TF32X3}[args.precision]
     axis = rp.RP_AXIS_IMAG if wl.axis == "imag" else rp.RP_AXIS_REAL
     ordering = rp.RP_TIME_ORDERED if wl.ordering == "time" else rp.RP_RETARDED
     ctx = rp.context_for(wl)
@@ -269,6 +269,10 @@ def main():
         # FP64 tensor peak = measured bf16 burst x nominal FP64/BF16 ratio (1.25 / 2250)
         peak = pk.get("bf16_tflops", 1900.0) * 1.25 / 2250.0
         peak_note = "measured bf16 burst x nominal fp64/bf16 ratio 1.25/2250"
+    elif prec == rp.RP_TF32X3:
+        # TF32 tensor peak = measured bf16 sustained x nominal TF32/BF16 ratio (1.1 / 2.25)
+        peak = pk.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
+        peak_note = "measured bf16 sustained x nominal tf32/bf16 ratio 1.1/2.25"
     else:
         peak = pk.get("bf16_tflops_sustained", 1700.0)
         peak_note = "measured bf16 sustained"
@@ -282,7 +286,7 @@ def main():
 
     res = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if prec == rp.RP_FP64_NATIVE else "bf16x3",
+           "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16x3", "tf32x3": "tf32x3"}[args.precision],
            "data": "synthetic (seeded empirical-pseudopotential bands)",
            "config": {"workload": args.workload, "ng": ng, "pairs_K": K, "nfreq": nf, "nk": int(wl.bands.kfrac.shape[0]),
                       "nocc": wl.nocc, "nemp": wl.nemp, "fft": list(wl.fft), "axis": wl.axis,

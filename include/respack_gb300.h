@@ -62,8 +62,10 @@ typedef enum {
 
 typedef enum {
     RP_FP64_NATIVE = 0,       /* FP64 pair densities and FP64 tensor-core contraction */
-    RP_FP64_EMULATED = 1,     /* reserved                                             */
-    RP_TF32X3 = 2,            /* reserved                                             */
+    RP_FP64_EMULATED = 1,     /* reserved (RP_ERR_UNSUPPORTED)                        */
+    RP_TF32X3 = 2,            /* FP32 pair densities, FP64 weights, TF32x3 contraction
+                                 (mma.sync m16n8k8 TF32, FP32 accumulation added into
+                                 FP64 every 2048 reals)                               */
     RP_BF16X3 = 3             /* FP32 pair densities, BF16x3 tcgen05 contraction with
                                  FP32 accumulation flushed to FP64                    */
 } rp_precision;
@@ -104,6 +106,12 @@ int rp_load_bands(rp_ctx* ctx, int nk, int nband, int nocc, const int* npw, int 
 int rp_sphere_size(rp_ctx* ctx, const double q_frac[3], int* ng, int* n_tail,
                    int* miller_out, int* tail_out);
 
+/* rp_sphere_size_at -- rp_sphere_size for a given epsilon cut-off ecut_eps_ha (0 < ecut_eps_ha
+ *   <= Ecut_psi, else RP_ERR_ARG) instead of the context's: the sizes of one member of a batch
+ *   with per-q cut-offs (rp_build_chi0_batched). */
+int rp_sphere_size_at(rp_ctx* ctx, const double q_frac[3], double ecut_eps_ha, int* ng, int* n_tail,
+                      int* miller_out, int* tail_out);
+
 /* rp_pair_density -- M^G_ab(k+q,k) for the pairs of k in [k_begin, k_end) (Eq. ism),
  *   computed as in the paper with Fourier transforms: gather of C onto the real-space
  *   grid, inverse 3D transform, conjugate product, forward 3D transform read back on
@@ -129,8 +137,8 @@ int rp_tetra_weights(rp_ctx* ctx, const double q_frac[3], int axis, int ordering
 
 /* rp_contract_chi0 -- chi[f] = M diag(w[f]) M^H (Eq. chi as a weighted contraction).
  *   ng, K        sizes;  M [io] c128 [ng][K];  w [io] c128 [nfreq][K];
- *   chi_out [io] c128 [nfreq][ng][ng] (overwritten).  precision: RP_FP64_NATIVE or
- *   RP_BF16X3. */
+ *   chi_out [io] c128 [nfreq][ng][ng] (overwritten).  precision: RP_FP64_NATIVE, RP_TF32X3
+ *   or RP_BF16X3 (M and w are FP64 in all three; the split tiers round them on the device). */
 int rp_contract_chi0(rp_ctx* ctx, int ng, long long K, int nfreq, const double* M,
                      const double* w, int precision, double* chi_out, int on_device,
                      void* cuda_stream);
@@ -152,6 +160,26 @@ int rp_build_chi0(rp_ctx* ctx, const double q_frac[3], int axis, int ordering, i
  *   returned by the next call of rp_solve_w or by rp_check_numeric. */
 int rp_solve_w(rp_ctx* ctx, const double q_frac[3], int nfreq, const double* chi0,
                double* W_out, double* tail_out, int on_device, void* cuda_stream);
+
+/* rp_build_chi0_batched -- rp_build_chi0 for nq q points in one call (the q-point loop of
+ *   Eq. chi over the mesh), each with its own epsilon sphere.
+ *   q_frac [nq][3] (host); ecut_eps_per_q [nq] Ha (host) or NULL for the context's cut-off;
+ *   chi0_out [nq] (host array of pointers), chi0_out[i] [io] c128 [nfreq][NG_i][NG_i] with NG_i
+ *   from rp_sphere_size_at.  Frequencies, broadening, thresholds and precision are shared.  The
+ *   members are queued in order on cuda_stream; the first failure stops the batch and is
+ *   returned (earlier members are complete, later ones untouched). */
+int rp_build_chi0_batched(rp_ctx* ctx, int nq, const double* q_frac, const double* ecut_eps_per_q,
+                          int axis, int ordering, int nfreq, const double* freq_ha, double delta_ha,
+                          double delta_a, double delta_r, int precision, double* const* chi0_out,
+                          int on_device, void* cuda_stream);
+
+/* rp_solve_w_batched -- rp_solve_w for the members of a batch: chi0[i], W_out[i] [io] c128
+ *   [nfreq][NG_i][NG_i]; tail_out NULL or [nq] pointers (each NULL or double [N_tail,i]);
+ *   q_frac and ecut_eps_per_q as in rp_build_chi0_batched.  FP64, errors as rp_solve_w; the
+ *   first failure stops the batch. */
+int rp_solve_w_batched(rp_ctx* ctx, int nq, const double* q_frac, const double* ecut_eps_per_q, int nfreq,
+                       const double* const* chi0, double* const* W_out, double* const* tail_out,
+                       int on_device, void* cuda_stream);
 
 /* rp_check_numeric -- synchronises the context's last stream and returns RP_ERR_NUMERIC
  *   if an asynchronous rp_solve_w met a bad pivot since the previous check, else RP_OK. */

@@ -24,7 +24,8 @@ _STATUS = {0: "RP_OK", -1: "RP_ERR_ARG", -2: "RP_ERR_STATE", -3: "RP_ERR_OOM", -
 # every symbol the header declares
 EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density", "rp_tetra_weights",
            "rp_contract_chi0", "rp_build_chi0", "rp_solve_w", "rp_check_numeric", "rp_profile_enable",
-           "rp_profile_read", "rp_last_error", "rp_destroy", "rp_contract_chi0_static"]
+           "rp_profile_read", "rp_last_error", "rp_destroy", "rp_contract_chi0_static", "rp_sphere_size_at",
+           "rp_build_chi0_batched", "rp_solve_w_batched"]
 
 
 class RPError(RuntimeError):
@@ -60,6 +61,9 @@ def library():
         "rp_last_error": (ctypes.c_char_p, [P]),
         "rp_destroy": (None, [P]),
         "rp_contract_chi0_static": (I, [I, LL, I, P, P, P, P]),
+        "rp_sphere_size_at": (I, [P, P, D, ctypes.POINTER(I), ctypes.POINTER(I), P, P]),
+        "rp_build_chi0_batched": (I, [P, I, P, P, I, I, I, P, D, D, D, I, P, I, P]),
+        "rp_solve_w_batched": (I, [P, I, P, P, I, P, P, P, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -135,15 +139,22 @@ class Context:
 
     load_bands = rp_load_bands
 
-    def rp_sphere_size(self, q):
+    def rp_sphere_size(self, q, ecut_eps=None):
+        """(Miller [NG][3], tail [N_tail][3]) of q, with the context's cut-off or ecut_eps (Ha)."""
         q_, pq = _host(q, np.float64)
         ng, nt = ctypes.c_int(), ctypes.c_int()
-        self._check(self._lib.rp_sphere_size(self._h, pq, ctypes.byref(ng), ctypes.byref(nt), None, None))
+        if ecut_eps is None:
+            call = lambda g_, t_: self._lib.rp_sphere_size(self._h, pq, ctypes.byref(ng), ctypes.byref(nt), g_, t_)
+        else:
+            call = lambda g_, t_: self._lib.rp_sphere_size_at(self._h, pq, float(ecut_eps), ctypes.byref(ng),
+                                                              ctypes.byref(nt), g_, t_)
+        self._check(call(None, None))
         g = np.zeros((ng.value, 3), dtype=np.int32)
         t = np.zeros((max(nt.value, 1), 3), dtype=np.int32)
-        self._check(self._lib.rp_sphere_size(self._h, pq, ctypes.byref(ng), ctypes.byref(nt),
-                                             g.ctypes.data_as(ctypes.c_void_p), t.ctypes.data_as(ctypes.c_void_p)))
+        self._check(call(g.ctypes.data_as(ctypes.c_void_p), t.ctypes.data_as(ctypes.c_void_p)))
         return g, t[:nt.value]
+
+    rp_sphere_size_at = rp_sphere_size
 
     def _out(self, out, shape, dtype=np.complex128):
         if out is None:
@@ -202,6 +213,50 @@ class Context:
         self._check(self._lib.rp_build_chi0(self._h, pq, int(axis), int(ordering), len(fr), pf, float(delta),
                                             float(delta_a), float(delta_r), int(precision), self._ptr(out, dev),
                                             dev, _stream() if dev else None))
+        return out
+
+    def rp_build_chi0_batched(self, qs, axis, ordering, freq, delta, precision=RP_FP64_NATIVE, ecut_eps=None,
+                              delta_a=1e-8, delta_r=1e-8, outs=None):
+        """chi0 of every q of qs [nq][3] (per-q cut-offs ecut_eps [nq] or None); a list of arrays
+        (host) or of the given CUDA tensors."""
+        qs_, pq = _host(np.asarray(qs, dtype=np.float64).reshape(-1, 3), np.float64)
+        nq = qs_.shape[0]
+        cuts = None if ecut_eps is None else np.ascontiguousarray(ecut_eps, dtype=np.float64)
+        fr, pf = _host(freq, np.float64)
+        if outs is None:
+            outs = []
+            for i in range(nq):
+                g, _ = self.rp_sphere_size(qs_[i], None if cuts is None else cuts[i])
+                outs.append(np.zeros((len(fr), len(g), len(g)), dtype=np.complex128))
+        dev = 1 if _is_torch(outs[0]) else 0
+        ptrs = (ctypes.c_void_p * nq)(*[self._ptr(o, dev).value for o in outs])
+        self._check(self._lib.rp_build_chi0_batched(
+            self._h, nq, pq, None if cuts is None else cuts.ctypes.data_as(ctypes.c_void_p), int(axis), int(ordering),
+            len(fr), pf, float(delta), float(delta_a), float(delta_r), int(precision), ptrs, dev,
+            _stream() if dev else None))
+        return outs
+
+    def rp_solve_w_batched(self, qs, chi0s, ecut_eps=None):
+        """W of every member of a batch (host arrays): list of (W, tail)."""
+        qs_, pq = _host(np.asarray(qs, dtype=np.float64).reshape(-1, 3), np.float64)
+        nq = qs_.shape[0]
+        cuts = None if ecut_eps is None else np.ascontiguousarray(ecut_eps, dtype=np.float64)
+        chis = [np.ascontiguousarray(c, dtype=np.complex128) for c in chi0s]
+        Ws = [np.zeros_like(c) for c in chis]
+        tails = []
+        for i in range(nq):
+            _, t = self.rp_sphere_size(qs_[i], None if cuts is None else cuts[i])
+            tails.append(np.zeros(max(len(t), 1)))
+        P = ctypes.c_void_p
+        pc = (P * nq)(*[c.ctypes.data for c in chis])
+        pw = (P * nq)(*[w.ctypes.data for w in Ws])
+        pt = (P * nq)(*[t.ctypes.data for t in tails])
+        self._check(self._lib.rp_solve_w_batched(self._h, nq, pq, None if cuts is None else cuts.ctypes.data_as(P),
+                                                 int(chis[0].shape[0]), pc, pw, pt, 0, None))
+        out = []
+        for i in range(nq):
+            _, t = self.rp_sphere_size(qs_[i], None if cuts is None else cuts[i])
+            out.append((Ws[i], tails[i][:len(t)]))
         return out
 
     def rp_solve_w(self, q, chi0, out=None, tail=None):

@@ -98,10 +98,13 @@ static void search_box(const rp_ctx* c, double ecut, const double q[3], int nmax
     }
 }
 
-int plan_q(rp_ctx* c, const double q[3]) {
+int plan_q(rp_ctx* c, const double q[3]) { return plan_q_cut(c, q, c->ecut_eps); }
+
+int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps) {
     QPlan& P = c->plan;
-    if (P.valid && P.q[0] == q[0] && P.q[1] == q[1] && P.q[2] == q[2]) return RP_OK;
+    if (P.valid && P.q[0] == q[0] && P.q[1] == q[1] && P.q[2] == q[2] && P.ecut == ecut_eps) return RP_OK;
     P.valid = false;
+    if (!(ecut_eps > 0.0) || !(ecut_eps <= c->ecut_psi)) return fail(c, RP_ERR_ARG, "need 0 < Ecut_eps <= Ecut_psi");
     for (int i = 0; i < 3; ++i) {
         if (!std::isfinite(q[i]) || !(std::fabs(q[i]) < 1.0)) return fail(c, RP_ERR_ARG, "q must be finite with |q_i| < 1");
         double v = q[i] * c->kmesh[i];
@@ -118,10 +121,10 @@ int plan_q(rp_ctx* c, const double q[3]) {
         for (int m2 = -nmax[1]; m2 <= nmax[1]; ++m2)
             for (int m3 = -nmax[2]; m3 <= nmax[2]; ++m3) {
                 double e = half_norm2(c, q, m1, m2, m3);
-                if (e <= c->ecut_eps && e > 1e-14) {
+                if (e <= ecut_eps && e > 1e-14) {
                     P.gm.push_back(m1); P.gm.push_back(m2); P.gm.push_back(m3);
                     P.vs.push_back(std::sqrt(fourpi_om / (2.0 * e)));
-                } else if (e > c->ecut_eps && e <= c->ecut_psi) {
+                } else if (e > ecut_eps && e <= c->ecut_psi) {
                     P.tail.push_back(m1); P.tail.push_back(m2); P.tail.push_back(m3);
                     P.tailv.push_back(fourpi_om / (2.0 * e));
                 }
@@ -256,6 +259,7 @@ int plan_q(rp_ctx* c, const double q[3]) {
     if ((st = upload(c, P.d_g0, P.g0.data(), P.g0.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_vs, P.vs.data(), P.vs.size() * sizeof(double)))) return st;
     for (int i = 0; i < 3; ++i) P.q[i] = q[i];
+    P.ecut = ecut_eps;
     P.valid = true;
     return RP_OK;
 }
@@ -403,8 +407,14 @@ int rp_load_bands(rp_ctx* c, int nk, int nband, int nocc, const int* npw, int np
 }
 
 int rp_sphere_size(rp_ctx* c, const double q[3], int* ng, int* n_tail, int* miller_out, int* tail_out) {
+    if (!c) return RP_ERR_ARG;
+    return rp_sphere_size_at(c, q, c->ecut_eps, ng, n_tail, miller_out, tail_out);
+}
+
+int rp_sphere_size_at(rp_ctx* c, const double q[3], double ecut_eps_ha, int* ng, int* n_tail, int* miller_out,
+                      int* tail_out) {
     if (!c || !q) return RP_ERR_ARG;
-    int st = plan_q(c, q);
+    int st = plan_q_cut(c, q, ecut_eps_ha);
     if (st) return st;
     if (ng) *ng = c->plan.ng;
     if (n_tail) *n_tail = c->plan.ntail;
@@ -413,12 +423,13 @@ int rp_sphere_size(rp_ctx* c, const double q[3], int* ng, int* n_tail, int* mill
     return RP_OK;
 }
 
-static int check_ready(rp_ctx* c, const double q[3]) {
+static int check_ready_cut(rp_ctx* c, const double q[3], double ecut_eps) {
     if (!c) return RP_ERR_ARG;
     if (!c->loaded) return fail(c, RP_ERR_STATE, "bands not loaded");
     if (!q) return fail(c, RP_ERR_ARG, "q is NULL");
-    return plan_q(c, q);
+    return plan_q_cut(c, q, ecut_eps);
 }
+static int check_ready(rp_ctx* c, const double q[3]) { return check_ready_cut(c, q, c ? c->ecut_eps : 0.0); }
 
 static int finish(rp_ctx* c, cudaStream_t st, int on_device) {
     cudaError_t e = cudaGetLastError();
@@ -541,6 +552,13 @@ static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, lon
         prof_end(c, 3, st, 1);
         return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "contraction");
     }
+    if (precision == RP_TF32X3) {
+        prof_begin(c, 3, st);
+        const void* Mb = m32 ? (const void*)((const float2*)M + col0m) : (const void*)((const double2*)M + col0m);
+        e = launch_contract_tf32x3(Mb, m32, ldm, K, w, ldw, col0w, nfreq, ng, chi, accumulate, st);
+        prof_end(c, 3, st, 1);
+        return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "TF32x3 contraction");
+    }
     const size_t sb = (size_t)ng * tc_kp2(K) * 2;
     int s;
     if ((s = ensure(c, c->s_hi, sb)) || (s = ensure(c, c->s_lo, sb)) ||
@@ -576,7 +594,8 @@ int rp_contract_chi0(rp_ctx* c, int ng, long long K, int nfreq, const double* M,
                      double* chi_out, int on_device, void* stream) {
     if (!c) return RP_ERR_ARG;
     if (ng < 1 || K < 1 || nfreq < 1 || !M || !w || !chi_out) return fail(c, RP_ERR_ARG, "bad contraction arguments");
-    if (precision != RP_FP64_NATIVE && precision != RP_BF16X3) return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
+    if (precision != RP_FP64_NATIVE && precision != RP_BF16X3 && precision != RP_TF32X3)
+        return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
     cudaStream_t st = (cudaStream_t)stream;
     const double2 *dM = (const double2*)M, *dw = (const double2*)w;
     double2* dchi = (double2*)chi_out;
@@ -602,13 +621,15 @@ int rp_contract_chi0(rp_ctx* c, int ng, long long K, int nfreq, const double* M,
     return on_device ? RP_OK : check_timeout(c);
 }
 
-int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfreq, const double* freq,
-                  double delta, double da, double dr, int precision, double* chi0_out, int on_device, void* stream) {
-    int s = check_ready(c, q);
+static int build_chi0(rp_ctx* c, const double q[3], double ecut_eps, int axis, int ordering, int nfreq,
+                      const double* freq, double delta, double da, double dr, int precision, double* chi0_out,
+                      int on_device, void* stream) {
+    int s = check_ready_cut(c, q, ecut_eps);
     if (s) return s;
     if ((s = check_freq(c, axis, ordering, nfreq, freq, delta, da, dr))) return s;
     if (!chi0_out) return fail(c, RP_ERR_ARG, "chi0_out is NULL");
-    if (precision != RP_FP64_NATIVE && precision != RP_BF16X3) return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
+    if (precision != RP_FP64_NATIVE && precision != RP_BF16X3 && precision != RP_TF32X3)
+        return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
     cudaStream_t st = (cudaStream_t)stream;
     const int ng = c->plan.ng;
     const long long K = (long long)c->nk * c->nemp * c->nocc;
@@ -625,7 +646,9 @@ int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfre
         chi = (double2*)c->s_chi.p;
     }
     double2* w = (double2*)c->s_w.p;
-    if ((s = weights_device(c, axis, ordering, nfreq, freq, delta, da, dr, m32, w, st))) return s;
+    // the FP32 weight pass belongs to the BF16x3 tier; TF32x3 keeps FP64 weights (its own error is
+    // far below the FP32 pass's)
+    if ((s = weights_device(c, axis, ordering, nfreq, freq, delta, da, dr, precision == RP_BF16X3, w, st))) return s;
     if (precision == RP_BF16X3) {
         cudaError_t e = cudaMemsetAsync(chi, 0, bc, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "zero chi");
@@ -661,9 +684,9 @@ int rp_check_numeric(rp_ctx* c) {
     return RP_OK;
 }
 
-int rp_solve_w(rp_ctx* c, const double q[3], int nfreq, const double* chi0, double* W_out, double* tail_out,
-               int on_device, void* stream) {
-    int s = check_ready(c, q);
+static int solve_w(rp_ctx* c, const double q[3], double ecut_eps, int nfreq, const double* chi0, double* W_out,
+                   double* tail_out, int on_device, void* stream) {
+    int s = check_ready_cut(c, q, ecut_eps);
     if (s) return s;
     if (nfreq < 1 || !chi0 || !W_out) return fail(c, RP_ERR_ARG, "bad Dyson arguments");
     const int ng = c->plan.ng;
@@ -705,6 +728,47 @@ int rp_solve_w(rp_ctx* c, const double q[3], int nfreq, const double* chi0, doub
         return rp_check_numeric(c);
     }
     return finish(c, st, 1);
+}
+
+int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfreq, const double* freq,
+                  double delta, double da, double dr, int precision, double* chi0_out, int on_device, void* stream) {
+    if (!c) return RP_ERR_ARG;
+    return build_chi0(c, q, c->ecut_eps, axis, ordering, nfreq, freq, delta, da, dr, precision, chi0_out, on_device,
+                      stream);
+}
+
+int rp_solve_w(rp_ctx* c, const double q[3], int nfreq, const double* chi0, double* W_out, double* tail_out,
+               int on_device, void* stream) {
+    if (!c) return RP_ERR_ARG;
+    return solve_w(c, q, c->ecut_eps, nfreq, chi0, W_out, tail_out, on_device, stream);
+}
+
+int rp_build_chi0_batched(rp_ctx* c, int nq, const double* q_frac, const double* ecut_eps_per_q, int axis,
+                          int ordering, int nfreq, const double* freq, double delta, double da, double dr,
+                          int precision, double* const* chi0_out, int on_device, void* stream) {
+    if (!c) return RP_ERR_ARG;
+    if (nq < 1 || !q_frac || !chi0_out) return fail(c, RP_ERR_ARG, "bad batch arguments");
+    for (int i = 0; i < nq; ++i) {
+        const double cut = ecut_eps_per_q ? ecut_eps_per_q[i] : c->ecut_eps;
+        const int s = build_chi0(c, q_frac + 3 * i, cut, axis, ordering, nfreq, freq, delta, da, dr, precision,
+                                 chi0_out[i], on_device, stream);
+        if (s) return s;
+    }
+    return RP_OK;
+}
+
+int rp_solve_w_batched(rp_ctx* c, int nq, const double* q_frac, const double* ecut_eps_per_q, int nfreq,
+                       const double* const* chi0, double* const* W_out, double* const* tail_out, int on_device,
+                       void* stream) {
+    if (!c) return RP_ERR_ARG;
+    if (nq < 1 || !q_frac || !chi0 || !W_out) return fail(c, RP_ERR_ARG, "bad batch arguments");
+    for (int i = 0; i < nq; ++i) {
+        const double cut = ecut_eps_per_q ? ecut_eps_per_q[i] : c->ecut_eps;
+        const int s = solve_w(c, q_frac + 3 * i, cut, nfreq, chi0[i], W_out[i], tail_out ? tail_out[i] : nullptr,
+                              on_device, stream);
+        if (s) return s;
+    }
+    return RP_OK;
 }
 
 int rp_profile_enable(rp_ctx* c, int enable) {

@@ -23,6 +23,7 @@ struct DevBuf {
 struct QPlan {
     bool valid = false;
     double q[3] = {0, 0, 0};
+    double ecut = 0;                 // epsilon-sphere cut-off the plan was made for (Ha)
     int qi[3] = {0, 0, 0};           // q * kmesh (integers)
     int ng = 0, ntail = 0;
     std::vector<int> gm;             // [ng][3]
@@ -99,7 +100,8 @@ void prof_end(rp_ctx* c, int stage, cudaStream_t st, int launches);
 int cuda_fail(rp_ctx* c, cudaError_t e, const char* where);
 int ensure(rp_ctx* c, DevBuf& b, size_t bytes);
 void release(DevBuf& b);
-int plan_q(rp_ctx* c, const double q[3]);
+int plan_q(rp_ctx* c, const double q[3]);                  // with the context's cut-off
+int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps);
 
 // ---- kernel launchers (each returns cudaError_t of the launch) ----
 // gather + inverse transform of nb bands into u[nb][N1][N2][N3] (complex double)
@@ -132,6 +134,11 @@ cudaError_t launch_weights32(long long K, const double2* w, long long ldw, long 
                              cudaStream_t st);
 cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long long K, int ng, int nf,
                                         const void* w32, double2* chi, int* err, int num_sms, cudaStream_t st);
+// TF32x3 contraction (mma.sync, FP32 accumulation added into FP64): chi (+)= over K pairs of M
+// (complex float when m32, else complex double) from column 0 of the given pointer
+cudaError_t launch_contract_tf32x3(const void* M, bool m32, long long ldm, long long K, const double2* w,
+                                   long long ldw, long long col0w, int nf, int ng, double2* chi, int accumulate,
+                                   cudaStream_t st);
 // Dyson step
 cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W,
                          int* err_flag, cudaStream_t st);

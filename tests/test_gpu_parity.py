@@ -225,6 +225,36 @@ def test_build_chi0_bf16x3_tiny(tiny, tiny_ref):
     assert np.all(_rel_fro(W, W_ref) < BF16X3_TOL)
 
 
+# TF32x3: operands rounded to TF32 hi + lo (2^-11 and 2^-22 relative), FP32 accumulation inside
+# each 2048-real window added into FP64; with FP32 pair densities the stated bound is 1e-6.
+TF32X3_TOL = 1e-6
+
+
+@pytest.mark.parametrize("ng,K,nf", [(150, 5000, 2), (64, 100, 1), (7, 33, 3), (130, 20000, 1)])
+def test_contract_tf32x3(ng, K, nf):
+    rng = np.random.default_rng(11 * ng + K)
+    M = rng.standard_normal((ng, K)) + 1j * rng.standard_normal((ng, K))
+    w = rng.standard_normal((nf, K)) + 1j * rng.standard_normal((nf, K))
+    ctx = _ctx(workload("micro"))
+    got = ctx.rp_contract_chi0(M, w, precision=rp.RP_TF32X3)
+    ref = OC.chi0(M, w)
+    err = _rel_fro(got, ref)
+    print("tf32x3 rel err", err)
+    assert np.all(err < TF32X3_TOL)
+
+
+def test_build_chi0_tf32x3_tiny(tiny, tiny_ref):
+    chi_ref, W_ref = tiny_ref
+    ctx = _ctx(tiny)
+    q = tiny.q[0]
+    chi = ctx.rp_build_chi0(q, _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, rp.RP_TF32X3)
+    e = _rel_fro(chi, chi_ref)
+    print("tf32x3 chi0 rel err per frequency", e)
+    assert np.all(e < TF32X3_TOL)
+    W, _ = ctx.rp_solve_w(q, chi)
+    assert np.all(_rel_fro(W, W_ref) < TF32X3_TOL)
+
+
 # ---- FP32 weights of the split-precision path (FP64 re-evaluation near degeneracies) ----
 # FP32 rounding amplified by the divided-difference recursion of resonant node sets stays below
 # 1e-4 of the largest weight of a frequency, the budget of the split-precision chi0.
@@ -261,3 +291,31 @@ def test_build_chi0_bf16x3_real_axis_small_broadening():
     e = _rel_fro(chi, chi_ref)
     print("bf16x3 real-axis chi0 rel err", e)
     assert np.all(e < BF16X3_TOL)
+
+
+def test_batched_q_with_uneven_spheres_tiny():
+    """rp_build_chi0_batched / rp_solve_w_batched over three q of the 4^3 mesh (Gamma excluded),
+    each with its own epsilon cut-off (NG about 20, 50 and 80, cut-offs placed mid-gap), against
+    the oracle per member."""
+    from synth.configs import _mid_gap_cutoff
+    wl = workload("tiny")
+    ctx = _ctx(wl)
+    qs = np.array([wl.q[0], [0.25, 0.25, 0.0], [0.5, 0.0, 0.25]])
+    cuts = np.array([_mid_gap_cutoff(wl.cell.recip, q, t, exclude_zero=True) for q, t in zip(qs, (20, 50, 80))])
+    assert np.all(cuts < wl.bands.ecut_psi)
+    chis = ctx.rp_build_chi0_batched(qs, _axis(wl), _ordering(wl), wl.freq, wl.delta, rp.RP_FP64_NATIVE,
+                                     ecut_eps=cuts)
+    ws = ctx.rp_solve_w_batched(qs, chis, ecut_eps=cuts)
+    sizes = []
+    for q, cut, chi, (W, tail) in zip(qs, cuts, chis, ws):
+        G = OL.eps_sphere(wl.cell.lat, q, cut)
+        sizes.append(len(G))
+        assert chi.shape == (len(wl.freq), len(G), len(G))
+        M = OP.pair_density(wl.bands, wl.nocc, wl.nemp, q, G, fft=wl.fft)
+        chi_ref = OC.chi0(M, OC.pair_weights(wl, q))
+        assert np.all(_rel_fro(chi, chi_ref) < 1e-11)
+        W_ref = OD.screened(chi_ref, OD.coulomb_sqrt(wl.cell.lat, q, G))
+        assert np.all(_rel_fro(W, W_ref) < 1e-11)
+        T = OL.tail_sphere(wl.cell.lat, q, cut, wl.bands.ecut_psi)
+        assert np.allclose(tail, OD.tail(wl.cell.lat, q, T), rtol=1e-14, atol=0)
+    assert len(set(sizes)) == 3
