@@ -65,7 +65,7 @@ typedef enum {
     RP_FP64_EMULATED = 1,     /* reserved (RP_ERR_UNSUPPORTED)                        */
     RP_TF32X3 = 2,            /* FP32 pair densities, FP64 weights, TF32x3 contraction
                                  (mma.sync m16n8k8 TF32, FP32 accumulation added into
-                                 FP64 every 2048 reals)                               */
+                                 FP64 every 16 reals)                                 */
     RP_BF16X3 = 3             /* FP32 pair densities, BF16x3 tcgen05 contraction with
                                  FP32 accumulation flushed to FP64                    */
 } rp_precision;

@@ -4,8 +4,9 @@
 // weighted operand contributes a re-row (P, Q) and an im-row (-Q, P), P = wr mr + wi mi,
 // Q = wr mi - wi mr), on the warp-level tensor-core instruction mma.sync m16n8k8 with TF32
 // inputs: every real operand is split x = hi + lo (hi = x rounded to TF32, lo = x - hi) and the
-// product is a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32 registers and added into
-// FP64 registers every TF_FLUSH chunks; the FP64 sums are added into chi at the end.
+// product is a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32 registers over one chunk (16
+// reals: at most 16 roundings of 2^-23, below the 2^-22 of the split) and added into FP64
+// registers after every chunk; the FP64 sums are added into chi at the end.
 // CTA: 256 threads, tile 64 G rows x 64 G' (128 weighted rows); K chunk of 16 reals (8 pairs)
 // staged in shared memory as TF32 hi / lo.
 #include "rp_internal.h"
@@ -16,7 +17,6 @@ namespace rp {
 #define TF_TN 64                 // G' per CTA (128 weighted rows)
 #define TF_KC 16                 // reals per chunk
 #define TF_LD (TF_KC + 4)        // padded row: conflict-free fragment loads
-#define TF_FLUSH 128             // chunks per FP32 window (2048 reals)
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) k_contract_tf32x3(const CM* __restrict__ 
                     mma_tf32(acc[i][j], al[i], bh[j]);
                 }
         }
-        if ((c + 1) % TF_FLUSH == 0 || c + 1 == nchunk) {
+        {
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll

@@ -225,9 +225,9 @@ def test_build_chi0_bf16x3_tiny(tiny, tiny_ref):
     assert np.all(_rel_fro(W, W_ref) < BF16X3_TOL)
 
 
-# TF32x3: operands rounded to TF32 hi + lo (2^-11 and 2^-22 relative), FP32 accumulation inside
-# each 2048-real window added into FP64; with FP32 pair densities the stated bound is 1e-6.
-TF32X3_TOL = 1e-6
+# TF32x3: operands split into TF32 hi + lo (2^-22 relative left out), FP32 accumulation over
+# chunks of 16 reals (at most 16 roundings of 2^-23 = 1.9e-6 relative) added into FP64: 2e-6.
+TF32X3_TOL = 2e-6
 
 
 @pytest.mark.parametrize("ng,K,nf", [(150, 5000, 2), (64, 100, 1), (7, 33, 3), (130, 20000, 1)])
