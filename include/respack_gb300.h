@@ -196,7 +196,7 @@ int rp_check_numeric(rp_ctx* ctx);
  *                 cuda_stream and the call returns without synchronising.
  *   Scratch: a 64 MiB array inside the library, held by every GPU that loads it until the
  *   process exits.  Limits: with kp2 = 2 K rounded up to a multiple of 64,
- *   ng * kp2 <= 12582912 and 2 * ceil(nfreq / 2) * kp2 / 2 <= 1048576; larger requests return RP_ERR_ARG
+ *   ng * kp2 <= 12582912 and 4 * ceil(nfreq / 4) * kp2 / 2 <= 1048576; larger requests return RP_ERR_ARG
  *   before anything is queued.  The first call on a device looks up the array's device address
  *   (once per device); make that first call before any stream capture.  Every call uses the
  *   same array: calls whose work overlaps on the GPU (other streams, other threads) race and

@@ -562,7 +562,7 @@ static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, lon
     const size_t sb = (size_t)ng * tc_kp2(K) * 2;
     int s;
     if ((s = ensure(c, c->s_hi, sb)) || (s = ensure(c, c->s_lo, sb)) ||
-        (s = ensure(c, c->s_w32, (size_t)((nfreq + 1) / 2 * 2) * (tc_kp2(K) / 2) * sizeof(float2))))
+        (s = ensure(c, c->s_w32, (size_t)tc_wrows(nfreq) * (tc_kp2(K) / 2) * sizeof(float2))))
         return s;
     prof_begin(c, 5, st);
     e = launch_split_bf16(M, m32, ldm, col0m, K, ng, c->s_hi.p, c->s_lo.p, st);

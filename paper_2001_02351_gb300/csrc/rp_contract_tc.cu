@@ -12,14 +12,18 @@
 // Tile (one tcgen05.mma M = 128, N = 208, K = 16 per step): the 128 rows of the MMA's A side are
 // built in shared memory from 32 rows M[G'] and the weights of two frequencies
 // (re f0 | im f0 | re f1 | im f1, 32 rows each); the 208 rows of the B side are raw rows M[G],
-// loaded by TMA.  Padding of NG is to multiples of 32 and 208 only, and one load of M[G'] serves
-// two frequencies.  A job is one tile over one accumulation window; the windows of a tile are
-// added into chi with FP64 atomics, so jobs spread evenly over the SMs.
+// loaded by TMA.  Padding of NG is to multiples of 32 and 208 only.  A job is a pair of such
+// tiles (four frequencies, the same 32 G' and the same 208 G) over one accumulation window: each
+// stage of raw rows, the operand every tile re-reads from L2, feeds both tiles, and one load of
+// M[G'] feeds four frequencies.  The two tiles have their own accumulators in tensor memory and
+// their own built buffer, so the builders make one tile while the tensor core multiplies the
+// other.  The windows of a tile are added into chi with FP64 atomics, so jobs spread evenly over
+// the SMs.
 //
-// CTA: 14 warps.  warp 0 = TMA producer (raw rows M[G] of the tile, rows M[G'], the stage's
-// weights of both frequencies; the stages two ahead are prefetched into L2), warp 1 = MMA
-// issuer, warps 2-9 = builders of the weighted rows (scale by w, split, write the
-// 128B-swizzled K-major tile), warps 10-13 = epilogue (tcgen05.ld -> FP64 atomics).
+// CTA: 14 warps.  warp 0 = TMA producer (raw rows M[G], rows M[G'], the stage's weights of the four
+// frequencies; the stages two ahead are prefetched into L2), warp 1 = MMA issuer, warps 2-9 =
+// builders of the weighted rows (scale by w, split, write the 128B-swizzled K-major tile), warps
+// 10-13 = epilogue (tcgen05.ld -> FP64 atomics).
 // Every wait is bounded; a wait that gives up records where in err_flag[1] and the CTA
 // leaves through the common teardown (its copies in flight are waited for, TMEM is freed).
 #include <cuda.h>
@@ -37,14 +41,15 @@ namespace rp {
 #define TC_FLUSH_STAGES 128     // stages per FP32 accumulation window (8192 reals)
 #define TC_THREADS 448
 #define TC_NBUILD 256           // builder threads (warps 2-9); epilogue = warps 10-13
-#define TC_TMEM_COLS 512        // two accumulators of TC_BN columns, 256 apart
+#define TC_TMEM_COLS 512        // the accumulators of the two tiles, TC_BN columns each, 256 apart
+#define TC_NF 4                 // frequencies per job (two tiles of two)
 
 #define TC_RAW_BYTES (TC_BN * TC_BK * 2)          // 26 KB (26 swizzle atoms)
 #define TC_R_BYTES (TC_GN * TC_BK * 2)            // 4 KB
 #define TC_W_BYTES (TC_BK / 2 * 8)                // 32 complex float weights = 256 B
 #define TC_OFF_R (2 * TC_RAW_BYTES)
 #define TC_OFF_W (2 * TC_RAW_BYTES + 2 * TC_R_BYTES)
-#define TC_STAGE_LOAD (2 * TC_RAW_BYTES + 2 * TC_R_BYTES + 2 * TC_W_BYTES)
+#define TC_STAGE_LOAD (2 * TC_RAW_BYTES + 2 * TC_R_BYTES + TC_NF * TC_W_BYTES)
 #define TC_STAGE_BYTES (TC_OFF_W + 1024)          // 61 KB, keeps 1024-B alignment
 #define TC_B_BYTES (TC_BM * TC_BK * 2)            // 16 KB (128 built rows)
 #define TC_SMEM_B0 (TC_NS * TC_STAGE_BYTES)
@@ -146,9 +151,9 @@ __device__ __forceinline__ void split2(float x, float& hi, float& lo) {
 }
 
 struct TcArgs {
-    const float2* w32;      // [2 * nfp][kp2/2] complex float weights of this block (zero padded)
+    const float2* w32;      // [TC_NF * nfq][kp2/2] complex float weights of this block (zero padded)
     long long K;
-    int ng, nf, nfp, nblk, mt, nst, nwin;
+    int ng, nf, nfq, nblk, mt, nst, nwin;
     double2* chi;
     int* err;
 };
@@ -156,6 +161,7 @@ struct TcArgs {
 static_assert(TC_BN % 16 == 0 && TC_BN <= 256 && TC_BN % 32 == 16, "epilogue reads TC_BN in 32- and one 16-column load");
 static_assert(TC_BN <= 256 && 256 + TC_BN <= TC_TMEM_COLS, "two accumulators fit the allocation");
 static_assert(TC_SMEM_TOTAL <= 232448, "shared memory per CTA");
+static_assert(TC_NF * TC_W_BYTES <= TC_STAGE_BYTES - TC_OFF_W, "weights of a stage fit their region");
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_contract_bf16x3(const __grid_constant__ CUtensorMap raw_hi, const __grid_constant__ CUtensorMap raw_lo,
@@ -165,13 +171,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bar0 = sbase + TC_SMEM_BAR;
-    // barriers: full[NS], empty[NS], bready[2], bfree[2], accf[2], acce[2], done
+    // barriers: full[NS], empty[NS], and per tile t: bready, bfree (its built buffer), accf, acce
+    // (its accumulator); done
     auto full = [&](int s) { return bar0 + 8 * s; };
     auto empty = [&](int s) { return bar0 + 8 * (TC_NS + s); };
-    auto bready = [&](int b) { return bar0 + 8 * (2 * TC_NS + b); };
-    auto bfree = [&](int b) { return bar0 + 8 * (2 * TC_NS + 2 + b); };
-    auto accf = [&](int b) { return bar0 + 8 * (2 * TC_NS + 4 + b); };
-    auto acce = [&](int b) { return bar0 + 8 * (2 * TC_NS + 6 + b); };
+    auto bready = [&](int t) { return bar0 + 8 * (2 * TC_NS + t); };
+    auto bfree = [&](int t) { return bar0 + 8 * (2 * TC_NS + 2 + t); };
+    auto accf = [&](int t) { return bar0 + 8 * (2 * TC_NS + 4 + t); };
+    auto acce = [&](int t) { return bar0 + 8 * (2 * TC_NS + 6 + t); };
     const uint32_t done_bar = bar0 + 8 * (2 * TC_NS + 8);
     uint32_t* taddr_slot = (uint32_t*)(smem + TC_SMEM_BAR + 8 * (2 * TC_NS + 9));
 
@@ -181,11 +188,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(full(s), 1);
             mbar_init(empty(s), TC_NBUILD + 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(bready(b), TC_NBUILD);
-            mbar_init(bfree(b), 1);
-            mbar_init(accf(b), 1);
-            mbar_init(acce(b), 128);
+        for (int t = 0; t < 2; ++t) {
+            mbar_init(bready(t), TC_NBUILD);
+            mbar_init(bfree(t), 1);
+            mbar_init(accf(t), 1);
+            mbar_init(acce(t), 128);
         }
         mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -201,17 +208,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *taddr_slot;
 
-    const int ntile = args.nfp * args.nblk * args.mt;
+    const int ntile = args.nfq * args.nblk * args.mt;
     const int njobs = ntile * args.nwin;
     const int nst = args.nst;
     int* err = args.err;
-    // job -> (accumulation window, frequency pair, G' block, G tile); consecutive jobs share a
-    // window.  The last block and tile are moved back to end at ng, so that (for ng >= TC_BN) every
-    // box lies inside the arrays; a block or tile writes only the rows from its own start (nown,
-    // mown) on, so rows covered twice are added once.
-    auto job_tile = [&](int job, int& w0, int& w1, int& fp, int& n0, int& m0, int& nown, int& mown) {
+    // job -> (accumulation window, group of four frequencies, G' block, G tile); consecutive jobs
+    // share a window.  The last block and tile are moved back to end at ng, so that (for ng >=
+    // TC_BN) every box lies inside the arrays; a block or tile writes only the rows from its own
+    // start (nown, mown) on, so rows covered twice are added once.
+    auto job_tile = [&](int job, int& w0, int& w1, int& fq, int& n0, int& m0, int& nown, int& mown) {
         const int win = job / ntile, t = job % ntile;
-        fp = t / (args.nblk * args.mt);
+        fq = t / (args.nblk * args.mt);
         const int r = t % (args.nblk * args.mt);
         nown = (r / args.mt) * TC_GN;
         mown = (r % args.mt) * TC_BN;
@@ -228,12 +235,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bool ok = true;
             const long long kpad = (long long)nst * (TC_BK / 2);
             for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
-                int w0, w1, fp, n0, m0, nown, mown;
-                job_tile(job, w0, w1, fp, n0, m0, nown, mown);
+                int w0, w1, fq, n0, m0, nown, mown;
+                job_tile(job, w0, w1, fq, n0, m0, nown, mown);
                 // L2 prefetch only of boxes that lie inside the arrays
                 const bool pf_raw = m0 + TC_BN <= args.ng, pf_row = n0 + TC_GN <= args.ng;
-                const float2* wrow0 = args.w32 + (size_t)(2 * fp) * kpad;
-                const float2* wrow1 = wrow0 + kpad;
+                const float2* wrow = args.w32 + (size_t)(TC_NF * fq) * kpad;
                 for (int st = w0; st < w1; ++st, ++sg) {
                     const int s = (int)(sg % TC_NS);
                     const uint32_t ph = (uint32_t)((sg / TC_NS) & 1);
@@ -251,8 +257,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (!(ok = mbar_wait(empty(s), ph ^ 1, err, 101))) break;
                     const uint32_t base = sbase + s * TC_STAGE_BYTES;
                     mbar_expect_tx(full(s), TC_STAGE_LOAD);
-                    bulk_load(base + TC_OFF_W, wrow0 + (size_t)st * (TC_BK / 2), TC_W_BYTES, full(s));
-                    bulk_load(base + TC_OFF_W + TC_W_BYTES, wrow1 + (size_t)st * (TC_BK / 2), TC_W_BYTES, full(s));
+#pragma unroll
+                    for (int fi = 0; fi < TC_NF; ++fi)
+                        bulk_load(base + TC_OFF_W + fi * TC_W_BYTES, wrow + (size_t)fi * kpad + (size_t)st * (TC_BK / 2),
+                                  TC_W_BYTES, full(s));
                     const int x = st * TC_BK;
                     tma_load_2d(base, &raw_hi, x, m0, full(s));
                     tma_load_2d(base + TC_RAW_BYTES, &raw_lo, x, m0, full(s));
@@ -270,32 +278,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             long long sg = 0, cg = 0;
             bool ok = true;
             for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x, ++cg) {
-                int w0, w1, fp, n0, m0, nown, mown;
-                job_tile(job, w0, w1, fp, n0, m0, nown, mown);
-                const int ab = (int)(cg & 1);
-                if (!(ok = mbar_wait(acce(ab), (uint32_t)(((cg >> 1) & 1) ^ 1), err, 111))) break;
+                int w0, w1, fq, n0, m0, nown, mown;
+                job_tile(job, w0, w1, fq, n0, m0, nown, mown);
+                // both accumulators drained by the epilogue of the previous job
+                for (int t = 0; t < 2 && ok; ++t)
+                    ok = mbar_wait(acce(t), (uint32_t)((cg & 1) ^ 1), err, 111);
+                if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t d = tmem + (uint32_t)(ab * 256);
                 for (int st = w0; st < w1; ++st, ++sg) {
                     const int s = (int)(sg % TC_NS);
-                    const int bb = (int)(sg & 1);
                     if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 112))) break;
-                    if (!(ok = mbar_wait(bready(bb), (uint32_t)((sg >> 1) & 1), err, 113))) break;
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t g_hi = sbase + s * TC_STAGE_BYTES, g_lo = g_hi + TC_RAW_BYTES;
-                    const uint32_t b_hi = sbase + TC_SMEM_B0 + bb * 2 * TC_B_BYTES, b_lo = b_hi + TC_B_BYTES;
+                    for (int t = 0; t < 2; ++t) {
+                        if (!(ok = mbar_wait(bready(t), (uint32_t)(sg & 1), err, 113))) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t d = tmem + (uint32_t)(t * 256);
+                        const uint32_t b_hi = sbase + TC_SMEM_B0 + t * 2 * TC_B_BYTES, b_lo = b_hi + TC_B_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                        const uint32_t off = kk * 32;
-                        const uint32_t first = (st == w0 && kk == 0) ? 0u : 1u;
-                        mma_bf16(d, sw128_desc(b_hi + off), sw128_desc(g_hi + off), first);
-                        mma_bf16(d, sw128_desc(b_hi + off), sw128_desc(g_lo + off), 1u);
-                        mma_bf16(d, sw128_desc(b_lo + off), sw128_desc(g_hi + off), 1u);
+                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                            const uint32_t off = kk * 32;
+                            const uint32_t first = (st == w0 && kk == 0) ? 0u : 1u;
+                            mma_bf16(d, sw128_desc(b_hi + off), sw128_desc(g_hi + off), first);
+                            mma_bf16(d, sw128_desc(b_hi + off), sw128_desc(g_lo + off), 1u);
+                            mma_bf16(d, sw128_desc(b_lo + off), sw128_desc(g_hi + off), 1u);
+                        }
+                        mma_commit(bfree(t));
                     }
+                    if (!ok) break;
                     mma_commit(empty(s));
-                    mma_commit(bfree(bb));
                 }
-                if (ok) mma_commit(accf(ab));
+                if (ok) {
+                    mma_commit(accf(0));
+                    mma_commit(accf(1));
+                }
             }
             // all issued MMAs complete before teardown
             mma_commit(done_bar);
@@ -303,23 +318,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp < 2 + TC_NBUILD / 32) {
         // ---------------- builders of the weighted rows (TC_NBUILD threads, one 16-B chunk each) ----
-        const int t = threadIdx.x - 64;
-        const int r = t >> 3, c = t & 7;
+        const int tid = threadIdx.x - 64;
+        const int r = tid >> 3, c = tid & 7;
         long long sg = 0;
         bool ok = true;
         for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
-            int w0, w1, fp, n0, m0, nown, mown;
-            job_tile(job, w0, w1, fp, n0, m0, nown, mown);
-            for (int st = w0; st < w1; ++st, ++sg) {
+            int w0, w1, fq, n0, m0, nown, mown;
+            job_tile(job, w0, w1, fq, n0, m0, nown, mown);
+            for (int st = w0; st < w1 && ok; ++st, ++sg) {
                 const int s = (int)(sg % TC_NS);
-                const int bb = (int)(sg & 1);
                 if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 121))) break;
-                if (!(ok = mbar_wait(bfree(bb), (uint32_t)(((sg >> 1) & 1) ^ 1), err, 122))) break;
                 const unsigned char* stage = smem + s * TC_STAGE_BYTES;
                 const unsigned char* rhi = stage + TC_OFF_R;
                 const unsigned char* rlo = rhi + TC_R_BYTES;
-                unsigned char* bhi = smem + TC_SMEM_B0 + bb * 2 * TC_B_BYTES;
-                unsigned char* blo = bhi + TC_B_BYTES;
                 const uint32_t o = sw128_off(r, c);
                 const uint4 vh = *reinterpret_cast<const uint4*>(rhi + o);
                 const uint4 vl = *reinterpret_cast<const uint4*>(rlo + o);
@@ -333,96 +344,104 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mr[i] = hh.x + ll.x;
                     mi[i] = hh.y + ll.y;
                 }
+                for (int t = 0; t < 2; ++t) {
+                    if (!(ok = mbar_wait(bfree(t), (uint32_t)((sg & 1) ^ 1), err, 122))) break;
+                    unsigned char* bhi = smem + TC_SMEM_B0 + t * 2 * TC_B_BYTES;
+                    unsigned char* blo = bhi + TC_B_BYTES;
 #pragma unroll
-                for (int fq = 0; fq < 2; ++fq) {
-                    const float2* ws = reinterpret_cast<const float2*>(stage + TC_OFF_W + fq * TC_W_BYTES);
-                    const float4 w01 = *reinterpret_cast<const float4*>(ws + 4 * c);
-                    const float4 w23 = *reinterpret_cast<const float4*>(ws + 4 * c + 2);
-                    const float wr[4] = {w01.x, w01.z, w23.x, w23.z};
-                    const float wi[4] = {w01.y, w01.w, w23.y, w23.w};
-                    uint32_t reh[4], rel[4], imh[4], iml[4];
+                    for (int fq2 = 0; fq2 < 2; ++fq2) {
+                        const float2* ws =
+                            reinterpret_cast<const float2*>(stage + TC_OFF_W + (2 * t + fq2) * TC_W_BYTES);
+                        const float4 w01 = *reinterpret_cast<const float4*>(ws + 4 * c);
+                        const float4 w23 = *reinterpret_cast<const float4*>(ws + 4 * c + 2);
+                        const float wr[4] = {w01.x, w01.z, w23.x, w23.z};
+                        const float wi[4] = {w01.y, w01.w, w23.y, w23.w};
+                        uint32_t reh[4], rel[4], imh[4], iml[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float P = wr[i] * mr[i] + wi[i] * mi[i];
-                        const float Q = wr[i] * mi[i] - wi[i] * mr[i];
-                        float ph, pl, qh, ql;
-                        split2(P, ph, pl);
-                        split2(Q, qh, ql);
-                        reh[i] = pack_bf16(ph, qh);
-                        rel[i] = pack_bf16(pl, ql);
-                        imh[i] = pack_bf16(-qh, ph);
-                        iml[i] = pack_bf16(-ql, pl);
+                        for (int i = 0; i < 4; ++i) {
+                            const float P = wr[i] * mr[i] + wi[i] * mi[i];
+                            const float Q = wr[i] * mi[i] - wi[i] * mr[i];
+                            float ph, pl, qh, ql;
+                            split2(P, ph, pl);
+                            split2(Q, qh, ql);
+                            reh[i] = pack_bf16(ph, qh);
+                            rel[i] = pack_bf16(pl, ql);
+                            imh[i] = pack_bf16(-qh, ph);
+                            iml[i] = pack_bf16(-ql, pl);
+                        }
+                        const int rre = fq2 * 2 * TC_GN + r, rim = rre + TC_GN;
+                        *reinterpret_cast<uint4*>(bhi + sw128_off(rre, c)) = make_uint4(reh[0], reh[1], reh[2], reh[3]);
+                        *reinterpret_cast<uint4*>(blo + sw128_off(rre, c)) = make_uint4(rel[0], rel[1], rel[2], rel[3]);
+                        *reinterpret_cast<uint4*>(bhi + sw128_off(rim, c)) = make_uint4(imh[0], imh[1], imh[2], imh[3]);
+                        *reinterpret_cast<uint4*>(blo + sw128_off(rim, c)) = make_uint4(iml[0], iml[1], iml[2], iml[3]);
                     }
-                    const int rre = fq * 2 * TC_GN + r, rim = rre + TC_GN;
-                    *reinterpret_cast<uint4*>(bhi + sw128_off(rre, c)) = make_uint4(reh[0], reh[1], reh[2], reh[3]);
-                    *reinterpret_cast<uint4*>(blo + sw128_off(rre, c)) = make_uint4(rel[0], rel[1], rel[2], rel[3]);
-                    *reinterpret_cast<uint4*>(bhi + sw128_off(rim, c)) = make_uint4(imh[0], imh[1], imh[2], imh[3]);
-                    *reinterpret_cast<uint4*>(blo + sw128_off(rim, c)) = make_uint4(iml[0], iml[1], iml[2], iml[3]);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive(bready(t));
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (!ok) break;
                 mbar_arrive(empty(s));
-                mbar_arrive(bready(bb));
             }
         }
     } else {
         // ---------------- epilogue (128 threads, TMEM lanes by warp % 4) ----------------
-        // lane quarter q4: 0 = Re f0, 1 = Im f0, 2 = Re f1, 3 = Im f1; lane = G' - n0
+        // lane quarter q4: 0 = Re f0, 1 = Im f0, 2 = Re f1, 3 = Im f1 of a tile; lane = G' - n0
         const int q4 = warp & 3;
         long long cg = 0;
         bool ok = true;
         double* chi = reinterpret_cast<double*>(args.chi);
         for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x, ++cg) {
-            int w0, w1, fp, n0, m0, nown, mown;
-            job_tile(job, w0, w1, fp, n0, m0, nown, mown);
-            const int f = 2 * fp + (q4 >> 1), comp = q4 & 1;
+            int w0, w1, fq, n0, m0, nown, mown;
+            job_tile(job, w0, w1, fq, n0, m0, nown, mown);
             const int gp = n0 + lane;
-            const bool live = f < args.nf && gp >= nown && gp < args.ng;
-            const int gmin = mown - m0;
-            double* out = chi + (((size_t)f * args.ng + m0) * args.ng + gp) * 2 + comp;
             const size_t ldo = (size_t)args.ng * 2;
-            const int ab = (int)(cg & 1);
-            if (!(ok = mbar_wait(accf(ab), (uint32_t)((cg >> 1) & 1), err, 131))) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * 256);
+            const int gmin = mown - m0;
             const int gmax = min(TC_BN, args.ng - m0);   // columns [gmin, gmax) are this tile's
+            for (int t = 0; t < 2 && ok; ++t) {
+                const int f = TC_NF * fq + 2 * t + (q4 >> 1), comp = q4 & 1;
+                const bool live = f < args.nf && gp >= nown && gp < args.ng;
+                double* out = chi + (((size_t)f * args.ng + m0) * args.ng + gp) * 2 + comp;
+                if (!(ok = mbar_wait(accf(t), (uint32_t)(cg & 1), err, 131))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * 256);
 #pragma unroll 1
-            for (int ch = 0; ch < TC_BN / 32; ++ch) {
-                uint32_t v[32];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-                      "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-                      "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(src + (uint32_t)(ch * 32)));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (live) {
+                for (int ch = 0; ch < TC_BN / 32; ++ch) {
+                    uint32_t v[32];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                        : "r"(src + (uint32_t)(ch * 32)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (live) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (ch * 32 + j >= gmin && ch * 32 + j < gmax)
-                            atomicAdd(out + (size_t)(ch * 32 + j) * ldo, (double)__uint_as_float(v[j]));
+                        for (int j = 0; j < 32; ++j)
+                            if (ch * 32 + j >= gmin && ch * 32 + j < gmax)
+                                atomicAdd(out + (size_t)(ch * 32 + j) * ldo, (double)__uint_as_float(v[j]));
+                    }
                 }
-            }
-            {
-                constexpr int ch = TC_BN / 32;
-                uint32_t v[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15])
-                    : "r"(src + (uint32_t)(ch * 32)));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                mbar_arrive(acce(ab));
-                if (live) {
+                {
+                    constexpr int ch = TC_BN / 32;
+                    uint32_t v[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(src + (uint32_t)(ch * 32)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(acce(t));
+                    if (live) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (ch * 32 + j >= gmin && ch * 32 + j < gmax)
-                            atomicAdd(out + (size_t)(ch * 32 + j) * ldo, (double)__uint_as_float(v[j]));
+                        for (int j = 0; j < 16; ++j)
+                            if (ch * 32 + j >= gmin && ch * 32 + j < gmax)
+                                atomicAdd(out + (size_t)(ch * 32 + j) * ldo, (double)__uint_as_float(v[j]));
+                    }
                 }
             }
         }
@@ -505,6 +524,7 @@ static bool make_map(CUtensorMap* map, void* base, int ng, long long kp2, int ro
 }
 
 long long tc_kp2(long long K) { return ((2 * K + TC_BK - 1) / TC_BK) * TC_BK; }
+int tc_wrows(int nf) { return (nf + TC_NF - 1) / TC_NF * TC_NF; }
 
 cudaError_t launch_split_bf16(const void* M, bool m32, long long ldm, long long col0, long long K, int ng, void* hi,
                               void* lo, cudaStream_t st) {
@@ -525,9 +545,9 @@ cudaError_t launch_split_bf16(const void* M, bool m32, long long ldm, long long 
 cudaError_t launch_weights32(long long K, const double2* w, long long ldw, long long col0, int nf, void* w32,
                              cudaStream_t st) {
     const long long kpad = tc_kp2(K) / 2;
-    const int nfp = (nf + 1) / 2;
-    const long long nw = (long long)2 * nfp * kpad;
-    k_weights32<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(w, ldw, col0, K, nf, 2 * nfp, kpad, (float2*)w32);
+    const int nrow = tc_wrows(nf);
+    const long long nw = (long long)nrow * kpad;
+    k_weights32<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(w, ldw, col0, K, nf, nrow, kpad, (float2*)w32);
     return cudaGetLastError();
 }
 
@@ -548,16 +568,15 @@ cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long lon
         !make_map(&mrow_hi, const_cast<void*>(hi), ng, kp2, TC_GN) ||
         !make_map(&mrow_lo, const_cast<void*>(lo), ng, kp2, TC_GN))
         return cudaErrorInvalidValue;
-    const int nfp = (nf + 1) / 2;
     TcArgs a;
     a.w32 = (const float2*)w32; a.K = K;
-    a.ng = ng; a.nf = nf; a.nfp = nfp;
+    a.ng = ng; a.nf = nf; a.nfq = tc_wrows(nf) / TC_NF;
     a.nblk = (ng + TC_GN - 1) / TC_GN;
     a.mt = (ng + TC_BN - 1) / TC_BN;
     a.nst = (int)(kp2 / TC_BK);
     a.nwin = (a.nst + TC_FLUSH_STAGES - 1) / TC_FLUSH_STAGES;
     a.chi = chi; a.err = err;
-    const long long njobs = (long long)a.nfp * a.nblk * a.mt * a.nwin;
+    const long long njobs = (long long)a.nfq * a.nblk * a.mt * a.nwin;
     if (njobs > 0x7fffffffLL) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_contract_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_TOTAL);
     if (e != cudaSuccess) return e;

@@ -123,9 +123,10 @@ cudaError_t launch_contract_f64(const double2* M, long long ldm, long long K, co
                                 int accumulate, cudaStream_t st);
 // BF16x3 tcgen05 contraction: split, then chi (+)= over the split block (chi zeroed by the caller)
 long long tc_kp2(long long K);
+int tc_wrows(int nf);   // rows of the float weight scratch (frequencies rounded up to whole jobs)
 cudaError_t launch_split_bf16(const void* M, bool m32, long long ldm, long long col0, long long K, int ng,
                               void* hi, void* lo, cudaStream_t st);
-// (w32: scratch of 2 * ceil(nf / 2) * tc_kp2(K) / 2 complex floats)
+// (w32: scratch of tc_wrows(nf) * tc_kp2(K) / 2 complex floats)
 cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, int ng, const double2* w,
                                    long long ldw, long long col0, int nf, void* w32, double2* chi, int* err,
                                    int num_sms, cudaStream_t st);

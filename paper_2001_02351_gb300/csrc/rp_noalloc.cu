@@ -53,7 +53,7 @@ extern "C" int rp_contract_chi0_static(int ng, long long K, int nfreq, const dou
     if (ng < 1 || K < 1 || nfreq < 1 || !M || !w || !chi_out) return RP_ERR_ARG;
     const long long kp2 = rp::tc_kp2(K);
     if ((unsigned long long)ng * (unsigned long long)kp2 * 2ULL > kSplitBytes) return RP_ERR_ARG;
-    if ((unsigned long long)((nfreq + 1) / 2 * 2) * (unsigned long long)(kp2 / 2) * 8ULL > kW32Bytes)
+    if ((unsigned long long)rp::tc_wrows(nfreq) * (unsigned long long)(kp2 / 2) * 8ULL > kW32Bytes)
         return RP_ERR_ARG;
     void* base = nullptr;
     int s = scratch_address(&base);
