@@ -699,7 +699,14 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
             cudaError_t e = cudaFuncSetAttribute(k_pair_x<C, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
             if (e != cudaSuccess) return e;
             const long long nchunk = (npair + PB - 1) / PB;
-            const unsigned grid = (unsigned)std::min<long long>(nchunk, c->num_sms);
+            // as many CTAs per SM as fit: each keeps its own chunk in flight
+            int per_sm = 1;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_x<C, CO>, PX_THREADS, xsm) != cudaSuccess ||
+                per_sm < 1) {
+                cudaGetLastError();
+                per_sm = 1;
+            }
+            const unsigned grid = (unsigned)std::min<long long>(nchunk, (long long)per_sm * c->num_sms);
             k_pair_x<C, CO><<<grid, PX_THREADS, xsm, st>>>(
                 (const C*)c->s_t2.p, npair, N1, ny * nz, nz, efwd[0], P.nset[0], (const int*)P.d_gpos_r.p, P.ng,
                 (typename CT<C>::R)(1.0 / (double)nr), M, ldm, col0);
