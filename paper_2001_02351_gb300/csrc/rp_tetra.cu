@@ -356,17 +356,32 @@ __device__ __noinline__ typename TT<R>::C dd_table_entry(const R (&x)[5], typena
     return dd5_table<R>(x, z, &unused);
 }
 
-// item of the deferred work list: pair t, frequency f, tetrahedron-vertex entry s, pole side,
-// kind (0: near-degenerate set, evaluated in FP64; 1: wide set of the FP32 pass, full table in FP32)
-__device__ __forceinline__ unsigned long long tetra_item(long long t, int f, int s, int side, int kind) {
-    return ((unsigned long long)t << 32) | ((unsigned long long)f << 16) | ((unsigned long long)s << 8) |
-           ((unsigned long long)kind << 1) | (unsigned long long)side;
+#define TT_NEAR 1e-5  // gap below which unmerged nodes make a set near-degenerate
+#define TT_FIELDS 7   // e1 .. e5, centre - D0, spread (negative: near-degenerate set)
+#define TT_FC 4       // frequencies per node-set read
+
+// pole z of side 0 (w + i d, or i(nu + d)) and side 1 (the second term of Eq. Xakqbk)
+__device__ __forceinline__ double2 tetra_pole(const double* __restrict__ freq, int f, int side, int axis,
+                                              int ordering, double delta) {
+    const double wv = freq[f];
+    if (axis == RP_AXIS_REAL)
+        return side == 0 ? make_double2(wv, delta) : make_double2(-wv, ordering == RP_TIME_ORDERED ? delta : -delta);
+    return side == 0 ? make_double2(0.0, wv + delta)
+                     : make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
+}
+
+// Work list of the FP32 pass: one item per (pair t, frequency f) that has node sets too wide for the
+// series, with the mask of those (tetrahedron-vertex entry s, pole side) as bit 2 s + side.
+// x = t << 16 | f, y = mask (48 bits).  Each (t, f) appears at most once, so its pass adds into the
+// weight without atomics.
+__device__ __forceinline__ ulonglong2 tetra_item(long long t, int f, unsigned long long mask) {
+    return make_ulonglong2(((unsigned long long)t << 16) | (unsigned long long)f, mask);
 }
 
 // Append an item to the work list with one counter update per warp (the converged lanes that
 // push take consecutive slots); false when the list is full.
-__device__ __forceinline__ bool queue_push(unsigned long long* queue, unsigned long long qcap,
-                                           unsigned long long* qcount, unsigned long long item) {
+__device__ __forceinline__ bool queue_push(ulonglong2* queue, unsigned long long qcap, unsigned long long* qcount,
+                                           ulonglong2 item) {
     const unsigned mask = __activemask();
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(mask) - 1;
@@ -379,48 +394,70 @@ __device__ __forceinline__ bool queue_push(unsigned long long* queue, unsigned l
     return true;
 }
 
-// Pass over the deferred items: one item per thread, result added to the weight
+// Sum of the divided differences of the entries in `mask` for pair (k, a, o) at frequency f: each
+// node set in FP32 relative to d0 with the full table, or in FP64 when two of its nodes lie closer
+// than TT_NEAR without being merged (the FP32 nodes decide, as in the main pass).
+__device__ double2 deferred_sum(const double* __restrict__ E, int nband, int nocc, int a, int o, int k,
+                                const int* __restrict__ kp, const int* __restrict__ tets,
+                                const int* __restrict__ tetk, const double* __restrict__ freq, int f, int axis,
+                                int ordering, double delta, double da, double dr, double d0,
+                                unsigned long long mask) {
+    double2 sum = make_double2(0.0, 0.0);
+    while (mask) {
+        const int bit = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        const int s = bit >> 1, side = bit & 1;
+        const double2 zd = tetra_pole(freq, f, side, axis, ordering, delta);
+        float xr[5];
+        tetra_nodes_rel32(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], d0, (float)da, (float)dr, xr);
+        bool near = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float g = xr[i + 1] - xr[i];
+            near = near || (g > 0.f && g < (float)TT_NEAR);
+        }
+        double2 r;
+        if (near) {
+            r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, zd);
+        } else {
+            const float2 rf = dd_table_entry<float>(xr, make_float2((float)(zd.x - d0), (float)zd.y));
+            r = make_double2((double)rf.x, (double)rf.y);
+        }
+        sum.x += r.x;
+        sum.y += r.y;
+    }
+    return sum;
+}
+
+// Pass over the work list: one (pair, frequency) per thread, its deferred entries added to the weight
 __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ E, const double* __restrict__ Tw,
                                                      int nband, int nocc, int nemp, int nk,
                                                      const int* __restrict__ kp, const int* __restrict__ tets,
                                                      const int* __restrict__ tetk, const double* __restrict__ freq,
                                                      int axis, int ordering, double delta, double da, double dr,
-                                                     const unsigned long long* __restrict__ queue,
+                                                     const ulonglong2* __restrict__ queue,
                                                      const unsigned long long* __restrict__ qcount,
                                                      unsigned long long qcap, double2* __restrict__ wout) {
     const unsigned long long n = min(*qcount, qcap);
+    const long long K = (long long)nk * nemp * nocc;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long item = queue[i];
-    const long long t = (long long)(item >> 32);
-    const int f = (int)((item >> 16) & 0xFFFF), s = (int)((item >> 8) & 0xFF), side = (int)(item & 1);
-    const int kind = (int)((item >> 1) & 1);
-    const long long K = (long long)nk * nemp * nocc;
-    const int o = (int)(t % nocc);
-    const int a = (int)((t / nocc) % nemp);
-    const int k = (int)(t / ((long long)nocc * nemp));
-    double pref = 2.0 / (double)nk;
-    if (Tw) pref *= 1.0 - Tw[(size_t)kp[k] * nband + nocc + a] * Tw[(size_t)k * nband + o];
-    const double wv = freq[f];
-    double2 zd;
-    if (axis == RP_AXIS_REAL)
-        zd = side == 0 ? make_double2(wv, delta) : make_double2(-wv, ordering == RP_TIME_ORDERED ? delta : -delta);
-    else
-        zd = side == 0 ? make_double2(0.0, wv + delta)
-                       : make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
-    double2 r;
-    if (kind == 0) {
-        r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, zd);
-    } else {
+        const ulonglong2 item = queue[i];
+        const long long t = (long long)(item.x >> 16);
+        const int f = (int)(item.x & 0xFFFF);
+        const int o = (int)(t % nocc);
+        const int a = (int)((t / nocc) % nemp);
+        const int k = (int)(t / ((long long)nocc * nemp));
+        double pref = 2.0 / (double)nk;
+        if (Tw) pref *= 1.0 - Tw[(size_t)kp[k] * nband + nocc + a] * Tw[(size_t)k * nband + o];
         const double d0 = E[(size_t)kp[k] * nband + nocc + a] - E[(size_t)k * nband + o];
-        float xr[5];
-        tetra_nodes_rel32(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], d0, (float)da, (float)dr, xr);
-        const float2 rf = dd_table_entry<float>(xr, make_float2((float)(zd.x - d0), (float)zd.y));
-        r = make_double2((double)rf.x, (double)rf.y);
-    }
-    double* dst = reinterpret_cast<double*>(wout + (size_t)f * K + t);
-    atomicAdd(dst, r.x * pref / 6.0);
-    atomicAdd(dst + 1, r.y * pref / 6.0);
+        const double2 r = deferred_sum(E, nband, nocc, a, o, k, kp, tets, tetk, freq, f, axis, ordering, delta, da,
+                                       dr, d0, item.y);
+        double2* dst = wout + (size_t)f * K + t;
+        double2 v = *dst;
+        v.x += r.x * pref / 6.0;
+        v.y += r.y * pref / 6.0;
+        *dst = v;
     }
 }
 
@@ -431,19 +468,6 @@ __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ 
 // frequencies are then taken TT_FC at a time, each node set read once for the 2 TT_FC poles.
 // With R = float, node sets with two nodes closer than TT_NEAR but not merged (near degeneracy)
 // go to the work list for FP64, and so do (for the FP32 table) the sets too wide for the series.
-#define TT_NEAR 1e-5
-#define TT_FIELDS 7   // e1 .. e5, centre - D0, spread (negative: near-degenerate set)
-#define TT_FC 4
-
-__device__ __forceinline__ double2 tetra_pole(const double* __restrict__ freq, int f, int side, int axis,
-                                              int ordering, double delta) {
-    const double wv = freq[f];
-    if (axis == RP_AXIS_REAL)
-        return side == 0 ? make_double2(wv, delta) : make_double2(-wv, ordering == RP_TIME_ORDERED ? delta : -delta);
-    return side == 0 ? make_double2(0.0, wv + delta)
-                     : make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
-}
-
 template <typename R>
 __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__ E, const double* __restrict__ Tw,
                                                       int nband, int nocc, int nemp, int nk,
@@ -451,8 +475,7 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
                                                       const int* __restrict__ tetk, int nf, int fch,
                                                       const double* __restrict__ freq, int axis, int ordering,
                                                       double delta, double da, double dr,
-                                                      double2* __restrict__ wout,
-                                                      unsigned long long* __restrict__ queue,
+                                                      double2* __restrict__ wout, ulonglong2* __restrict__ queue,
                                                       unsigned long long qcap, unsigned long long* qcount) {
     using C = typename TT<R>::C;
     extern __shared__ __align__(16) unsigned char tsm_raw[];
@@ -497,9 +520,11 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
     const int fend = min(nf, (int)(blockIdx.y + 1) * fch);
     for (int f0 = blockIdx.y * fch; f0 < fend; f0 += TT_FC) {
         C zr[TT_FC][2], acc[TT_FC];
+        unsigned long long dmask[TT_FC];         // entries of each frequency left to the work list
 #pragma unroll
         for (int fi = 0; fi < TT_FC; ++fi) {
             acc[fi] = TT<R>::mk(0, 0);
+            dmask[fi] = 0ull;
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
                 const double2 zd = tetra_pole(freq, min(f0 + fi, nf - 1), side, axis, ordering, delta);
@@ -523,17 +548,12 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
                         acc[fi] = tadd(acc[fi], dd5_series<R>(e, spread, y, r2));
                         continue;
                     }
-                    // a wide set (the series does not apply): in the FP32 pass it goes to the work
-                    // list, for the full table in FP32 there, or in FP64 when two of its nodes
-                    // nearly coincide, so that the warps here stay on the series path
+                    // a wide set (the series does not apply): in the FP32 pass it is marked for the
+                    // work list (the full table in FP32 there, or FP64 when two of its nodes nearly
+                    // coincide), so that the warps here stay on the series path
                     if (sizeof(R) == 4) {
-                        if (queue_push(queue, qcap, qcount, tetra_item(t, f0 + fi, s, side, near ? 0 : 1))) continue;
-                        if (near) {
-                            const double2 r = dd_fp64_entry(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr,
-                                                            tetra_pole(freq, f0 + fi, side, axis, ordering, delta));
-                            acc[fi] = tadd(acc[fi], TT<R>::mk((R)r.x, (R)r.y));
-                            continue;
-                        }
+                        dmask[fi] |= 1ull << (2 * s + side);
+                        continue;
                     }
                     R xr[5];
                     if constexpr (sizeof(R) == 4) {
@@ -550,10 +570,17 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
             }
         }
 #pragma unroll
-        for (int fi = 0; fi < TT_FC; ++fi)
-            if (f0 + fi < fend)
-                wout[(size_t)(f0 + fi) * K + t] =
-                    make_double2((double)acc[fi].x * pref / 6.0, (double)acc[fi].y * pref / 6.0);
+        for (int fi = 0; fi < TT_FC; ++fi) {
+            if (f0 + fi >= fend) break;
+            double2 extra = make_double2(0.0, 0.0);
+            if (sizeof(R) == 4 && dmask[fi] != 0ull &&
+                !queue_push(queue, qcap, qcount, tetra_item(t, f0 + fi, dmask[fi])))
+                // the list is full: the same evaluation here
+                extra = deferred_sum(E, nband, nocc, a, o, k, kp, tets, tetk, freq, f0 + fi, axis, ordering, delta,
+                                     da, dr, d0, dmask[fi]);
+            wout[(size_t)(f0 + fi) * K + t] = make_double2(((double)acc[fi].x + extra.x) * pref / 6.0,
+                                                           ((double)acc[fi].y + extra.y) * pref / 6.0);
+        }
     }
 }
 
@@ -565,13 +592,14 @@ cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double
         cudaError_t e = cudaMemcpyToSymbolAsync(c_bq, bq, sizeof(bq), 0, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
     }
-    // FP64 work list of the FP32 pass: up to 2% of all evaluations (overflow is evaluated in place)
+    // work list of the FP32 pass: up to a quarter of all (pair, frequency) (overflow is evaluated in
+    // place); 16-byte items after a 16-byte counter
     const long long Kp = (long long)c->nk * c->nemp * c->nocc;
-    unsigned long long qcap = (unsigned long long)std::max(1LL << 16, (long long)(0.02 * 48.0 * nf * Kp));
-    if (fp32 && ensure(c, c->s_queue, (qcap + 1) * sizeof(unsigned long long)) != RP_OK)
+    unsigned long long qcap = (unsigned long long)std::max(1LL << 16, (long long)(0.25 * nf * Kp));
+    if (fp32 && ensure(c, c->s_queue, (qcap + 1) * sizeof(ulonglong2)) != RP_OK)
         return cudaErrorMemoryAllocation;
     unsigned long long* qcount = fp32 ? (unsigned long long*)c->s_queue.p : nullptr;
-    unsigned long long* queue = fp32 ? qcount + 1 : nullptr;
+    ulonglong2* queue = fp32 ? (ulonglong2*)c->s_queue.p + 1 : nullptr;
     if (fp32) {
         cudaError_t e = cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st);
         if (e != cudaSuccess) return e;
