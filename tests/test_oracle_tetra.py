@@ -159,3 +159,30 @@ def test_tetrahedra_geometry(micro):
         p = np.where(p - p[0] < -n / 2, p + n, p)
         vols.append(abs(np.linalg.det(p[1:] - p[0])) / 6.0)
     assert np.allclose(vols, 1.0 / 6.0)
+
+
+def test_large_nu_asymptote(micro):
+    """At z = +-i nu with nu far above the transition energies, each divided difference over five
+    nodes tends to 1/(4 (z - c)), c the mean of its nodes (the Taylor series of f_z about c starts
+    with f''''(c)/4! and h_1 of the centred nodes vanishes).  The two poles then give -c / (2 nu^2),
+    so nu^2 x(k) -> -(1/12) sum over the 24 tetrahedra t around k of (sum_v D_v + D_k) / 5, with an
+    error of order (D / nu)^2; for flat bands this is the -2 D of the Lorentzian X."""
+    b = micro.bands
+    q = micro.q[0]
+    kp, _ = umklapp(b.kmesh, q)
+    e_occ = b.energy[:, :micro.nocc]
+    e_emp = b.energy[kp, micro.nocc:micro.nocc + micro.nemp]
+    tets = tetra.tetrahedra(b.kmesh, b.cell.recip)
+    nu = 1.0e3
+    z1, z2 = tetra.poles(np.array([nu]), "imag", 0.0, "time")
+    x = tetra.vertex_weights(e_occ, e_emp, tets, z1, z2, 1e-8, 1e-8)[..., 0]      # [k, a, o]
+    D = e_emp[:, :, None] - e_occ[:, None, :]                                     # [k, a, o]
+    want = np.zeros_like(D)
+    for k in range(D.shape[0]):
+        around = tets[np.any(tets == k, axis=1)]
+        assert len(around) == 24
+        for t in around:
+            want[k] += (D[t].sum(axis=0) + D[k]) / 5.0
+    want *= -1.0 / 12.0
+    assert np.abs(x.imag).max() < 1e-12 * np.abs(x.real).max()
+    assert np.allclose(nu ** 2 * x.real, want, rtol=1e-5, atol=0)
