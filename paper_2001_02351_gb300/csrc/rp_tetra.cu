@@ -140,8 +140,10 @@ __device__ __forceinline__ void esym5(const R (&t)[5], R (&e)[5]) {
     }
 }
 
-// 6 / (m (m-1) (m-2) (m-3)) for m = 0 .. 63 (entries below 4 unused)
+// 6 / (m (m-1) (m-2) (m-3)) for m = 0 .. 63 (entries below 4 unused), and the same values rounded
+// to float for the FP32 table (no double load or conversion per term)
 __constant__ double c_bq[64];
+__constant__ float c_bqf[64];
 
 // Divided difference of order n = m - 1 over the sorted run x[i..j] (m nodes) by the Taylor
 // series about its first node x_i, whose logarithm L = log(z - x_i) is known:
@@ -173,7 +175,8 @@ __device__ typename TT<R>::C dd_run_about_node(const R (&x)[5], int i, int j, ty
         h4 = h3; h3 = h2; h2 = h1; h1 = hk; hk = hn;
         uk = tmul(uk, u);
         const int q = n + k;
-        const C b = q >= 4 ? TT<R>::mk((R)c_bq[q < 64 ? q : 63], 0) : bcoef<R>(q, L);
+        const int qc = q < 64 ? q : 63;
+        const C b = q >= 4 ? TT<R>::mk(sizeof(R) == 4 ? (R)c_bqf[qc] : (R)c_bq[qc], 0) : bcoef<R>(q, L);
         S = tadd(S, tscale(tmul(b, uk), hk));
     }
     C p = TT<R>::mk(1, 0);
@@ -370,6 +373,80 @@ __device__ __forceinline__ double2 tetra_pole(const double* __restrict__ freq, i
                      : make_double2(0.0, ordering == RP_TIME_ORDERED ? -wv + delta : -wv - delta);
 }
 
+// The 2 TT_FC poles of one FP32 node set (nodes c + t, centre c = ct relative to D0), summed by the
+// series of dd5_series with the pole-independent part done once: with sg the half-spread,
+//   h_k(t / r) u^k = h_k(t / sg) w^k,  w = sg conj(y) / r^2,  y = z - c,
+// so the complete homogeneous polynomials of the half-spread-scaled nodes (e: their elementary
+// symmetric polynomials) are formed once for the set, c_k = b_{4+k} h_k, and each pole sums
+// 1/4 + sum_k c_k w^k by Horner and multiplies by 1/y.  The term count of a pole is the bound of
+// dd5_series (rho = sg / r); the poles of one side take the largest count over their frequencies
+// and the converged lanes, so that the four Horner chains of a side run side by side.  A pole whose
+// set is too wide for the series (rho > 1/4) marks bit 2 s + side of its frequency's work-list mask.
+__device__ __forceinline__ void series_poles32(const float (&e)[5], float spread, float ct,
+                                               const float2 (&zr)[TT_FC][2], int nfc, int s,
+                                               float2 (&acc)[TT_FC], unsigned long long (&dmask)[TT_FC]) {
+    constexpr int KM = 13;                        // the count at rho = 1/4
+    const unsigned am = __activemask();
+    const float sg = 0.5f * spread;
+    float2 g[TT_FC][2], w[TT_FC][2];
+    bool use[TT_FC][2];
+    int ksd[2] = {0, 0};
+#pragma unroll
+    for (int fi = 0; fi < TT_FC; ++fi)
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const float yx = zr[fi][side].x - ct, yy = zr[fi][side].y;
+            const float r2 = yx * yx + yy * yy;
+            const bool live = fi < nfc;
+            const bool ok = spread * spread <= (float)(TT_TAU * TT_TAU) * r2;
+            if (live && !ok) dmask[fi] |= 1ull << (2 * s + side);
+            use[fi][side] = live && ok;
+            const float inv = __fdividef(1.f, r2);
+            g[fi][side] = make_float2(yx * inv, -yy * inv);
+            w[fi][side] = make_float2(sg * g[fi][side].x, sg * g[fi][side].y);
+            const float rho2 = sg * sg * inv;
+            int K = 0;
+            if (live && ok && rho2 > 0.f) K = (int)ceilf(__fdividef(-50.5f, __log2f(rho2)));  // rho^K < 2^-25.25
+            K = K < KM ? K : KM;
+            ksd[side] = max(ksd[side], __reduce_max_sync(am, K));
+        }
+    const int ks = max(ksd[0], ksd[1]);
+    float c[KM + 1];
+    float h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f, hk = 1.f;
+#pragma unroll
+    for (int k = 1; k <= KM; ++k) {
+        c[k] = 0.f;
+        if (k <= ks) {
+            const float hn = (e[0] * hk - e[1] * h1) + (e[2] * h2 - e[3] * h3) + e[4] * h4;
+            h4 = h3; h3 = h2; h2 = h1; h1 = hk; hk = hn;
+            c[k] = (float)(6.0 / ((double)(k + 4) * (k + 3) * (k + 2) * (k + 1))) * hn;
+        }
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        float2 P[TT_FC];
+#pragma unroll
+        for (int fi = 0; fi < TT_FC; ++fi) P[fi] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = KM; k >= 1; --k) {
+            if (k > ksd[side]) continue;
+#pragma unroll
+            for (int fi = 0; fi < TT_FC; ++fi) {
+                const float px = P[fi].x + c[k];
+                P[fi] = make_float2(px * w[fi][side].x - P[fi].y * w[fi][side].y,
+                                    px * w[fi][side].y + P[fi].y * w[fi][side].x);
+            }
+        }
+#pragma unroll
+        for (int fi = 0; fi < TT_FC; ++fi) {
+            if (!use[fi][side]) continue;
+            const float sx = 0.25f + P[fi].x, sy = P[fi].y;
+            acc[fi].x += sx * g[fi][side].x - sy * g[fi][side].y;
+            acc[fi].y += sx * g[fi][side].y + sy * g[fi][side].x;
+        }
+    }
+}
+
 // Work list of the FP32 pass: one item per (pair t, frequency f) that has node sets too wide for the
 // series, with the mask of those (tetrahedron-vertex entry s, pole side) as bit 2 s + side.
 // x = t << 16 | f, y = mask (48 bits).  Each (t, f) appears at most once, so its pass adds into the
@@ -450,13 +527,14 @@ __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ 
         const int k = (int)(t / ((long long)nocc * nemp));
         double pref = 2.0 / (double)nk;
         if (Tw) pref *= 1.0 - Tw[(size_t)kp[k] * nband + nocc + a] * Tw[(size_t)k * nband + o];
+        const double ps = pref / 6.0;
         const double d0 = E[(size_t)kp[k] * nband + nocc + a] - E[(size_t)k * nband + o];
         const double2 r = deferred_sum(E, nband, nocc, a, o, k, kp, tets, tetk, freq, f, axis, ordering, delta, da,
                                        dr, d0, item.y);
         double2* dst = wout + (size_t)f * K + t;
         double2 v = *dst;
-        v.x += r.x * pref / 6.0;
-        v.y += r.y * pref / 6.0;
+        v.x += r.x * ps;
+        v.y += r.y * ps;
         *dst = v;
     }
 }
@@ -466,8 +544,9 @@ __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ 
 // FP32 relative to the pair's own transition energy D0 for R = float) and kept in shared memory as
 // their centre, spread and the elementary symmetric polynomials of the centred nodes; the
 // frequencies are then taken TT_FC at a time, each node set read once for the 2 TT_FC poles.
-// With R = float, node sets with two nodes closer than TT_NEAR but not merged (near degeneracy)
-// go to the work list for FP64, and so do (for the FP32 table) the sets too wide for the series.
+// With R = float the centred nodes are stored over the half-spread (for series_poles32), and the
+// node sets too wide for the series go to the work list (there the FP32 table, or FP64 when two
+// of the set's nodes lie closer than TT_NEAR without being merged).
 template <typename R>
 __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__ E, const double* __restrict__ Tw,
                                                       int nband, int nocc, int nemp, int nk,
@@ -490,6 +569,7 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
     const int k = (int)(t / ((long long)nocc * nemp));
     double pref = 2.0 / (double)nk;
     if (Tw) pref *= 1.0 - Tw[(size_t)kp[k] * nband + nocc + a] * Tw[(size_t)k * nband + o];
+    const double ps = pref / 6.0;
     const double d0 = E[(size_t)kp[k] * nband + nocc + a] - E[(size_t)k * nband + o];
     for (int s = 0; s < 24; ++s) {
         R x[5];
@@ -509,9 +589,18 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
             const R g = x[i + 1] - x[i];
             near = near || (g > (R)0 && g < (R)TT_NEAR);
         }
-        const R tc[5] = {(R)-0.5 * spread, x[1] - cd, x[2] - cd, x[3] - cd, (R)0.5 * spread};
         R e[5];
-        esym5<R>(tc, e);
+        if constexpr (sizeof(R) == 4) {
+            // centred nodes over the half-spread sg: -1, t1, t2, t3, 1 (all zero when the set is a point)
+            const float sg = 0.5f * spread;
+            const float si = sg > 0.f ? 1.f / sg : 0.f;
+            const float tc[5] = {sg > 0.f ? -1.f : 0.f, (x[1] - cd) * si, (x[2] - cd) * si, (x[3] - cd) * si,
+                                 sg > 0.f ? 1.f : 0.f};
+            esym5<float>(tc, e);
+        } else {
+            const R tc[5] = {(R)-0.5 * spread, x[1] - cd, x[2] - cd, x[3] - cd, (R)0.5 * spread};
+            esym5<R>(tc, e);
+        }
 #pragma unroll
         for (int j = 0; j < 5; ++j) fld(s, j) = e[j];
         fld(s, 5) = cd;
@@ -537,35 +626,27 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
             const R spread = near ? -sp - (R)1 : sp;
             const R e[5] = {fld(s, 0), fld(s, 1), fld(s, 2), fld(s, 3), fld(s, 4)};
             const R ct = fld(s, 5);
+            if constexpr (sizeof(R) == 4) {
+                series_poles32(e, spread, ct, zr, fend - f0, s, acc, dmask);
+            } else {
 #pragma unroll
-            for (int fi = 0; fi < TT_FC; ++fi) {
-                if (f0 + fi >= fend) break;
+                for (int fi = 0; fi < TT_FC; ++fi) {
+                    if (f0 + fi >= fend) break;
 #pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const C y = TT<R>::mk(zr[fi][side].x - ct, zr[fi][side].y);
-                    const R r2 = y.x * y.x + y.y * y.y;
-                    if (spread * spread <= (R)(TT_TAU * TT_TAU) * r2) {
-                        acc[fi] = tadd(acc[fi], dd5_series<R>(e, spread, y, r2));
-                        continue;
-                    }
-                    // a wide set (the series does not apply): in the FP32 pass it is marked for the
-                    // work list (the full table in FP32 there, or FP64 when two of its nodes nearly
-                    // coincide), so that the warps here stay on the series path
-                    if (sizeof(R) == 4) {
-                        dmask[fi] |= 1ull << (2 * s + side);
-                        continue;
-                    }
-                    R xr[5];
-                    if constexpr (sizeof(R) == 4) {
-                        tetra_nodes_rel32(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], d0, (float)da,
-                                          (float)dr, xr);
-                    } else {
+                    for (int side = 0; side < 2; ++side) {
+                        const C y = TT<R>::mk(zr[fi][side].x - ct, zr[fi][side].y);
+                        const R r2 = y.x * y.x + y.y * y.y;
+                        if (spread * spread <= (R)(TT_TAU * TT_TAU) * r2) {
+                            acc[fi] = tadd(acc[fi], dd5_series<R>(e, spread, y, r2));
+                            continue;
+                        }
                         double xa[5];
+                        R xr[5];
                         tetra_nodes(E, nband, nocc, a, o, kp, tets, tetk[24 * k + s], da, dr, xa);
 #pragma unroll
-                        for (int i = 0; i < 5; ++i) xr[i] = xa[i] - d0;
+                        for (int i = 0; i < 5; ++i) xr[i] = (R)(xa[i] - d0);
+                        acc[fi] = tadd(acc[fi], dd_table_entry<R>(xr, zr[fi][side]));
                     }
-                    acc[fi] = tadd(acc[fi], dd_table_entry<R>(xr, zr[fi][side]));
                 }
             }
         }
@@ -578,8 +659,8 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
                 // the list is full: the same evaluation here
                 extra = deferred_sum(E, nband, nocc, a, o, k, kp, tets, tetk, freq, f0 + fi, axis, ordering, delta,
                                      da, dr, d0, dmask[fi]);
-            wout[(size_t)(f0 + fi) * K + t] = make_double2(((double)acc[fi].x + extra.x) * pref / 6.0,
-                                                           ((double)acc[fi].y + extra.y) * pref / 6.0);
+            wout[(size_t)(f0 + fi) * K + t] = make_double2(((double)acc[fi].x + extra.x) * ps,
+                                                           ((double)acc[fi].y + extra.y) * ps);
         }
     }
 }
@@ -588,8 +669,13 @@ cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double
                          double da, double dr, bool fp32, double2* w, cudaStream_t st) {
     {   // series coefficients 6 / (m (m-1) (m-2) (m-3)) of the resonant path
         static double bq[64];
-        for (int m = 0; m < 64; ++m) bq[m] = m >= 4 ? 6.0 / ((double)m * (m - 1) * (m - 2) * (m - 3)) : 0.0;
+        static float bqf[64];
+        for (int m = 0; m < 64; ++m) {
+            bq[m] = m >= 4 ? 6.0 / ((double)m * (m - 1) * (m - 2) * (m - 3)) : 0.0;
+            bqf[m] = (float)bq[m];
+        }
         cudaError_t e = cudaMemcpyToSymbolAsync(c_bq, bq, sizeof(bq), 0, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_bqf, bqf, sizeof(bqf), 0, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
     }
     // work list of the FP32 pass: up to a quarter of all (pair, frequency) (overflow is evaluated in
