@@ -231,6 +231,20 @@ int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps) {
             }
         }
     }
+    // symmetric window for the FP32 plane kernel (square planes): the narrowest built half-width
+    // that holds every y and z component of the sphere
+    P.zyw = 0;
+    std::vector<int> gpos_w(P.gpos);
+    if (P.fused && P.nfft[1] == P.nfft[2]) {
+        int m = 0;
+        for (int g = 0; g < P.ng; ++g) m = std::max(m, std::max(std::abs(P.gm[3 * g + 1]), std::abs(P.gm[3 * g + 2])));
+        P.zyw = zy_window(P.nfft[1], m);
+        if (P.zyw > 0)
+            for (int g = 0; g < P.ng; ++g) {
+                gpos_w[3 * g + 1] = P.gm[3 * g + 1] + P.zyw;
+                gpos_w[3 * g + 2] = P.gm[3 * g + 2] + P.zyw;
+            }
+    }
     int st;
     // inverse-transform phases exp(+2 pi i m x / N) for m = -lb..lb (Eq. pak on the grid)
     if (c->lb > 0) {
@@ -254,6 +268,7 @@ int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps) {
         }
     }
     if ((st = upload(c, P.d_gpos_r, gpos_r.data(), gpos_r.size() * sizeof(int)))) return st;
+    if ((st = upload(c, P.d_gpos_w, gpos_w.data(), gpos_w.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_gpos, P.gpos.data(), P.gpos.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_kp, P.kp.data(), P.kp.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_g0, P.g0.data(), P.g0.size() * sizeof(int)))) return st;
@@ -809,7 +824,7 @@ void rp_destroy(rp_ctx* c) {
                       &c->s_io3, &c->s_hi, &c->s_lo, &c->s_w32, &c->s_queue, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
                       &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_zmap, &c->plan.d_ymap,
-                      &c->plan.d_gpos_r};
+                      &c->plan.d_gpos_r, &c->plan.d_gpos_w};
     for (DevBuf* b : bufs) release(*b);
     for (int i = 0; i < RP_NSTAGE; ++i)
         for (cudaEvent_t e : c->prof_ev[i]) cudaEventDestroy(e);

@@ -45,6 +45,10 @@ struct QPlan {
     bool masks = false;
     unsigned ymask = 0, zmask = 0;
     DevBuf d_gpos_r;
+    // symmetric residue window of the FP32 plane kernel: half-width zyw (0: none) holding every
+    // sphere value of the y and z axes, and the sphere positions with those components at g + zyw
+    int zyw = 0;
+    DevBuf d_gpos_w;
     // grid of the pair-density transforms: the requested grid, or a smaller cubic one on which
     // the transforms are still exact for this sphere (see plan_q), with its inverse-transform
     // phases exp(+2 pi i m x / N) for m = -lb..lb, [N_axis][2 lb + 1] (FP64 and FP32)
@@ -110,6 +114,8 @@ cudaError_t launch_gather_inverse(rp_ctx* c, int k0, int nkb, bool fp32, cudaStr
 cudaError_t launch_pair_forward(rp_ctx* c, int nkb, double2* M, long long ldm, long long col0,
                                 cudaStream_t st, int* nlaunch);
 // the same in FP32 (for the split-precision tiers), M as complex float
+// half-width of the FP32 plane kernel's residue window for plane length n holding |g| <= m (0: none)
+int zy_window(int n, int m);
 cudaError_t launch_pair_forward32(rp_ctx* c, int nkb, float2* M, long long ldm, long long col0,
                                   cudaStream_t st, int* nlaunch);
 // tetrahedron weights for all pairs: w[nf][K]

@@ -374,12 +374,18 @@ __global__ void __launch_bounds__(256) k_pair_yx(const C* __restrict__ T1, int n
 // warps without a column go straight on to the next band.  One barrier per occupied band.  The
 // y and z axes of T2 hold the residues present on the sphere in ascending order: residue r of
 // an axis is kept when bit r of its mask is set, at position popc(mask & (2^r - 1)).
+// With W > 0 the y and z axes of T2 instead hold the symmetric window of values -W .. W (value g at
+// position g + W; every sphere value lies in it, 2 W + 1 <= N): the stores then have compile-time
+// offsets, no mask is tested per output, and the outputs outside the window are never formed.
 // k_pair_x: the x sum on the sphere points, M[g][col0 + pair] = scale * sum_x Ex[gx][x] T2[...],
 // with T2 streamed through shared memory a few pairs at a time (double-buffered cp.async).
-template <typename C, int N3, int N2>
+template <typename C, int N3, int N2, int W>
 __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const C* __restrict__ u, int nband, int nocc, int nemp, int N1,
-                                                 unsigned zmask, int nz, unsigned ymask, int ny,
+                                                 unsigned zmask, int nz_, unsigned ymask, int ny_,
                                                  C* __restrict__ T2) {
+    static_assert(W == 0 || (2 * W + 1 <= N2 && 2 * W + 1 <= N3), "window wider than the plane");
+    constexpr int NW = 2 * W + 1;
+    const int nz = W > 0 ? NW : nz_, ny = W > 0 ? NW : ny_;
     constexpr int A = 128 / N2;
     constexpr int LD = N3 + 1;
     constexpr int PER = 16 / sizeof(C);                 // complex values per 16-byte load
@@ -420,9 +426,17 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
 #pragma unroll
             for (int z = 0; z < N3; ++z) v[z] = c_conjmul(sa[(ai * N2 + y) * LD + z], sb[y * LD + z]);
             LineFFT<C, N3>::run(v);
+            if constexpr (W > 0) {
 #pragma unroll
-            for (int z = 0; z < N3; ++z)
-                if ((zmask >> z) & 1u) tb[(ai * N2 + y) * nz + __popc(zmask & ((1u << z) - 1u))] = v[z];
+                for (int z = 0; z < N3; ++z) {
+                    const int r = z <= N3 / 2 ? z : z - N3;     // signed value of residue z
+                    if (r >= -W && r <= W) tb[(ai * N2 + y) * NW + r + W] = v[z];
+                }
+            } else {
+#pragma unroll
+                for (int z = 0; z < N3; ++z)
+                    if ((zmask >> z) & 1u) tb[(ai * N2 + y) * nz + __popc(zmask & ((1u << z) - 1u))] = v[z];
+            }
         }
         if (more) {
             C* dst = so + ((o + 1) & 1) * N2 * LD;
@@ -444,9 +458,17 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
             LineFFT<C, N2>::run(v);
             const size_t pair = ((size_t)kl * nemp + a0 + q) * nocc + o;
             C* dst = T2 + (pair * N1 + x) * nyz + iz;
+            if constexpr (W > 0) {
 #pragma unroll
-            for (int yy = 0; yy < N2; ++yy)
-                if ((ymask >> yy) & 1u) dst[__popc(ymask & ((1u << yy) - 1u)) * nz] = v[yy];
+                for (int yy = 0; yy < N2; ++yy) {
+                    const int r = yy <= N2 / 2 ? yy : yy - N2;
+                    if (r >= -W && r <= W) dst[(r + W) * NW] = v[yy];
+                }
+            } else {
+#pragma unroll
+                for (int yy = 0; yy < N2; ++yy)
+                    if ((ymask >> yy) & 1u) dst[__popc(ymask & ((1u << yy) - 1u)) * nz] = v[yy];
+            }
         }
     }
 }
@@ -529,28 +551,66 @@ __global__ void __launch_bounds__(PX_THREADS) k_pair_x(const C* __restrict__ T2,
     cp_async_wait<0>();
 }
 
-template <typename C, int N>
+template <typename C, int N, int W>
 static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int N1, unsigned zmask, int nz,
                         unsigned ymask, int ny, C* T2, cudaStream_t st) {
     constexpr int A = 128 / N;
+    if (W > 0) nz = ny = 2 * W + 1;
     const size_t smem = sizeof(C) * ((size_t)(A + 2) * N * (N + 1) + (size_t)2 * A * N * nz);
     if (smem > 200 * 1024) return false;
-    if (cudaFuncSetAttribute(k_pair_zy<C, N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_pair_zy<C, N, N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return false;
     dim3 grid(N1, (nemp + A - 1) / A, nkb);
-    k_pair_zy<C, N, N><<<grid, 128, smem, st>>>(u, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2);
+    k_pair_zy<C, N, N, W><<<grid, 128, smem, st>>>(u, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2);
     return true;
 }
 
-// plane-wise path for square planes N2 == N3 of a supported length
+// half-widths of the symmetric residue windows the FP32 plane kernel is built for, per plane
+// length 16, 24, 32 (ascending; the plan takes the narrowest that holds the sphere)
+static constexpr int kZyWin[3][4] = {{2, 3, 5, 7}, {3, 5, 7, 11}, {5, 7, 11, 15}};
+
+int zy_window(int n, int m) {
+    const int i = n == 16 ? 0 : n == 24 ? 1 : n == 32 ? 2 : -1;
+    if (i < 0) return 0;
+    for (int w : kZyWin[i])
+        if (w >= m) return w;
+    return 0;
+}
+
+template <int N>
+static bool launch_zy_win(int w, const float2* u, int nkb, int nband, int nocc, int nemp, int N1, float2* T2,
+                          cudaStream_t st) {
+    constexpr int i = N == 16 ? 0 : N == 24 ? 1 : 2;
+    if (w == kZyWin[i][0]) return launch_zy_n<float2, N, kZyWin[i][0]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
+    if (w == kZyWin[i][1]) return launch_zy_n<float2, N, kZyWin[i][1]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
+    if (w == kZyWin[i][2]) return launch_zy_n<float2, N, kZyWin[i][2]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
+    if (w == kZyWin[i][3]) return launch_zy_n<float2, N, kZyWin[i][3]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
+    return false;
+}
+
+// plane-wise path for square planes N2 == N3 of a supported length: the residue masks, or (FP32
+// lines, w > 0) the symmetric window of half-width w
 template <typename C>
-static bool launch_zy(int n2, int n3, const C* u, int nkb, int nband, int nocc, int nemp, int N1, unsigned zmask,
-                      int nz, unsigned ymask, int ny, C* T2, cudaStream_t st) {
+static bool launch_zy(int n2, int n3, int w, const C* u, int nkb, int nband, int nocc, int nemp, int N1,
+                      unsigned zmask, int nz, unsigned ymask, int ny, C* T2, cudaStream_t st) {
     if (n2 != n3) return false;
+    if constexpr (sizeof(C) == 8) {
+        if (w > 0) {
+            switch (n3) {
+                case 16: return launch_zy_win<16>(w, u, nkb, nband, nocc, nemp, N1, T2, st);
+                case 24: return launch_zy_win<24>(w, u, nkb, nband, nocc, nemp, N1, T2, st);
+                case 32: return launch_zy_win<32>(w, u, nkb, nband, nocc, nemp, N1, T2, st);
+                default: return false;
+            }
+        }
+    } else {
+        if (w > 0) return false;
+    }
     switch (n3) {
-        case 16: return launch_zy_n<C, 16>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
-        case 24: return launch_zy_n<C, 24>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
-        case 32: return launch_zy_n<C, 32>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
+        case 16: return launch_zy_n<C, 16, 0>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
+        case 24: return launch_zy_n<C, 24, 0>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
+        case 32: return launch_zy_n<C, 32, 0>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
         default: return false;
     }
 }
@@ -687,15 +747,19 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
     const int ny = P.nset[1], nz = P.nset[2];
     const long long nr = c->plan.nr;
     const int bs = 256;
-    // plane-wise path: z and y transforms on chip, then the x sum on the sphere points
+    // plane-wise path: z and y transforms on chip, then the x sum on the sphere points; FP32 lines
+    // use the symmetric residue window when the plan found one
     {
+        const int w = sizeof(C) == 8 ? P.zyw : 0;
+        const int wy = w > 0 ? 2 * w + 1 : ny, wz = w > 0 ? 2 * w + 1 : nz;
         const long long npair = (long long)nkb * c->nemp * c->nocc;
-        const size_t t2 = (size_t)npair * N1 * ny * nz * sizeof(C);
+        const size_t t2 = (size_t)npair * N1 * wy * wz * sizeof(C);
         constexpr int PB = PairX<C>::PB;
-        const size_t xsm = ((size_t)2 * PB * N1 * ny * nz + (size_t)P.nset[0] * N1 + (size_t)P.ng * PB) * sizeof(C);
-        if (P.fused && P.masks && xsm <= 200 * 1024 && t2 <= (size_t)16 << 30 && ensure(c, c->s_t2, t2) == RP_OK &&
-            launch_zy<C>(N2, N3, (const C*)c->s_u.p, nkb, c->nband, c->nocc, c->nemp, N1, P.zmask, nz, P.ymask, ny,
-                         (C*)c->s_t2.p, st)) {
+        const size_t xsm = ((size_t)2 * PB * N1 * wy * wz + (size_t)P.nset[0] * N1 + (size_t)P.ng * PB) * sizeof(C);
+        if (P.fused && (w > 0 || P.masks) && xsm <= 200 * 1024 && t2 <= (size_t)16 << 30 &&
+            ensure(c, c->s_t2, t2) == RP_OK &&
+            launch_zy<C>(N2, N3, w, (const C*)c->s_u.p, nkb, c->nband, c->nocc, c->nemp, N1, P.zmask, nz, P.ymask,
+                         ny, (C*)c->s_t2.p, st)) {
             cudaError_t e = cudaFuncSetAttribute(k_pair_x<C, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
             if (e != cudaSuccess) return e;
             const long long nchunk = (npair + PB - 1) / PB;
@@ -708,7 +772,8 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
             }
             const unsigned grid = (unsigned)std::min<long long>(nchunk, (long long)per_sm * c->num_sms);
             k_pair_x<C, CO><<<grid, PX_THREADS, xsm, st>>>(
-                (const C*)c->s_t2.p, npair, N1, ny * nz, nz, efwd[0], P.nset[0], (const int*)P.d_gpos_r.p, P.ng,
+                (const C*)c->s_t2.p, npair, N1, wy * wz, wz, efwd[0], P.nset[0],
+                (const int*)(w > 0 ? P.d_gpos_w.p : P.d_gpos_r.p), P.ng,
                 (typename CT<C>::R)(1.0 / (double)nr), M, ldm, col0);
             *nlaunch += 2;
             return cudaGetLastError();
