@@ -231,19 +231,23 @@ int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps) {
             }
         }
     }
-    // symmetric window for the FP32 plane kernel (square planes): the narrowest built half-width
-    // that holds every y and z component of the sphere
+    // symmetric window for the FP32 pair kernels (cubic grids): the narrowest built half-width
+    // that holds every component of the sphere
     P.zyw = 0;
-    std::vector<int> gpos_w(P.gpos);
-    if (P.fused && P.nfft[1] == P.nfft[2]) {
+    std::vector<int> gpos_w(P.gpos), colg;
+    if (P.fused && P.nfft[0] == P.nfft[1] && P.nfft[1] == P.nfft[2]) {
         int m = 0;
-        for (int g = 0; g < P.ng; ++g) m = std::max(m, std::max(std::abs(P.gm[3 * g + 1]), std::abs(P.gm[3 * g + 2])));
+        for (int g = 0; g < 3 * P.ng; ++g) m = std::max(m, std::abs(P.gm[g]));
         P.zyw = zy_window(P.nfft[1], m);
-        if (P.zyw > 0)
+        if (P.zyw > 0) {
+            const int W = P.zyw, NW = 2 * W + 1;
+            colg.assign((size_t)NW * NW * NW, -1);
             for (int g = 0; g < P.ng; ++g) {
-                gpos_w[3 * g + 1] = P.gm[3 * g + 1] + P.zyw;
-                gpos_w[3 * g + 2] = P.gm[3 * g + 2] + P.zyw;
+                gpos_w[3 * g + 1] = P.gm[3 * g + 1] + W;
+                gpos_w[3 * g + 2] = P.gm[3 * g + 2] + W;
+                colg[(size_t)(P.gm[3 * g] + W) * NW * NW + (P.gm[3 * g + 1] + W) * NW + P.gm[3 * g + 2] + W] = g;
             }
+        }
     }
     int st;
     // inverse-transform phases exp(+2 pi i m x / N) for m = -lb..lb (Eq. pak on the grid)
@@ -269,6 +273,7 @@ int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps) {
     }
     if ((st = upload(c, P.d_gpos_r, gpos_r.data(), gpos_r.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_gpos_w, gpos_w.data(), gpos_w.size() * sizeof(int)))) return st;
+    if (!colg.empty() && (st = upload(c, P.d_colg, colg.data(), colg.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_gpos, P.gpos.data(), P.gpos.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_kp, P.kp.data(), P.kp.size() * sizeof(int)))) return st;
     if ((st = upload(c, P.d_g0, P.g0.data(), P.g0.size() * sizeof(int)))) return st;
@@ -824,7 +829,7 @@ void rp_destroy(rp_ctx* c) {
                       &c->s_io3, &c->s_hi, &c->s_lo, &c->s_w32, &c->s_queue, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
                       &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_zmap, &c->plan.d_ymap,
-                      &c->plan.d_gpos_r, &c->plan.d_gpos_w};
+                      &c->plan.d_gpos_r, &c->plan.d_gpos_w, &c->plan.d_colg};
     for (DevBuf* b : bufs) release(*b);
     for (int i = 0; i < RP_NSTAGE; ++i)
         for (cudaEvent_t e : c->prof_ev[i]) cudaEventDestroy(e);

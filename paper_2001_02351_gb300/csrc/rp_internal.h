@@ -45,10 +45,12 @@ struct QPlan {
     bool masks = false;
     unsigned ymask = 0, zmask = 0;
     DevBuf d_gpos_r;
-    // symmetric residue window of the FP32 plane kernel: half-width zyw (0: none) holding every
-    // sphere value of the y and z axes, and the sphere positions with those components at g + zyw
+    // symmetric residue window of the FP32 pair kernels (cubic grids): half-width zyw (0: none)
+    // holding every sphere component on all three axes; the sphere positions with the y and z
+    // components at g + zyw, and the sphere index of each window point (gx, gy, gz) as
+    // colg[gx + zyw][(gy + zyw) (2 zyw + 1) + gz + zyw] (-1 off the sphere)
     int zyw = 0;
-    DevBuf d_gpos_w;
+    DevBuf d_gpos_w, d_colg;
     // grid of the pair-density transforms: the requested grid, or a smaller cubic one on which
     // the transforms are still exact for this sphere (see plan_q), with its inverse-transform
     // phases exp(+2 pi i m x / N) for m = -lb..lb, [N_axis][2 lb + 1] (FP64 and FP32)

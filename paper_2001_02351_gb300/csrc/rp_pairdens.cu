@@ -551,6 +551,71 @@ __global__ void __launch_bounds__(PX_THREADS) k_pair_x(const C* __restrict__ T2,
     cp_async_wait<0>();
 }
 
+// x read-out for the windowed T2 (FP32 lines, half-width W on all three axes): one thread per
+// (pair, yz point of the window) loads the point's N1 values along x (consecutive threads on
+// consecutive points, so each x plane is read coalesced), transforms them in registers (the same
+// +i line transform as z and y) and parks the outputs that lie on the sphere (colg) in shared
+// memory; then the block writes its PB pairs as M[g][col0 + pair], PB consecutive columns per row.
+template <int W>
+struct PairXW {
+    static constexpr int NW = 2 * W + 1, NC = NW * NW;
+    static constexpr int TPP = (NC + 31) / 32 * 32;             // threads per pair
+    static constexpr int PB = TPP >= 256 ? 1 : 256 / TPP;       // pairs per block
+    static constexpr int THREADS = PB * TPP;
+};
+
+template <int N, int W, typename CO>
+__global__ void __launch_bounds__(PairXW<W>::THREADS) k_pair_x_w(const float2* __restrict__ T2, long long npair,
+                                                                const int* __restrict__ colg, int ng, float scale,
+                                                                CO* __restrict__ M, long long ldm, long long col0) {
+    using X = PairXW<W>;
+    static_assert(2 * W + 1 <= N, "window wider than the axis");
+    extern __shared__ __align__(16) unsigned char sm_xw[];
+    float2* xo = reinterpret_cast<float2*>(sm_xw);            // [ng][PB]
+    const int j = threadIdx.x / X::TPP, c = threadIdx.x % X::TPP;
+    const long long p0 = (long long)blockIdx.x * X::PB, p = p0 + j;
+    if (p < npair && c < X::NC) {
+        float2 v[N];
+        const float2* src = T2 + (size_t)p * N * X::NC + c;
+#pragma unroll
+        for (int x = 0; x < N; ++x) v[x] = __ldg(src + (size_t)x * X::NC);
+        LineFFT<float2, N>::run(v);
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            const int gx = r <= N / 2 ? r : r - N;                 // signed value of residue r
+            if (gx >= -W && gx <= W) {
+                const int g = __ldg(colg + (gx + W) * X::NC + c);
+                if (g >= 0) xo[g * X::PB + j] = make_float2(v[r].x * scale, v[r].y * scale);
+            }
+        }
+    }
+    __syncthreads();
+    const int np = (int)min((long long)X::PB, npair - p0);
+    for (int e = threadIdx.x; e < ng * np; e += X::THREADS) {
+        const int g = e / np, jj = e % np;
+        const float2 v = xo[g * X::PB + jj];
+        M[(size_t)g * ldm + col0 + p0 + jj] = CT<CO>::make((typename CT<CO>::R)v.x, (typename CT<CO>::R)v.y);
+    }
+}
+
+template <int N, int W, typename CO>
+static bool launch_x_w_n(const float2* T2, long long npair, const int* colg, int ng, float scale, CO* M, long long ldm,
+                         long long col0, cudaStream_t st) {
+    using X = PairXW<W>;
+    if constexpr (X::TPP > 256) {       // wider windows: not built (k_pair_x reads the same layout)
+        return false;
+    } else {
+        const size_t smem = (size_t)ng * X::PB * sizeof(float2);
+        if (smem > 200 * 1024) return false;
+        if (cudaFuncSetAttribute(k_pair_x_w<N, W, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return false;
+        const long long nblk = (npair + X::PB - 1) / X::PB;
+        k_pair_x_w<N, W, CO><<<(unsigned)nblk, X::THREADS, smem, st>>>(T2, npair, colg, ng, scale, M, ldm, col0);
+        return true;
+    }
+}
+
 template <typename C, int N, int W>
 static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int N1, unsigned zmask, int nz,
                         unsigned ymask, int ny, C* T2, cudaStream_t st) {
@@ -587,6 +652,30 @@ static bool launch_zy_win(int w, const float2* u, int nkb, int nband, int nocc, 
     if (w == kZyWin[i][2]) return launch_zy_n<float2, N, kZyWin[i][2]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
     if (w == kZyWin[i][3]) return launch_zy_n<float2, N, kZyWin[i][3]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
     return false;
+}
+
+template <int N, typename CO>
+static bool launch_x_win_n(int w, const float2* T2, long long npair, const int* colg, int ng, float scale, CO* M,
+                           long long ldm, long long col0, cudaStream_t st) {
+    constexpr int i = N == 16 ? 0 : N == 24 ? 1 : 2;
+    if (w == kZyWin[i][0]) return launch_x_w_n<N, kZyWin[i][0], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
+    if (w == kZyWin[i][1]) return launch_x_w_n<N, kZyWin[i][1], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
+    if (w == kZyWin[i][2]) return launch_x_w_n<N, kZyWin[i][2], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
+    if (w == kZyWin[i][3]) return launch_x_w_n<N, kZyWin[i][3], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
+    return false;
+}
+
+// x read-out of the windowed T2 by line transforms (false: not built for this window; the caller
+// then uses k_pair_x on the same layout)
+template <typename CO>
+static bool launch_x_win(int n, int w, const float2* T2, long long npair, const int* colg, int ng, float scale,
+                         CO* M, long long ldm, long long col0, cudaStream_t st) {
+    switch (n) {
+        case 16: return launch_x_win_n<16, CO>(w, T2, npair, colg, ng, scale, M, ldm, col0, st);
+        case 24: return launch_x_win_n<24, CO>(w, T2, npair, colg, ng, scale, M, ldm, col0, st);
+        case 32: return launch_x_win_n<32, CO>(w, T2, npair, colg, ng, scale, M, ldm, col0, st);
+        default: return false;
+    }
 }
 
 // plane-wise path for square planes N2 == N3 of a supported length: the residue masks, or (FP32
@@ -760,6 +849,13 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
             ensure(c, c->s_t2, t2) == RP_OK &&
             launch_zy<C>(N2, N3, w, (const C*)c->s_u.p, nkb, c->nband, c->nocc, c->nemp, N1, P.zmask, nz, P.ymask,
                          ny, (C*)c->s_t2.p, st)) {
+            if constexpr (sizeof(C) == 8) {
+                if (w > 0 && launch_x_win<CO>(N1, w, (const float2*)c->s_t2.p, npair, (const int*)P.d_colg.p, P.ng,
+                                              (float)(1.0 / (double)nr), M, ldm, col0, st)) {
+                    *nlaunch += 2;
+                    return cudaGetLastError();
+                }
+            }
             cudaError_t e = cudaFuncSetAttribute(k_pair_x<C, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
             if (e != cudaSuccess) return e;
             const long long nchunk = (npair + PB - 1) / PB;
