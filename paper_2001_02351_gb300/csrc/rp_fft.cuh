@@ -89,6 +89,24 @@ __device__ __forceinline__ C twiddle() {
     return Cx<C>::mk((R)c, (R)s);
 }
 
+// a * W_N^E; the quarter turns (1, i, -1, -i) are exact swaps and sign changes, so they cost no
+// multiplication by a literal zero or one
+template <typename C, int N, int E>
+__device__ __forceinline__ C tw_mul(C a) {
+    constexpr int r = ((E % N) + N) % N;
+    if constexpr (r == 0) {
+        return a;
+    } else if constexpr (4 * r == N) {
+        return Cx<C>::mk(-a.y, a.x);
+    } else if constexpr (2 * r == N) {
+        return Cx<C>::mk(-a.x, -a.y);
+    } else if constexpr (4 * r == 3 * N) {
+        return Cx<C>::mk(a.y, -a.x);
+    } else {
+        return c_mul(a, twiddle<C, N, E>());
+    }
+}
+
 template <int N>
 struct Radix {
     static constexpr int value = (N % 4 == 0 && N > 4) ? 4 : (N % 3 == 0 ? 3 : (N % 2 == 0 ? 2 : N));
@@ -134,9 +152,9 @@ struct LineFFT {
         if constexpr (K < M) {
             C t[R];
             t[0] = sub[0][K];
-            t[1] = c_mul(sub[1][K], twiddle<C, N, K>());
-            if constexpr (R > 2) t[2] = c_mul(sub[2][K], twiddle<C, N, 2 * K>());
-            if constexpr (R > 3) t[3] = c_mul(sub[3][K], twiddle<C, N, 3 * K>());
+            t[1] = tw_mul<C, N, K>(sub[1][K]);
+            if constexpr (R > 2) t[2] = tw_mul<C, N, 2 * K>(sub[2][K]);
+            if constexpr (R > 3) t[3] = tw_mul<C, N, 3 * K>(sub[3][K]);
             small_dft<C>(t);
 #pragma unroll
             for (int q = 0; q < R; ++q) x[K + M * q] = t[q];

@@ -379,6 +379,16 @@ __global__ void __launch_bounds__(256) k_pair_yx(const C* __restrict__ T1, int n
 // offsets, no mask is tested per output, and the outputs outside the window are never formed.
 // k_pair_x: the x sum on the sphere points, M[g][col0 + pair] = scale * sum_x Ex[gx][x] T2[...],
 // with T2 streamed through shared memory a few pairs at a time (double-buffered cp.async).
+// shared-memory layout of k_pair_zy: planes [N2][LD] (FP32 lines: LD even, so a row is read with
+// 16-byte loads, conflict-free for N = 16, 24, 32) and the z-transformed lines [2][A][N2][nz]
+// (nz = 2 W + 1 with a window); at N = 24, W = 5 four CTAs fit an SM
+template <typename C, int N>
+struct ZyLayout {
+    static constexpr int A = 128 / N;
+    static constexpr int LD = sizeof(C) == 8 ? N + 2 : N + 1;
+    static size_t smem(int nz) { return sizeof(C) * ((size_t)(A + 2) * N * LD + (size_t)2 * A * N * nz); }
+};
+
 template <typename C, int N3, int N2, int W>
 __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const C* __restrict__ u, int nband, int nocc, int nemp, int N1,
                                                  unsigned zmask, int nz_, unsigned ymask, int ny_,
@@ -386,8 +396,10 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
     static_assert(W == 0 || (2 * W + 1 <= N2 && 2 * W + 1 <= N3), "window wider than the plane");
     constexpr int NW = 2 * W + 1;
     const int nz = W > 0 ? NW : nz_, ny = W > 0 ? NW : ny_;
-    constexpr int A = 128 / N2;
-    constexpr int LD = N3 + 1;
+    static_assert(N2 == N3, "square planes");
+    using L = ZyLayout<C, N3>;
+    constexpr int A = L::A;
+    constexpr int LD = L::LD;
     constexpr int PER = 16 / sizeof(C);                 // complex values per 16-byte load
     constexpr int NE = N2 * N3 / PER;                   // 16-byte pieces of a plane
     constexpr int NV = (NE + 127) / 128;                // pieces per thread (the last one guarded)
@@ -423,8 +435,19 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
         }
         if (ai < na) {
             C v[N3];
+            if constexpr (sizeof(C) == 8) {
+                const float4* ra = reinterpret_cast<const float4*>(sa + (ai * N2 + y) * LD);
+                const float4* rb = reinterpret_cast<const float4*>(sb + y * LD);
 #pragma unroll
-            for (int z = 0; z < N3; ++z) v[z] = c_conjmul(sa[(ai * N2 + y) * LD + z], sb[y * LD + z]);
+                for (int z2 = 0; z2 < N3 / 2; ++z2) {
+                    const float4 p = ra[z2], q = rb[z2];
+                    v[2 * z2] = c_conjmul(make_float2(p.x, p.y), make_float2(q.x, q.y));
+                    v[2 * z2 + 1] = c_conjmul(make_float2(p.z, p.w), make_float2(q.z, q.w));
+                }
+            } else {
+#pragma unroll
+                for (int z = 0; z < N3; ++z) v[z] = c_conjmul(sa[(ai * N2 + y) * LD + z], sb[y * LD + z]);
+            }
             LineFFT<C, N3>::run(v);
             if constexpr (W > 0) {
 #pragma unroll
@@ -619,9 +642,9 @@ static bool launch_x_w_n(const float2* T2, long long npair, const int* colg, int
 template <typename C, int N, int W>
 static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int N1, unsigned zmask, int nz,
                         unsigned ymask, int ny, C* T2, cudaStream_t st) {
-    constexpr int A = 128 / N;
+    constexpr int A = ZyLayout<C, N>::A;
     if (W > 0) nz = ny = 2 * W + 1;
-    const size_t smem = sizeof(C) * ((size_t)(A + 2) * N * (N + 1) + (size_t)2 * A * N * nz);
+    const size_t smem = ZyLayout<C, N>::smem(nz);
     if (smem > 200 * 1024) return false;
     if (cudaFuncSetAttribute(k_pair_zy<C, N, N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
