@@ -360,7 +360,8 @@ __device__ __noinline__ typename TT<R>::C dd_table_entry(const R (&x)[5], typena
 }
 
 #define TT_NEAR 1e-5  // gap below which unmerged nodes make a set near-degenerate
-#define TT_FIELDS 7   // e1 .. e5, centre - D0, spread (negative: near-degenerate set)
+#define TT_FIELDS 7   // FP64 node sets: e1 .. e5, centre - D0, spread (negative: near-degenerate set)
+#define TT_FIELDS32 5 // FP32 node sets: the three inner centred nodes over the half-spread, centre - D0, spread
 #define TT_FC 4       // frequencies per node-set read
 
 // pole z of side 0 (w + i d, or i(nu + d)) and side 1 (the second term of Eq. Xakqbk)
@@ -541,14 +542,16 @@ __global__ void __launch_bounds__(128) k_tetra_fixup(const double* __restrict__ 
 
 // Weights for one (k, a, o) per thread and a chunk of frequencies per grid row.  The 24
 // tetrahedron-vertex node sets are prepared once (sorted, merged, centred; FP64 for R = double,
-// FP32 relative to the pair's own transition energy D0 for R = float) and kept in shared memory as
-// their centre, spread and the elementary symmetric polynomials of the centred nodes; the
-// frequencies are then taken TT_FC at a time, each node set read once for the 2 TT_FC poles.
-// With R = float the centred nodes are stored over the half-spread (for series_poles32), and the
-// node sets too wide for the series go to the work list (there the FP32 table, or FP64 when two
-// of the set's nodes lie closer than TT_NEAR without being merged).
+// FP32 relative to the pair's own transition energy D0 for R = float) and kept in shared memory:
+// for R = double their centre, spread and the elementary symmetric polynomials of the centred
+// nodes; for R = float (five fields, which with 168 registers lets six 64-thread blocks share an
+// SM) their centre, spread and the three inner centred nodes over the half-spread, whose
+// symmetric polynomials (with the outer nodes -1 and 1) are formed again at each read.  The
+// frequencies are then taken TT_FC at a time, each node set read once for the 2 TT_FC poles.  With
+// R = float the node sets too wide for the series go to the work list (there the FP32 table, or
+// FP64 when two of the set's nodes lie closer than TT_NEAR without being merged).
 template <typename R>
-__global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__ E, const double* __restrict__ Tw,
+__global__ void __launch_bounds__(64, sizeof(R) == 4 ? 6 : 1) k_tetra_weights(const double* __restrict__ E, const double* __restrict__ Tw,
                                                       int nband, int nocc, int nemp, int nk,
                                                       const int* __restrict__ kp, const int* __restrict__ tets,
                                                       const int* __restrict__ tetk, int nf, int fch,
@@ -560,7 +563,8 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
     extern __shared__ __align__(16) unsigned char tsm_raw[];
     R* tsm = reinterpret_cast<R*>(tsm_raw);
     const int bd = blockDim.x, tid = threadIdx.x;
-    auto fld = [&](int s, int f) -> R& { return tsm[(s * TT_FIELDS + f) * bd + tid]; };
+    constexpr int NFLD = sizeof(R) == 4 ? TT_FIELDS32 : TT_FIELDS;
+    auto fld = [&](int s, int f) -> R& { return tsm[(s * NFLD + f) * bd + tid]; };
     const long long t = (long long)blockIdx.x * bd + tid;
     const long long K = (long long)nk * nemp * nocc;
     if (t >= K) return;
@@ -583,28 +587,30 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
         }
         const R cd = (R)0.5 * (x[0] + x[4]);
         const R spread = x[4] - x[0];
-        bool near = false;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const R g = x[i + 1] - x[i];
-            near = near || (g > (R)0 && g < (R)TT_NEAR);
-        }
-        R e[5];
         if constexpr (sizeof(R) == 4) {
-            // centred nodes over the half-spread sg: -1, t1, t2, t3, 1 (all zero when the set is a point)
+            // inner centred nodes over the half-spread sg (the outer two are -1 and 1)
             const float sg = 0.5f * spread;
             const float si = sg > 0.f ? 1.f / sg : 0.f;
-            const float tc[5] = {sg > 0.f ? -1.f : 0.f, (x[1] - cd) * si, (x[2] - cd) * si, (x[3] - cd) * si,
-                                 sg > 0.f ? 1.f : 0.f};
-            esym5<float>(tc, e);
+            fld(s, 0) = (x[1] - cd) * si;
+            fld(s, 1) = (x[2] - cd) * si;
+            fld(s, 2) = (x[3] - cd) * si;
+            fld(s, 3) = cd;
+            fld(s, 4) = spread;
         } else {
+            bool near = false;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const R g = x[i + 1] - x[i];
+                near = near || (g > (R)0 && g < (R)TT_NEAR);
+            }
+            R e[5];
             const R tc[5] = {(R)-0.5 * spread, x[1] - cd, x[2] - cd, x[3] - cd, (R)0.5 * spread};
             esym5<R>(tc, e);
-        }
 #pragma unroll
-        for (int j = 0; j < 5; ++j) fld(s, j) = e[j];
-        fld(s, 5) = cd;
-        fld(s, 6) = near ? -spread - (R)1 : spread;
+            for (int j = 0; j < 5; ++j) fld(s, j) = e[j];
+            fld(s, 5) = cd;
+            fld(s, 6) = near ? -spread - (R)1 : spread;
+        }
     }
     const int fend = min(nf, (int)(blockIdx.y + 1) * fch);
     for (int f0 = blockIdx.y * fch; f0 < fend; f0 += TT_FC) {
@@ -621,14 +627,18 @@ __global__ void __launch_bounds__(64) k_tetra_weights(const double* __restrict__
             }
         }
         for (int s = 0; s < 24; ++s) {
-            const R sp = fld(s, 6);
-            const bool near = sp < (R)0;
-            const R spread = near ? -sp - (R)1 : sp;
-            const R e[5] = {fld(s, 0), fld(s, 1), fld(s, 2), fld(s, 3), fld(s, 4)};
-            const R ct = fld(s, 5);
             if constexpr (sizeof(R) == 4) {
+                const float spread = fld(s, 4), ct = fld(s, 3);
+                const float one = spread > 0.f ? 1.f : 0.f;
+                const float tc[5] = {-one, fld(s, 0), fld(s, 1), fld(s, 2), one};
+                float e[5];
+                esym5<float>(tc, e);
                 series_poles32(e, spread, ct, zr, fend - f0, s, acc, dmask);
             } else {
+                const R sp = fld(s, 6);
+                const R spread = sp < (R)0 ? -sp - (R)1 : sp;
+                const R e[5] = {fld(s, 0), fld(s, 1), fld(s, 2), fld(s, 3), fld(s, 4)};
+                const R ct = fld(s, 5);
 #pragma unroll
                 for (int fi = 0; fi < TT_FC; ++fi) {
                     if (f0 + fi >= fend) break;
@@ -695,7 +705,7 @@ cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double
     // frequencies per grid row: all of them when the pairs alone fill the GPU
     const int fch = K >= 4LL * 152 * bs ? nf : std::max(1, (int)((nf * K + 4LL * 152 * bs - 1) / (4LL * 152 * bs)));
     dim3 grid((unsigned)((K + bs - 1) / bs), (unsigned)((nf + fch - 1) / fch));
-    const size_t smem = (size_t)24 * TT_FIELDS * bs * (fp32 ? sizeof(float) : sizeof(double));
+    const size_t smem = (size_t)24 * (fp32 ? TT_FIELDS32 : TT_FIELDS) * bs * (fp32 ? sizeof(float) : sizeof(double));
     if (fp32) {
         cudaFuncSetAttribute(k_tetra_weights<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_tetra_weights<float><<<grid, bs, smem, st>>>(
