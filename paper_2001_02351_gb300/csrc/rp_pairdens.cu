@@ -575,15 +575,16 @@ __global__ void __launch_bounds__(PX_THREADS) k_pair_x(const C* __restrict__ T2,
 }
 
 // x read-out for the windowed T2 (FP32 lines, half-width W on all three axes): one thread per
-// (pair, yz point of the window) loads the point's N1 values along x (consecutive threads on
-// consecutive points, so each x plane is read coalesced), transforms them in registers (the same
-// +i line transform as z and y) and parks the outputs that lie on the sphere (colg) in shared
-// memory; then the block writes its PB pairs as M[g][col0 + pair], PB consecutive columns per row.
+// (pair, yz point of the window; a window of more than 256 points is taken 256 points at a time)
+// loads the point's N1 values along x (consecutive threads on consecutive points, so each x plane
+// is read coalesced), transforms them in registers (the same +i line transform as z and y) and
+// parks the outputs that lie on the sphere (colg) in shared memory; then the block writes its PB
+// pairs as M[g][col0 + pair], PB consecutive columns per row.
 template <int W>
 struct PairXW {
     static constexpr int NW = 2 * W + 1, NC = NW * NW;
-    static constexpr int TPP = (NC + 31) / 32 * 32;             // threads per pair
-    static constexpr int PB = TPP >= 256 ? 1 : 256 / TPP;       // pairs per block
+    static constexpr int TPP = NC >= 256 ? 256 : (NC + 31) / 32 * 32;   // threads per pair
+    static constexpr int PB = 256 / TPP;                                // pairs per block
     static constexpr int THREADS = PB * TPP;
 };
 
@@ -597,9 +598,9 @@ __global__ void __launch_bounds__(PairXW<W>::THREADS) k_pair_x_w(const float2* _
     float2* xo = reinterpret_cast<float2*>(sm_xw);            // [ng][PB]
     const int j = threadIdx.x / X::TPP, c = threadIdx.x % X::TPP;
     const long long p0 = (long long)blockIdx.x * X::PB, p = p0 + j;
-    if (p < npair && c < X::NC) {
+    for (int cl = c; p < npair && cl < X::NC; cl += X::TPP) {
         float2 v[N];
-        const float2* src = T2 + (size_t)p * N * X::NC + c;
+        const float2* src = T2 + (size_t)p * N * X::NC + cl;
 #pragma unroll
         for (int x = 0; x < N; ++x) v[x] = __ldg(src + (size_t)x * X::NC);
         LineFFT<float2, N>::run(v);
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(PairXW<W>::THREADS) k_pair_x_w(const float2* _
         for (int r = 0; r < N; ++r) {
             const int gx = r <= N / 2 ? r : r - N;                 // signed value of residue r
             if (gx >= -W && gx <= W) {
-                const int g = __ldg(colg + (gx + W) * X::NC + c);
+                const int g = __ldg(colg + (gx + W) * X::NC + cl);
                 if (g >= 0) xo[g * X::PB + j] = make_float2(v[r].x * scale, v[r].y * scale);
             }
         }
@@ -625,18 +626,14 @@ template <int N, int W, typename CO>
 static bool launch_x_w_n(const float2* T2, long long npair, const int* colg, int ng, float scale, CO* M, long long ldm,
                          long long col0, cudaStream_t st) {
     using X = PairXW<W>;
-    if constexpr (X::TPP > 256) {       // wider windows: not built (k_pair_x reads the same layout)
+    const size_t smem = (size_t)ng * X::PB * sizeof(float2);
+    if (smem > 200 * 1024) return false;
+    if (cudaFuncSetAttribute(k_pair_x_w<N, W, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return false;
-    } else {
-        const size_t smem = (size_t)ng * X::PB * sizeof(float2);
-        if (smem > 200 * 1024) return false;
-        if (cudaFuncSetAttribute(k_pair_x_w<N, W, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return false;
-        const long long nblk = (npair + X::PB - 1) / X::PB;
-        k_pair_x_w<N, W, CO><<<(unsigned)nblk, X::THREADS, smem, st>>>(T2, npair, colg, ng, scale, M, ldm, col0);
-        return true;
-    }
+    const long long nblk = (npair + X::PB - 1) / X::PB;
+    k_pair_x_w<N, W, CO><<<(unsigned)nblk, X::THREADS, smem, st>>>(T2, npair, colg, ng, scale, M, ldm, col0);
+    return true;
 }
 
 template <typename C, int N, int W>
@@ -688,8 +685,8 @@ static bool launch_x_win_n(int w, const float2* T2, long long npair, const int* 
     return false;
 }
 
-// x read-out of the windowed T2 by line transforms (false: not built for this window; the caller
-// then uses k_pair_x on the same layout)
+// x read-out of the windowed T2 by line transforms (built for every window; false only when a
+// launch attribute is refused, and the caller then uses k_pair_x on the same layout)
 template <typename CO>
 static bool launch_x_win(int n, int w, const float2* T2, long long npair, const int* colg, int ng, float scale,
                          CO* M, long long ldm, long long col0, cudaStream_t st) {
@@ -867,7 +864,10 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
         const long long npair = (long long)nkb * c->nemp * c->nocc;
         const size_t t2 = (size_t)npair * N1 * wy * wz * sizeof(C);
         constexpr int PB = PairX<C>::PB;
-        const size_t xsm = ((size_t)2 * PB * N1 * wy * wz + (size_t)P.nset[0] * N1 + (size_t)P.ng * PB) * sizeof(C);
+        // shared memory of the x read-out that will run: k_pair_x_w holds only its pairs' outputs
+        const size_t xsm = w > 0 ? (size_t)P.ng * PairXW<2>::PB * sizeof(C)
+                                          : ((size_t)2 * PB * N1 * wy * wz + (size_t)P.nset[0] * N1 +
+                                             (size_t)P.ng * PB) * sizeof(C);
         if (P.fused && (w > 0 || P.masks) && xsm <= 200 * 1024 && t2 <= (size_t)16 << 30 &&
             ensure(c, c->s_t2, t2) == RP_OK &&
             launch_zy<C>(N2, N3, w, (const C*)c->s_u.p, nkb, c->nband, c->nocc, c->nemp, N1, P.zmask, nz, P.ymask,

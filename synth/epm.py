@@ -140,6 +140,19 @@ def _solve_k(args):
     return m.astype(np.int32), e, v.T.copy()
 
 
+def _cuda_in_process():
+    """True when this process may hold a CUDA context (torch initialised it, or a library such
+    as the C-ABI one has the driver mapped), so a worker pool must not be forked."""
+    torch = sys.modules.get("torch")
+    if torch is not None and torch.cuda.is_initialized():
+        return True
+    try:
+        with open("/proc/self/maps") as f:
+            return any("libcuda.so" in line for line in f)
+    except OSError:
+        return False
+
+
 def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None):
     """Diagonalise H_k on the whole mesh; returns zero-padded arrays (see Bands)."""
     rng = np.random.default_rng(seed)
@@ -165,9 +178,9 @@ def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None):
         saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
         for v in saved:
             os.environ[v] = "1"
-        # fork is safe (and needs no importable __main__) while CUDA is not initialised here
-        torch = sys.modules.get("torch")
-        cuda_up = torch is not None and torch.cuda.is_initialized()
+        # fork is safe (and needs no importable __main__) only while no CUDA context can exist in
+        # this process: spawn once torch has initialised CUDA or any library has loaded the driver
+        cuda_up = _cuda_in_process()
         try:
             with cf.ProcessPoolExecutor(max_workers=workers,
                                         mp_context=mp.get_context("spawn" if cuda_up else "fork")) as ex:

@@ -81,6 +81,38 @@ def test_pair_density_on_a_smaller_exact_grid(name, fft):
     assert np.all(_rel_fro(chi, chi_ref) < BF16X3_TOL)
 
 
+# wide epsilon spheres (E_cut^eps just below E_cut^psi): on the 24-point grid the sphere reaches 6
+# (window of half-width 7), on the 32-point grid it reaches 8 (half-width 11, a window of 529
+# points that the x read-out takes in passes of 256)
+WIDE = {
+    "w24": ("small", dict(npw=700, ng=600, fft=(32, 32, 32)), 6),
+    "w32": ("micro", dict(kmesh=(2, 2, 2), npw=1600, ng=1400, fft=(48, 48, 48)), 8),
+}
+
+
+@pytest.mark.parametrize("case", sorted(WIDE))
+def test_wide_sphere_window(case):
+    """Pair densities and the split-tier chi0 on wide epsilon spheres: the FP32 pair kernels take
+    the windows of half-width 7 (24-point grid) and 11 (32-point grid).  chi0 of the split tier
+    against the oracle, and the FP64 pair densities (residue masks) of two k points."""
+    from dataclasses import replace
+    base, kw, reach = WIDE[case]
+    wl = workload(base, **kw)
+    wl = replace(wl, freq=np.asarray(wl.freq)[:2])
+    assert wl.ecut_eps[0] <= wl.bands.ecut_psi
+    ctx = _ctx(wl)
+    q = wl.q[0]
+    G = OL.eps_sphere(wl.cell.lat, q, wl.ecut_eps[0])
+    assert np.abs(G).max() == reach
+    M = OP.pair_density(wl.bands, wl.nocc, wl.nemp, q, G, fft=wl.fft)
+    npk = wl.nocc * wl.nemp
+    got = ctx.rp_pair_density(q, 0, 2)
+    assert np.abs(got - M[:, :2 * npk]).max() <= 1e-12 * np.abs(M).max()
+    chi_ref = OC.chi0(M, OC.pair_weights(wl, q))
+    chi = ctx.rp_build_chi0(q, _axis(wl), _ordering(wl), wl.freq, wl.delta, rp.RP_BF16X3)
+    assert np.all(_rel_fro(chi, chi_ref) < BF16X3_TOL)
+
+
 @pytest.mark.parametrize("name", ["micro", "small"])
 def test_tetra_weights(name):
     wl = workload(name)
