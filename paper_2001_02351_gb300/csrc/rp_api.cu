@@ -381,21 +381,22 @@ int rp_load_bands(rp_ctx* c, int nk, int nband, int nocc, const int* npw, int np
     if (nocc < 1 || nband <= nocc) return fail(c, RP_ERR_ARG, "need 1 <= nocc < nband");
     if (!npw || !miller || !coef || !energy_ha || npw_max < nband) return fail(c, RP_ERR_ARG, "bad band arrays");
     int maxm = 0, mu[3] = {0, 0, 0};
-    std::vector<unsigned char> mark((size_t)c->nr);
+    // grid point -> (k + 1) of the last k whose sphere holds it: no clearing between k points
+    std::vector<int> mark((size_t)c->nr, 0);
     for (int k = 0; k < nk; ++k) {
         if (npw[k] < nband || npw[k] > npw_max) return fail(c, RP_ERR_ARG, "npw out of range");
-        std::fill(mark.begin(), mark.end(), 0);
         for (int p = 0; p < npw[k]; ++p) {
             long long idx = 0;
             for (int a = 0; a < 3; ++a) {
-                int m = miller[((size_t)k * npw_max + p) * 3 + a];
+                const int m = miller[((size_t)k * npw_max + p) * 3 + a], n = c->fft[a];
                 maxm = std::max(maxm, std::abs(m));
                 mu[a] = std::max(mu[a], std::abs(m));
-                int w = ((m % c->fft[a]) + c->fft[a]) % c->fft[a];
-                idx = idx * c->fft[a] + w;
+                int w = m < 0 ? m + n : m;                   // residue of m modulo n when |m| < n
+                if (w < 0 || w >= n) w = ((m % n) + n) % n;
+                idx = idx * n + w;
             }
-            if (mark[idx]) return fail(c, RP_ERR_ARG, "wave-function sphere does not fit the FFT grid");
-            mark[idx] = 1;
+            if (mark[idx] == k + 1) return fail(c, RP_ERR_ARG, "wave-function sphere does not fit the FFT grid");
+            mark[idx] = k + 1;
         }
     }
     for (long long i = 0; i < (long long)nk * nband; ++i) {

@@ -201,6 +201,15 @@ def test_errors_are_reported():
         ctx.nk, ctx.nemp, ctx.nocc = 8, 4, 4
         ctx.rp_tetra_weights(wl.q[0], rp.RP_AXIS_IMAG, rp.RP_TIME_ORDERED, wl.freq, 0.0)
     assert e.value.code == rp.RP_ERR_STATE
+    # more plane waves than grid points (at least 110 on 4^3): two of them share a grid point, and
+    # the load is refused
+    ws = workload("small")
+    bs, nbs = ws.bands, ws.nocc + ws.nemp
+    assert np.min(bs.npw) > 64
+    narrow = rp.Context(bs.cell.lat, bs.kmesh, (4, 4, 4), bs.ecut_psi, float(ws.ecut_eps[0]))
+    with pytest.raises(rp.RPError) as e:
+        narrow.load_bands(ws.nocc, bs.npw, bs.miller, bs.coef[:, :nbs], bs.energy[:, :nbs])
+    assert e.value.code == rp.RP_ERR_ARG and "does not fit" in str(e.value)
     ctx = _ctx(wl)
     with pytest.raises(rp.RPError) as e:
         ctx.rp_sphere_size([0.3, 0.0, 0.0])           # not a mesh vector
