@@ -7,8 +7,12 @@
 //   4. forward transform with the same +i sign (the matrix element carries e^{+iG.r}),
 //      pruned on every axis to the Miller values present in the epsilon sphere,
 //   5. read-back on the sphere and normalisation by 1/(N1 N2 N3).
-// Every transform stage is a pruned discrete Fourier sum along one axis written as a
-// batched product with a small phase matrix E[out][in].
+// On transform grids of 16, 24 or 32 points the transforms are in-register line FFTs
+// (rp_fft.cuh): k_gather_fft (steps 1-2), k_pair_zy (steps 3-4 along z and y, one x plane per
+// CTA) and the x read-out (step 5): k_pair_x_w, a line transform of each (pair, yz) point of the
+// symmetric residue window (FP32 lines), or k_pair_x, a sum over x for each sphere point (FP64
+// lines).  The other grids take the general path, where each stage is a pruned discrete Fourier
+// sum along one axis written as a batched product with a small phase matrix E[out][in].
 #include "rp_internal.h"
 #include "rp_fft.cuh"
 
