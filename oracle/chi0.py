@@ -6,6 +6,12 @@ The factor 2 is the spin sum; T = 0 is the usual RPA (Eq. tak).  The pair
 weight w_b(w) = (2/N_k)(1 - T T) x carries everything but the matrix
 elements, so chi(w) = M diag(w(w)) M^H with M[G, b] (pair order of
 pair_density.py).
+
+Occupations: band-index occupations by default (the n_occ lowest bands of
+each k are occupied, the next n_emp empty).  With `fermi` given, a pair
+counts only when its occupied state lies below the Fermi energy and its
+empty state at k+q on or above it (energy occupations of a metal, as in the
+free-electron gas); this selection is a factor on the pair weight.
 """
 import numpy as np
 
@@ -13,7 +19,7 @@ from .lattice import umklapp
 from .tetra import poles, tetrahedra, vertex_weights, lorentz_x
 
 
-def pair_weights(wl, q_frac, k_list=None, kind="tetra"):
+def pair_weights(wl, q_frac, k_list=None, kind="tetra", fermi=None):
     """w[f, b] for the pairs of k_list (default all), Eq. chi prefactors x X."""
     b = wl.bands
     nk = b.kfrac.shape[0]
@@ -30,8 +36,12 @@ def pair_weights(wl, q_frac, k_list=None, kind="tetra"):
     else:
         raise ValueError(kind)
     if wl.T is not None:
+        # empty band a at k' = k+q, occupied band o at k
         tt = 1.0 - wl.T[kp][:, wl.nocc:wl.nocc + wl.nemp][:, :, None] * wl.T[:, :wl.nocc][:, None, :]
         x = x * tt[ks][..., None]
+    if fermi is not None:
+        sel = (e_occ < fermi)[:, None, :] & (e_emp >= fermi)[:, :, None]     # [k, a, o]
+        x = x * sel[ks][..., None]
     w = (2.0 / nk) * x                                    # [k, a, o, f]
     return np.ascontiguousarray(w.reshape(-1, w.shape[-1]).T)   # [f, b]
 
