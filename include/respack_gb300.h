@@ -145,10 +145,24 @@ int rp_contract_chi0(rp_ctx* ctx, int ng, long long K, int nfreq, const double* 
 
 /* rp_build_chi0 -- the whole chi0 path for one q: pair densities, tetrahedron weights and
  *   the contraction, streamed over blocks of k so that M is never held whole.
- *   chi0_out [io] c128 [nfreq][NG][NG].  Other arguments as above. */
+ *   chi0_out [io] c128 [nfreq][NG][NG].  Other arguments as above.
+ *   RP_ERR_TIMEOUT if a bounded wait of the RP_BF16X3 contraction kernel gave up (chi0_out is then
+ *   unspecified); with on_device = 1 that status is only known after the stream has run and is
+ *   returned by rp_check_numeric. */
 int rp_build_chi0(rp_ctx* ctx, const double q_frac[3], int axis, int ordering, int nfreq,
                   const double* freq_ha, double delta_ha, double delta_a, double delta_r,
                   int precision, double* chi0_out, int on_device, void* cuda_stream);
+
+/* rp_build_chi0_kset -- rp_build_chi0 with the k sum of Eq. chi restricted to the nks distinct
+ *   mesh points of k_list (host, any order): the pairs (k, a, o) with k in the list contribute, each
+ *   with its full-mesh tetrahedron weight, so the chi0 of a partition of the mesh into k sets sums
+ *   to the chi0 of the whole mesh.  Used for a sampled reference of a workload too large for a
+ *   full FP64 build, and as the unit of a build whose k points are shared out over several GPUs.
+ *   chi0_out [io] c128 [nfreq][NG][NG] (overwritten).  RP_ERR_ARG for an index outside [0, N_k) or
+ *   a repeated one.  Other arguments and errors as rp_build_chi0. */
+int rp_build_chi0_kset(rp_ctx* ctx, const double q_frac[3], int nks, const int* k_list, int axis, int ordering,
+                       int nfreq, const double* freq_ha, double delta_ha, double delta_a, double delta_r,
+                       int precision, double* chi0_out, int on_device, void* cuda_stream);
 
 /* rp_solve_w -- Dyson step (Eq. epsGG, Eq. Wq) in FP64:
  *   eps = 1 - v^1/2 chi0 v^1/2,  W = v^1/2 eps^-1 v^1/2,  v^1/2_G = sqrt(4 pi/Omega)/|q+G|,
@@ -181,9 +195,19 @@ int rp_solve_w_batched(rp_ctx* ctx, int nq, const double* q_frac, const double* 
                        const double* const* chi0, double* const* W_out, double* const* tail_out,
                        int on_device, void* cuda_stream);
 
-/* rp_check_numeric -- synchronises the context's last stream and returns RP_ERR_NUMERIC
- *   if an asynchronous rp_solve_w met a bad pivot since the previous check, else RP_OK. */
+/* rp_check_numeric -- synchronises the context's last stream and reports what the asynchronous
+ *   (on_device = 1) calls since the previous check left in the context's device flags:
+ *   RP_ERR_TIMEOUT if a bounded device wait of a contraction gave up (its chi0 is unspecified),
+ *   else RP_ERR_NUMERIC if an rp_solve_w met a bad pivot, else RP_OK.  Both flags are cleared. */
 int rp_check_numeric(rp_ctx* ctx);
+
+/* rp_set_wait_limit -- testing aid with no counterpart in the paper: the time after which a
+ *   bounded device wait of the context's RP_BF16X3 contraction kernel gives up (default 2e9 ns).
+ *   A wait that gives up sets the context's timeout flag and the kernel returns through its
+ *   teardown (copies and tensor-core operations in flight are drained with the fixed 2 s limit,
+ *   tensor memory is freed), so a short limit exercises that path without hanging the device.
+ *   limit_ns >= 0, else RP_ERR_ARG. */
+int rp_set_wait_limit(rp_ctx* ctx, long long limit_ns);
 
 /* rp_contract_chi0_static -- the RP_BF16X3 contraction of rp_contract_chi0 without any
  *   device allocation, for callers that cannot allocate device memory when they need chi0
@@ -201,9 +225,17 @@ int rp_check_numeric(rp_ctx* ctx);
  *   (once per device); make that first call before any stream capture.  Every call uses the
  *   same array: calls whose work overlaps on the GPU (other streams, other threads) race and
  *   must be serialised by the caller.  A device-side wait that gives up leaves chi_out
- *   unspecified.  Returns RP_OK, RP_ERR_ARG or RP_ERR_CUDA. */
+ *   unspecified and sets a flag in the array; rp_contract_chi0_static_status reports it.
+ *   Returns RP_OK, RP_ERR_ARG or RP_ERR_CUDA. */
 int rp_contract_chi0_static(int ng, long long K, int nfreq, const double* M, const double* w,
                             double* chi_out, void* cuda_stream);
+
+/* rp_contract_chi0_static_status -- synchronises cuda_stream and returns RP_ERR_TIMEOUT if the
+ *   last rp_contract_chi0_static on the current device had a device-side wait give up (the flag
+ *   in the library's array is then cleared), RP_OK if not, RP_ERR_CUDA if the synchronisation or
+ *   the read failed.  Allocates nothing.  Call it after the call it checks and before the next
+ *   one (each call clears the flag when it starts).  No counterpart in the paper. */
+int rp_contract_chi0_static_status(void* cuda_stream);
 
 /* rp_profile_enable -- measurement aid (no counterpart in the paper).  enable = 1 starts
  *   recording a CUDA event pair on the launching stream around every stage of the path and

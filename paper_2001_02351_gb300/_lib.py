@@ -25,7 +25,8 @@ _STATUS = {0: "RP_OK", -1: "RP_ERR_ARG", -2: "RP_ERR_STATE", -3: "RP_ERR_OOM", -
 EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density", "rp_tetra_weights",
            "rp_contract_chi0", "rp_build_chi0", "rp_solve_w", "rp_check_numeric", "rp_profile_enable",
            "rp_profile_read", "rp_last_error", "rp_destroy", "rp_contract_chi0_static", "rp_sphere_size_at",
-           "rp_build_chi0_batched", "rp_solve_w_batched"]
+           "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_contract_chi0_static_status",
+           "rp_build_chi0_kset"]
 
 
 class RPError(RuntimeError):
@@ -64,6 +65,9 @@ def library():
         "rp_sphere_size_at": (I, [P, P, D, ctypes.POINTER(I), ctypes.POINTER(I), P, P]),
         "rp_build_chi0_batched": (I, [P, I, P, P, I, I, I, P, D, D, D, I, P, I, P]),
         "rp_solve_w_batched": (I, [P, I, P, P, I, P, P, P, I, P]),
+        "rp_set_wait_limit": (I, [P, LL]),
+        "rp_build_chi0_kset": (I, [P, P, I, P, I, I, I, P, D, D, D, I, P, I, P]),
+        "rp_contract_chi0_static_status": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -215,6 +219,19 @@ class Context:
                                             dev, _stream() if dev else None))
         return out
 
+    def rp_build_chi0_kset(self, q, k_list, axis, ordering, freq, delta, precision=RP_FP64_NATIVE, delta_a=1e-8,
+                           delta_r=1e-8, out=None):
+        """chi0 of q summed over the pairs of the mesh points k_list only (full-mesh weights)."""
+        g, _ = self.rp_sphere_size(q)
+        fr, pf = _host(freq, np.float64)
+        ks, pk = _host(k_list, np.int32)
+        out, dev = self._out(out, (len(fr), len(g), len(g)))
+        q_, pq = _host(q, np.float64)
+        self._check(self._lib.rp_build_chi0_kset(self._h, pq, len(ks), pk, int(axis), int(ordering), len(fr), pf,
+                                                 float(delta), float(delta_a), float(delta_r), int(precision),
+                                                 self._ptr(out, dev), dev, _stream() if dev else None))
+        return out
+
     def rp_build_chi0_batched(self, qs, axis, ordering, freq, delta, precision=RP_FP64_NATIVE, ecut_eps=None,
                               delta_a=1e-8, delta_r=1e-8, outs=None):
         """chi0 of every q of qs [nq][3] (per-q cut-offs ecut_eps [nq] or None); a list of arrays
@@ -280,6 +297,9 @@ class Context:
 
     def rp_check_numeric(self):
         self._check(self._lib.rp_check_numeric(self._h))
+
+    def rp_set_wait_limit(self, limit_ns):
+        self._check(self._lib.rp_set_wait_limit(self._h, int(limit_ns)))
 
     def rp_profile_enable(self, enable=True):
         self._check(self._lib.rp_profile_enable(self._h, 1 if enable else 0))

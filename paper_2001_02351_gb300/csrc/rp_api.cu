@@ -469,7 +469,15 @@ static int finish(rp_ctx* c, cudaStream_t st, int on_device) {
 static int pair_density_device(rp_ctx* c, int k0, int k1, void* M, bool fp32, long long ldm, long long col0,
                                cudaStream_t st) {
     const size_t per_k = (size_t)c->nband * c->plan.nr * (fp32 ? sizeof(float2) : sizeof(double2));
-    const int kb = (int)std::max<size_t>(1, std::min<size_t>((size_t)(k1 - k0), ((size_t)2 << 30) / (3 * per_k)));
+    // plane sums of one k point in the windowed (FP32) or residue-set (FP64) layout of the plane-wise
+    // pair kernels: the sub-block keeps them within those kernels' 16 GB budget
+    const QPlan& P = c->plan;
+    const int W = fp32 ? P.zyw : 0;
+    const size_t wyz = W > 0 ? (size_t)(2 * W + 1) * (2 * W + 1) : (size_t)P.nset[1] * P.nset[2];
+    const size_t t2_k = (size_t)c->nemp * c->nocc * P.nfft[0] * wyz * (fp32 ? sizeof(float2) : sizeof(double2));
+    const size_t kb_t2 = std::max<size_t>(1, ((size_t)16 << 30) / std::max<size_t>(1, t2_k));
+    const int kb = (int)std::max<size_t>(
+        1, std::min<size_t>(std::min<size_t>((size_t)(k1 - k0), ((size_t)2 << 30) / (3 * per_k)), kb_t2));
     for (int k = k0; k < k1; k += kb) {
         const int nkb = std::min(kb, k1 - k);
         prof_begin(c, 0, st);
@@ -527,15 +535,17 @@ static int weights_device(rp_ctx* c, int axis, int ordering, int nfreq, const do
                           double da, double dr, bool fp32, double2* w, cudaStream_t st) {
     int s = ensure(c, c->s_io3, nfreq * sizeof(double));
     if (s) return s;
-    cudaError_t e = cudaMemcpyAsync(c->s_io3.p, freq, nfreq * sizeof(double), cudaMemcpyHostToDevice, st);
+    // the frequencies go through a pageable host copy owned by the context: a copy from pageable
+    // memory is staged before cudaMemcpyAsync returns, so neither buffer has to outlive the call
+    // and the stream is not synchronised (the caller's array might be pinned)
+    c->freq_stage.assign(freq, freq + nfreq);
+    cudaError_t e = cudaMemcpyAsync(c->s_io3.p, c->freq_stage.data(), nfreq * sizeof(double),
+                                    cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "copy frequencies");
     prof_begin(c, 2, st);
     e = launch_tetra(c, axis, ordering, nfreq, (const double*)c->s_io3.p, delta, da, dr, fp32, w, st);
     prof_end(c, 2, st, fp32 ? 2 : 1);
-    if (e != cudaSuccess) return cuda_fail(c, e, "tetrahedron weights");
-    // the frequency copy is from pageable host memory; keep it valid until it has landed
-    e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "synchronize");
+    return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "tetrahedron weights");
 }
 
 int rp_tetra_weights(rp_ctx* c, const double q[3], int axis, int ordering, int nfreq, const double* freq,
@@ -592,7 +602,7 @@ static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, lon
     if (e == cudaSuccess) {
         prof_begin(c, 3, st);
         e = launch_contract_bf16x3_core(c->s_hi.p, c->s_lo.p, K, ng, nfreq, c->s_w32.p, chi, (int*)c->d_err.p + 1,
-                                        c->num_sms, st);
+                                        c->num_sms, c->wait_ns, st);
         prof_end(c, 3, st, 1);
     }
     return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "bf16x3 contraction");
@@ -642,13 +652,30 @@ int rp_contract_chi0(rp_ctx* c, int ng, long long K, int nfreq, const double* M,
     return on_device ? RP_OK : check_timeout(c);
 }
 
+// chi0 of q summed over the pairs of the k points in klist[nks] (all k when klist is NULL), with
+// weights from the whole mesh's tetrahedra
 static int build_chi0(rp_ctx* c, const double q[3], double ecut_eps, int axis, int ordering, int nfreq,
                       const double* freq, double delta, double da, double dr, int precision, double* chi0_out,
-                      int on_device, void* stream) {
+                      int on_device, void* stream, int nks = 0, const int* klist = nullptr) {
     int s = check_ready_cut(c, q, ecut_eps);
     if (s) return s;
     if ((s = check_freq(c, axis, ordering, nfreq, freq, delta, da, dr))) return s;
     if (!chi0_out) return fail(c, RP_ERR_ARG, "chi0_out is NULL");
+    // runs of consecutive k points: [runs[2i], runs[2i+1])
+    std::vector<int> runs;
+    if (klist) {
+        if (nks < 1 || nks > c->nk) return fail(c, RP_ERR_ARG, "bad k-point count");
+        std::vector<int> ks(klist, klist + nks);
+        std::sort(ks.begin(), ks.end());
+        for (int i = 0; i < nks; ++i) {
+            if (ks[i] < 0 || ks[i] >= c->nk) return fail(c, RP_ERR_ARG, "k index out of range");
+            if (i > 0 && ks[i] == ks[i - 1]) return fail(c, RP_ERR_ARG, "repeated k index");
+            if (i > 0 && ks[i] == ks[i - 1] + 1) runs.back() = ks[i] + 1;
+            else { runs.push_back(ks[i]); runs.push_back(ks[i] + 1); }
+        }
+    } else {
+        runs = {0, c->nk};
+    }
     if (precision != RP_FP64_NATIVE && precision != RP_BF16X3 && precision != RP_TF32X3)
         return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
     cudaStream_t st = (cudaStream_t)stream;
@@ -675,14 +702,17 @@ static int build_chi0(rp_ctx* c, const double q[3], double ecut_eps, int axis, i
         if (e != cudaSuccess) return cuda_fail(c, e, "zero chi");
     }
     void* M = c->s_m.p;
-    for (int k0 = 0; k0 < c->nk; k0 += kb) {
-        const int k1 = std::min(c->nk, k0 + kb);
-        const long long cols = (long long)(k1 - k0) * kcols;
-        if ((s = pair_density_device(c, k0, k1, M, m32, cols, 0, st))) return s;
-        if ((s = contract_block(c, precision, M, m32, cols, 0, cols, w, K, (long long)k0 * kcols, nfreq, ng, chi,
-                                k0 > 0, st)))
-            return s;
-    }
+    bool first = true;
+    for (size_t r = 0; r < runs.size(); r += 2)
+        for (int k0 = runs[r]; k0 < runs[r + 1]; k0 += kb) {
+            const int k1 = std::min(runs[r + 1], k0 + kb);
+            const long long cols = (long long)(k1 - k0) * kcols;
+            if ((s = pair_density_device(c, k0, k1, M, m32, cols, 0, st))) return s;
+            if ((s = contract_block(c, precision, M, m32, cols, 0, cols, w, K, (long long)k0 * kcols, nfreq, ng, chi,
+                                    first ? 0 : 1, st)))
+                return s;
+            first = false;
+        }
     if (!on_device) {
         cudaError_t e = cudaMemcpyAsync(chi0_out, chi, bc, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "copy chi0");
@@ -695,13 +725,23 @@ int rp_check_numeric(rp_ctx* c) {
     if (!c) return RP_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize(c->last_stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
-    int flag = 0;
-    e = cudaMemcpy(&flag, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(c, e, "read error flag");
-    if (flag) {
-        cudaMemset(c->d_err.p, 0, sizeof(int));
-        return fail(c, RP_ERR_NUMERIC, "zero or non-finite pivot in the Dyson solve");
+    int flag[2] = {0, 0};
+    e = cudaMemcpy(flag, c->d_err.p, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read error flags");
+    if (flag[0] || flag[1]) cudaMemset(c->d_err.p, 0, 2 * sizeof(int));
+    if (flag[1]) {
+        char buf[112];
+        snprintf(buf, sizeof(buf), "a bounded device wait of an asynchronous contraction gave up (site %d)", flag[1]);
+        return fail(c, RP_ERR_TIMEOUT, buf);
     }
+    if (flag[0]) return fail(c, RP_ERR_NUMERIC, "zero or non-finite pivot in the Dyson solve");
+    return RP_OK;
+}
+
+int rp_set_wait_limit(rp_ctx* c, long long limit_ns) {
+    if (!c) return RP_ERR_ARG;
+    if (limit_ns < 0) return fail(c, RP_ERR_ARG, "negative wait limit");
+    c->wait_ns = (unsigned long long)limit_ns;
     return RP_OK;
 }
 
@@ -737,10 +777,14 @@ static int solve_w(rp_ctx* c, const double q[3], double ecut_eps, int nfreq, con
     prof_end(c, 4, st, 1);
     if (e != cudaSuccess) return cuda_fail(c, e, "Dyson solve");
     if (tail_out && c->plan.ntail > 0) {
-        e = cudaMemcpyAsync(tail_out, c->plan.tailv.data(), c->plan.ntail * sizeof(double),
-                            on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "tail");
-        if (on_device) cudaStreamSynchronize(st);   // the source is host memory owned by the plan
+        if (on_device) {
+            // staged from the plan's pageable vector before the call returns
+            e = cudaMemcpyAsync(tail_out, c->plan.tailv.data(), c->plan.ntail * sizeof(double),
+                                cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "tail");
+        } else {
+            std::memcpy(tail_out, c->plan.tailv.data(), c->plan.ntail * sizeof(double));
+        }
     }
     if (!on_device) {
         e = cudaMemcpyAsync(W_out, dW, bc, cudaMemcpyDeviceToHost, st);
@@ -756,6 +800,15 @@ int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfre
     if (!c) return RP_ERR_ARG;
     return build_chi0(c, q, c->ecut_eps, axis, ordering, nfreq, freq, delta, da, dr, precision, chi0_out, on_device,
                       stream);
+}
+
+int rp_build_chi0_kset(rp_ctx* c, const double q[3], int nks, const int* k_list, int axis, int ordering, int nfreq,
+                       const double* freq, double delta, double da, double dr, int precision, double* chi0_out,
+                       int on_device, void* stream) {
+    if (!c) return RP_ERR_ARG;
+    if (!k_list) return fail(c, RP_ERR_ARG, "k_list is NULL");
+    return build_chi0(c, q, c->ecut_eps, axis, ordering, nfreq, freq, delta, da, dr, precision, chi0_out, on_device,
+                      stream, nks, k_list);
 }
 
 int rp_solve_w(rp_ctx* c, const double q[3], int nfreq, const double* chi0, double* W_out, double* tail_out,

@@ -24,8 +24,9 @@
 // frequencies; the stages two ahead are prefetched into L2), warp 1 = MMA issuer, warps 2-9 =
 // builders of the weighted rows (scale by w, split, write the 128B-swizzled K-major tile), warps
 // 10-13 = epilogue (tcgen05.ld -> FP64 atomics).
-// Every wait is bounded; a wait that gives up records where in err_flag[1] and the CTA
-// leaves through the common teardown (its copies in flight are waited for, TMEM is freed).
+// Every wait is bounded; a wait that gives up (after the caller's limit, 2 s by default) records
+// where in err_flag[1] and the CTA leaves through the common teardown: its copies and MMAs in
+// flight are waited for (with the fixed 2 s limit), then TMEM is freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -56,7 +57,7 @@ namespace rp {
 #define TC_SMEM_BAR (TC_SMEM_B0 + 2 * 2 * TC_B_BYTES)
 #define TC_SMEM_TOTAL (TC_SMEM_BAR + 256 + 1024)
 
-#define TC_WAIT_NS 2000000000ULL   // a wait gives up after 2 s
+#define TC_WAIT_NS 2000000000ULL   // default limit of a wait, and the limit of the teardown's drains
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -83,14 +84,15 @@ __device__ __forceinline__ uint64_t gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// bounded wait: false (and err_flag set to `code`) if the phase does not complete within TC_WAIT_NS
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+// bounded wait: false (and err_flag set to `code`) if the phase does not complete within limit_ns
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code,
+                                          uint64_t limit_ns = TC_WAIT_NS) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try(bar, parity)) return true;
-        if (gtimer() - t0 > TC_WAIT_NS) break;
+        if (gtimer() - t0 > limit_ns) break;
     }
     atomicExch(err, code);
     return false;
@@ -156,6 +158,7 @@ struct TcArgs {
     int ng, nf, nfq, nblk, mt, nst, nwin;
     double2* chi;
     int* err;
+    unsigned long long wait_ns;   // limit of the pipeline's waits (the teardown drains use TC_WAIT_NS)
 };
 
 static_assert(TC_BN % 16 == 0 && TC_BN <= 256 && TC_BN % 32 == 16, "epilogue reads TC_BN in 32- and one 16-column load");
@@ -212,6 +215,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int njobs = ntile * args.nwin;
     const int nst = args.nst;
     int* err = args.err;
+    const uint64_t lim = args.wait_ns;
     // job -> (accumulation window, group of four frequencies, G' block, G tile); consecutive jobs
     // share a window.  The last block and tile are moved back to end at ng, so that (for ng >=
     // TC_BN) every box lies inside the arrays; a block or tile writes only the rows from its own
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             tma_prefetch_2d(&row_lo, xp, n0);
                         }
                     }
-                    if (!(ok = mbar_wait(empty(s), ph ^ 1, err, 101))) break;
+                    if (!(ok = mbar_wait(empty(s), ph ^ 1, err, 101, lim))) break;
                     const uint32_t base = sbase + s * TC_STAGE_BYTES;
                     mbar_expect_tx(full(s), TC_STAGE_LOAD);
 #pragma unroll
@@ -282,15 +286,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 job_tile(job, w0, w1, fq, n0, m0, nown, mown);
                 // both accumulators drained by the epilogue of the previous job
                 for (int t = 0; t < 2 && ok; ++t)
-                    ok = mbar_wait(acce(t), (uint32_t)((cg & 1) ^ 1), err, 111);
+                    ok = mbar_wait(acce(t), (uint32_t)((cg & 1) ^ 1), err, 111, lim);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int st = w0; st < w1; ++st, ++sg) {
                     const int s = (int)(sg % TC_NS);
-                    if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 112))) break;
+                    if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 112, lim))) break;
                     const uint32_t g_hi = sbase + s * TC_STAGE_BYTES, g_lo = g_hi + TC_RAW_BYTES;
                     for (int t = 0; t < 2; ++t) {
-                        if (!(ok = mbar_wait(bready(t), (uint32_t)(sg & 1), err, 113))) break;
+                        if (!(ok = mbar_wait(bready(t), (uint32_t)(sg & 1), err, 113, lim))) break;
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t d = tmem + (uint32_t)(t * 256);
                         const uint32_t b_hi = sbase + TC_SMEM_B0 + t * 2 * TC_B_BYTES, b_lo = b_hi + TC_B_BYTES;
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             job_tile(job, w0, w1, fq, n0, m0, nown, mown);
             for (int st = w0; st < w1 && ok; ++st, ++sg) {
                 const int s = (int)(sg % TC_NS);
-                if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 121))) break;
+                if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 121, lim))) break;
                 const unsigned char* stage = smem + s * TC_STAGE_BYTES;
                 const unsigned char* rhi = stage + TC_OFF_R;
                 const unsigned char* rlo = rhi + TC_R_BYTES;
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mi[i] = hh.y + ll.y;
                 }
                 for (int t = 0; t < 2; ++t) {
-                    if (!(ok = mbar_wait(bfree(t), (uint32_t)((sg & 1) ^ 1), err, 122))) break;
+                    if (!(ok = mbar_wait(bfree(t), (uint32_t)((sg & 1) ^ 1), err, 122, lim))) break;
                     unsigned char* bhi = smem + TC_SMEM_B0 + t * 2 * TC_B_BYTES;
                     unsigned char* blo = bhi + TC_B_BYTES;
 #pragma unroll
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int f = TC_NF * fq + 2 * t + (q4 >> 1), comp = q4 & 1;
                 const bool live = f < args.nf && gp >= nown && gp < args.ng;
                 double* out = chi + (((size_t)f * args.ng + m0) * args.ng + gp) * 2 + comp;
-                if (!(ok = mbar_wait(accf(t), (uint32_t)(cg & 1), err, 131))) break;
+                if (!(ok = mbar_wait(accf(t), (uint32_t)(cg & 1), err, 131, lim))) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * 256);
 #pragma unroll 1
@@ -556,11 +560,12 @@ cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, 
                                    int num_sms, cudaStream_t st) {
     cudaError_t e = launch_weights32(K, w, ldw, col0, nf, w32, st);
     if (e != cudaSuccess) return e;
-    return launch_contract_bf16x3_core(hi, lo, K, ng, nf, w32, chi, err, num_sms, st);
+    return launch_contract_bf16x3_core(hi, lo, K, ng, nf, w32, chi, err, num_sms, TC_WAIT_NS, st);
 }
 
 cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long long K, int ng, int nf,
-                                        const void* w32, double2* chi, int* err, int num_sms, cudaStream_t st) {
+                                        const void* w32, double2* chi, int* err, int num_sms,
+                                        unsigned long long wait_ns, cudaStream_t st) {
     const long long kp2 = tc_kp2(K);
     CUtensorMap mraw_hi, mraw_lo, mrow_hi, mrow_lo;
     if (!make_map(&mraw_hi, const_cast<void*>(hi), ng, kp2, TC_BN) ||
@@ -576,6 +581,7 @@ cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long lon
     a.nst = (int)(kp2 / TC_BK);
     a.nwin = (a.nst + TC_FLUSH_STAGES - 1) / TC_FLUSH_STAGES;
     a.chi = chi; a.err = err;
+    a.wait_ns = wait_ns;
     const long long njobs = (long long)a.nfq * a.nblk * a.mt * a.nwin;
     if (njobs > 0x7fffffffLL) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_contract_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_TOTAL);

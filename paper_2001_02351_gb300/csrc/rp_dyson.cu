@@ -132,6 +132,9 @@ __global__ void __launch_bounds__(DY_THREADS) k_dyson(const double2* __restrict_
 // (identical scan of column j), copies column j and the pivot row into shared memory, then after a
 // grid-wide sync applies the interchange and the elimination to its own columns; a second sync
 // closes the step.  Row interchanges are undone afterwards as column interchanges, row by row.
+// The grid barriers are shared by all frequencies, so every CTA passes exactly 2 n + 1 of them
+// whatever the data: a frequency that meets a bad pivot keeps passing both barriers of each
+// remaining step and skips only the arithmetic.
 #define DC_THREADS 512
 
 __global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __restrict__ chi,
@@ -162,6 +165,11 @@ __global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __rest
     if (tid == 0) s_bad = 0;
     grid.sync();
     for (int j = 0; j < n; ++j) {
+        if (s_bad) {          // read after a barrier: the same value in every thread of the CTA
+            grid.sync();
+            grid.sync();
+            continue;
+        }
         double best = -1.0;
         int bi = j;
         for (int i = j + tid; i < n; i += DC_THREADS) {
@@ -185,7 +193,11 @@ __global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __rest
             if (!(best > 0.0) || !isfinite(best)) s_bad = 1;
         }
         __syncthreads();
-        if (s_bad) break;     // every CTA sees the same pivot, so all leave together
+        if (s_bad) {          // this frequency's CTAs all see the same pivot; the grid keeps going
+            grid.sync();
+            grid.sync();
+            continue;
+        }
         const int p = s_piv;
         for (int i = tid; i < n; i += DC_THREADS) {
             const int src = (i == j) ? p : (i == p ? j : i);

@@ -7,7 +7,8 @@
 // (which can synchronise the whole device) is not allowed.  They pass inputs and outputs that
 // they own; the bf16 split of M, the float copy of the weights and the wait-timeout flag live
 // in g_static_scratch below.  That array is held by every GPU that loads this library, for as
-// long as the process runs.
+// long as the process runs.  rp_contract_chi0_static_status reads (and clears) the timeout flag
+// the last call left there, also without allocating.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -46,7 +47,31 @@ int scratch_address(void** out) {
     return RP_OK;
 }
 
+// the timeout flag inside the array
+int* static_flag(void* base) { return (int*)((unsigned char*)base + 2 * kSplitBytes + kW32Bytes); }
+
 }  // namespace
+
+extern "C" int rp_contract_chi0_static_status(void* cuda_stream) {
+    void* base = nullptr;
+    int s = scratch_address(&base);
+    if (s != RP_OK) return s;
+    int* flag = static_flag(base);
+    if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {
+        cudaGetLastError();
+        return RP_ERR_CUDA;
+    }
+    int v = 0;
+    if (cudaMemcpy(&v, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return RP_ERR_CUDA;
+    }
+    if (v) {
+        if (cudaMemset(flag, 0, sizeof(int)) != cudaSuccess) return RP_ERR_CUDA;
+        return RP_ERR_TIMEOUT;
+    }
+    return RP_OK;
+}
 
 extern "C" int rp_contract_chi0_static(int ng, long long K, int nfreq, const double* M, const double* w,
                                        double* chi_out, void* cuda_stream) {
@@ -62,7 +87,7 @@ extern "C" int rp_contract_chi0_static(int ng, long long K, int nfreq, const dou
     void* hi = p;
     void* lo = p + kSplitBytes;
     void* w32 = p + 2 * kSplitBytes;
-    int* flag = (int*)(p + 2 * kSplitBytes + kW32Bytes);
+    int* flag = static_flag(base);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int nsm = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

@@ -785,7 +785,7 @@ template <typename C, int N>
 static bool gather_fft_n(rp_ctx* c, int k0, long long nbands, cudaStream_t st) {
     const int B = 2 * c->lb + 1;
     const size_t smem = sizeof(C) * ((size_t)N * B * B + (size_t)256 * B);
-    if (B > N || smem > 200 * 1024) return false;
+    if (B > N || smem > 227 * 1024) return false;      // the opt-in maximum per CTA
     if (ensure(c, c->s_u, (size_t)nbands * c->plan.nr * sizeof(C))) return false;
     if (cudaFuncSetAttribute(k_gather_fft<C, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return false;

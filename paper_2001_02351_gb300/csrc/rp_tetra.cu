@@ -703,7 +703,8 @@ cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double
     const long long K = (long long)c->nk * c->nemp * c->nocc;
     const int bs = 64;
     // frequencies per grid row: all of them when the pairs alone fill the GPU
-    const int fch = K >= 4LL * 152 * bs ? nf : std::max(1, (int)((nf * K + 4LL * 152 * bs - 1) / (4LL * 152 * bs)));
+    const long long fill = 4LL * c->num_sms * bs;
+    const int fch = K >= fill ? nf : std::max(1, (int)((nf * K + fill - 1) / fill));
     dim3 grid((unsigned)((K + bs - 1) / bs), (unsigned)((nf + fch - 1) / fch));
     const size_t smem = (size_t)24 * (fp32 ? TT_FIELDS32 : TT_FIELDS) * bs * (fp32 ? sizeof(float) : sizeof(double));
     if (fp32) {

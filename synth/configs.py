@@ -35,6 +35,29 @@ def _mid_gap_cutoff(recip, shift, target, exclude_zero):
     return 0.5 * (e[n - 1] + e[n])
 
 
+def _mid_gap_cutoff_mesh(recip, kmesh, target):
+    """Wave-function cut-off with about `target` points at k = 0, placed in the middle of a gap of
+    the values 1/2|k+G|^2 of every mesh point k, so that no sphere of the mesh has a member on
+    the cut-off (a value on it would make membership depend on rounding)."""
+    from .epm import kmesh_frac
+    vol_bz = abs(np.linalg.det(recip))
+    radius = 2.0 * (3.0 * target * vol_bz / (4.0 * np.pi)) ** (1.0 / 3.0)
+    e0 = _mid_gap_cutoff(recip, (0.0, 0.0, 0.0), target, exclude_zero=False)
+    g = _miller_box(recip, radius, (1.0, 1.0, 1.0))
+    # every value of the mesh within 3% of e0, then the gap whose middle is nearest to e0
+    near = [np.zeros(0)]
+    for k in kmesh_frac(kmesh):
+        e = 0.5 * np.sum(((g + k[None, :]) @ recip) ** 2, axis=1)
+        near.append(e[np.abs(e - e0) <= 0.03 * e0])
+    v = np.unique(np.concatenate(near))
+    tol = 1e-9 * max(1.0, e0)
+    gaps = np.nonzero(np.diff(v) > tol)[0]
+    if gaps.size == 0:
+        raise ValueError("no gap of the mesh's kinetic energies near the cut-off")
+    mids = 0.5 * (v[gaps] + v[gaps + 1])
+    return float(mids[np.argmin(np.abs(mids - e0))])
+
+
 def log_grid(lo, hi, n):
     return lo * (hi / lo) ** (np.arange(n) / (n - 1))
 
@@ -60,11 +83,11 @@ CONFIGS = {
     "precision": dict(cell=("fcc", 10.2), pot=dict(kind="shells", nshell=6, vmin=0.1, vmax=0.3),
                       npw=4000, fft=(48, 48, 48), kmesh=(10, 10, 10), nocc=64, nemp=448, ng=1500,
                       axis="real", freq=np.linspace(0.0, 20.0, 30) / HARTREE_EV,
-                      delta=0.05 / HARTREE_EV, q=[(0.1, 0.0, 0.0)]),
+                      delta=0.05 / HARTREE_EV, q=[(0.1, 0.0, 0.0)], symmetry=True),
     # batched: all 216 q of a 6^3 mesh, NG 300..900 per q, 24 imaginary frequencies
     "batched": dict(cell=("fcc", 10.2), pot=dict(kind="shells", nshell=6, vmin=0.1, vmax=0.3),
                     npw=1200, fft=(32, 32, 32), kmesh=(6, 6, 6), nocc=16, nemp=64, ng=(300, 900),
-                    axis="imag", freq=log_grid(0.01, 2.0, 24), delta=0.0, q="all"),
+                    axis="imag", freq=log_grid(0.01, 2.0, 24), delta=0.0, q="all", symmetry=True),
     # large: simple-cubic a=20 bohr, 64 Gaussian "atoms", 2^3 mesh, 256+1024 bands
     "large": dict(cell=("sc", 20.0), pot=dict(kind="atoms", natoms=64, amin=0.5, amax=1.5, smin=0.8, smax=1.6),
                   npw=9000, fft=(72, 72, 72), kmesh=(2, 2, 2), nocc=256, nemp=1024, ng=4000,
@@ -107,9 +130,14 @@ def make_workload(name, crpa=False, cache=True, workers=None, **overrides):
     kind, a = spec["cell"]
     cell = fcc_cell(a) if kind == "fcc" else sc_cell(a)
     nband = spec["nocc"] + spec["nemp"]
-    ecut_psi = _mid_gap_cutoff(cell.recip, (0.0, 0.0, 0.0), spec["npw"], exclude_zero=False)
-    key = hashlib.sha1(repr((name, seed, spec["kmesh"], ecut_psi, nband, spec["pot"], a, kind)).encode()).hexdigest()[:16]
+    ecut_psi = _mid_gap_cutoff_mesh(cell.recip, spec["kmesh"], spec["npw"])
+    symmetry = bool(spec.get("symmetry", False))
+    key = hashlib.sha1(repr((name, seed, spec["kmesh"], ecut_psi, nband, spec["pot"], a, kind,
+                             symmetry)).encode()).hexdigest()[:16]
     path = os.path.join(_cache_dir(), f"{name}_{key}.npz")
+    # band sets of several GB are regenerated rather than written to and read from disk
+    big = np.prod(spec["kmesh"]) * nband * spec["npw"] * 16 > (2 << 30)
+    cache = cache and not big
     bands = None
     if cache and os.path.exists(path):
         z = np.load(path, allow_pickle=False)
@@ -117,7 +145,8 @@ def make_workload(name, crpa=False, cache=True, workers=None, **overrides):
                       miller=z["miller"], coef=z["coef"], energy=z["energy"], ecut_psi=float(ecut_psi),
                       meta={"seed": seed, "cached": True})
     if bands is None:
-        bands = make_bands(cell, spec["kmesh"], ecut_psi, nband, spec["pot"], seed, workers=workers)
+        bands = make_bands(cell, spec["kmesh"], ecut_psi, nband, spec["pot"], seed, workers=workers,
+                           symmetry=symmetry)
         if cache:
             tmp = path + ".tmp.npz"
             np.savez(tmp, kfrac=bands.kfrac, npw=bands.npw, miller=bands.miller,

@@ -6,6 +6,14 @@ lowest `nband` states.  The plane-wave set per k is the sphere
 eigenvector is multiplied by a seeded random phase so that no accidental
 reality of the coefficients hides a conjugation error downstream.
 
+With `symmetry=True` (shell potential only) H_k is diagonalised only at one mesh point of each
+orbit of the cube's 48 rotations and the other points are filled by rotating its eigenvectors:
+V depends on |G| alone and is real and even, so for a rotation R, with S the integer matrix of R
+on fractional reciprocal coordinates (row vectors: (k S) B = R (k B)) and R k = k' + G_s (k' on
+the mesh), the coefficients C_{k'}(G S + G_s) = C_k(G) are eigenvectors of H_{k'} with the same
+energies.  The resulting sets are as valid as directly computed ones (any orthonormal basis of a
+degenerate subspace is), and they cost one diagonalisation per orbit.
+
 Two potentials are provided:
   * "shells": V constant on the first n reciprocal-lattice shells, magnitudes
     uniform in [vmin, vmax] Ha with random sign (real, inversion symmetric);
@@ -153,12 +161,69 @@ def _cuda_in_process():
         return False
 
 
-def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None):
-    """Diagonalise H_k on the whole mesh; returns zero-padded arrays (see Bands)."""
+def cubic_rotations(recip):
+    """Integer matrices S of the rotations R of the cube (the 48 signed permutations of the
+    Cartesian axes) that map the reciprocal lattice onto itself: (k S) B = R (k B) for fractional
+    row vectors k and B the rows b1, b2, b3."""
+    import itertools
+    B = np.asarray(recip, dtype=np.float64)
+    Binv = np.linalg.inv(B)
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1.0, -1.0), repeat=3):
+            R = np.zeros((3, 3))
+            for i in range(3):
+                R[i, perm[i]] = signs[i]
+            S = B @ R.T @ Binv
+            Si = np.rint(S)
+            if np.abs(S - Si).max() < 1e-9:
+                out.append(Si.astype(np.int64))
+    return out
+
+
+def irreducible_mesh(kmesh, rotations):
+    """For every mesh point k': (index of its orbit's representative k, S, G_s) with
+    k S = k' + G_s, k' the mesh point in [0, 1)^3.  Representatives map to themselves with S = 1."""
+    n = np.asarray(kmesh, dtype=np.int64)
+    kf = kmesh_frac(n)
+    nk = kf.shape[0]
+    idx = np.rint(kf * n).astype(np.int64)
+    rep = -np.ones(nk, dtype=np.int64)
+    rot = [None] * nk
+    shift = np.zeros((nk, 3), dtype=np.int64)
+    for k in range(nk):
+        if rep[k] >= 0:
+            continue
+        for S in rotations:
+            jf = ((idx[k] / n) @ S) * n              # n * (k S), component-wise
+            j = np.rint(jf).astype(np.int64)
+            if np.abs(jf - j).max() > 1e-9:          # the rotation leaves the mesh
+                continue
+            jm = np.mod(j, n)
+            kk = int((jm[0] * n[1] + jm[1]) * n[2] + jm[2])
+            if rep[kk] >= 0:
+                continue
+            rep[kk] = k
+            rot[kk] = S
+            shift[kk] = (j - jm) // n
+    return rep, rot, shift
+
+
+def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None, symmetry=False):
+    """Diagonalise H_k on the whole mesh (or on one point per orbit of the cube's rotations and
+    rotate, `symmetry=True`, shell potential only); returns zero-padded arrays (see Bands)."""
     rng = np.random.default_rng(seed)
     vfun, meta = _potential_fn(cell, pot, rng)
     kf = kmesh_frac(kmesh)
     nk = kf.shape[0]
+    if symmetry:
+        if pot["kind"] != "shells":
+            raise ValueError("rotating eigenvectors needs the shell potential (V a function of |G|)")
+        rots = cubic_rotations(cell.recip)
+        rep, rot, gshift = irreducible_mesh(kmesh, rots)
+        reps = np.unique(rep)
+    else:
+        reps = np.arange(nk)
     # potential table over all Miller differences that can occur
     gmax = np.sqrt(2.0 * ecut_psi) + np.linalg.norm(cell.recip, axis=1).max()
     a_len = np.linalg.norm(cell.lat, axis=1)
@@ -167,10 +232,10 @@ def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None):
     grid = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1)
     vtab = vfun(grid.reshape(-1, 3)).reshape(grid.shape[:3])
     vofs = np.array([L, L, L])
-    jobs = [(kf[i], cell.recip, ecut_psi, nband, vtab, vofs) for i in range(nk)]
+    jobs = [(kf[i], cell.recip, ecut_psi, nband, vtab, vofs) for i in reps]
     if workers is None:
         workers = min(16, os.cpu_count() or 1)
-    work = nk * float(max(1, len(psi_sphere(cell.recip, kf[0], ecut_psi)))) ** 3
+    work = len(reps) * float(max(1, len(psi_sphere(cell.recip, kf[0], ecut_psi)))) ** 3
     if work > 2e10 and workers > 1:
         import concurrent.futures as cf
         import multiprocessing as mp
@@ -193,6 +258,20 @@ def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None):
                     os.environ[v] = val
     else:
         res = [_solve_k(j) for j in jobs]
+    if symmetry:
+        # rotate each orbit representative's eigenvectors onto the other points of its orbit
+        by_rep = {int(r): res[i] for i, r in enumerate(reps)}
+        full = []
+        for k in range(nk):
+            m, e, v = by_rep[int(rep[k])]
+            if rep[k] == k:
+                full.append((m, e, v))
+                continue
+            mk = m.astype(np.int64) @ rot[k] + gshift[k]      # G S + G_s
+            order = np.lexsort((mk[:, 2], mk[:, 1], mk[:, 0]))
+            full.append((mk[order].astype(np.int32), e, v[:, order]))
+        res = full
+        meta.update({"irreducible_k": int(len(reps))})
     npw = np.array([r_[0].shape[0] for r_ in res], dtype=np.int32)
     if np.any(npw < nband):
         raise ValueError("plane-wave set smaller than the number of bands")
@@ -203,7 +282,8 @@ def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None):
     phase = np.exp(2j * np.pi * rng.uniform(size=(nk, nband)))
     for i, (m, e, v) in enumerate(res):
         miller[i, : m.shape[0]] = m
-        coef[i, :, : m.shape[0]] = v * phase[i][:, None]
+        coef[i, :, : m.shape[0]] = v
+        coef[i, :, : m.shape[0]] *= phase[i][:, None]
         energy[i] = e
     meta.update({"seed": seed})
     return Bands(cell=cell, kmesh=tuple(int(x) for x in kmesh), kfrac=kf, npw=npw,

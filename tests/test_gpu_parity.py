@@ -231,6 +231,74 @@ def test_errors_are_reported():
     assert np.allclose(W[0], np.diag(vs * vs), rtol=1e-14, atol=0)
 
 
+def test_bad_pivot_in_one_of_several_frequencies_cooperative():
+    """The cooperative Dyson kernel runs all frequencies in one grid with shared barriers: one
+    frequency with a non-finite chi0 is reported as RP_ERR_NUMERIC (through rp_check_numeric after
+    an asynchronous call), while the other frequency's W is still exact (chi0 = 0 gives W = v).
+    NG is about 150, so the cooperative form (several CTAs per frequency) is the one that runs."""
+    from synth.configs import _mid_gap_cutoff
+    wl = workload("tiny")
+    b = wl.bands
+    q = wl.q[0]
+    cut = _mid_gap_cutoff(wl.cell.recip, q, 150, exclude_zero=True)
+    assert cut < b.ecut_psi
+    ctx = rp.Context(b.cell.lat, b.kmesh, wl.fft, b.ecut_psi, cut)
+    nb = wl.nocc + wl.nemp
+    ctx.load_bands(wl.nocc, b.npw, b.miller, b.coef[:, :nb], b.energy[:, :nb])
+    G = OL.eps_sphere(wl.cell.lat, q, cut)
+    assert len(G) >= 128
+    vs = OD.coulomb_sqrt(wl.cell.lat, q, G)
+    chi = torch.zeros((3, len(G), len(G)), dtype=torch.complex128, device="cuda")
+    chi[1, :, 0] = float("nan")
+    W, _ = ctx.rp_solve_w(q, chi)
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_check_numeric()
+    assert e.value.code == rp.RP_ERR_NUMERIC
+    Wh = W.cpu().numpy()
+    for f in (0, 2):
+        assert np.allclose(Wh[f], np.diag(vs * vs), rtol=1e-14, atol=0)
+    # the flag was cleared: the next solve is clean
+    W, _ = ctx.rp_solve_w(q, torch.zeros_like(chi))
+    ctx.rp_check_numeric()
+    assert np.allclose(W.cpu().numpy()[1], np.diag(vs * vs), rtol=1e-14, atol=0)
+
+
+def test_contraction_wait_that_gives_up_is_reported():
+    """With the wait limit set to zero the BF16x3 contraction's pipeline waits give up at once:
+    the kernel returns through its teardown (in-flight copies and MMAs drained with the fixed
+    limit) and the call reports RP_ERR_TIMEOUT, on host buffers directly and, for device buffers,
+    through rp_check_numeric.  With the default limit restored the same context is correct again."""
+    rng = np.random.default_rng(5)
+    ng, K, nf = 150, 5000, 2
+    M = rng.standard_normal((ng, K)) + 1j * rng.standard_normal((ng, K))
+    w = rng.standard_normal((nf, K)) + 1j * rng.standard_normal((nf, K))
+    ctx = _ctx(workload("micro"))
+    ctx.rp_set_wait_limit(0)
+    codes = []
+    for _ in range(3):
+        try:
+            ctx.rp_contract_chi0(M, w, precision=rp.RP_BF16X3)
+            codes.append(rp.RP_OK)
+        except rp.RPError as ex:
+            codes.append(ex.code)
+    assert set(codes) <= {rp.RP_OK, rp.RP_ERR_TIMEOUT}
+    assert rp.RP_ERR_TIMEOUT in codes
+    Md = torch.from_numpy(M).cuda()
+    wd = torch.from_numpy(w).cuda()
+    seen = False
+    for _ in range(3):
+        ctx.rp_contract_chi0(Md, wd, precision=rp.RP_BF16X3)
+        try:
+            ctx.rp_check_numeric()
+        except rp.RPError as ex:
+            assert ex.code == rp.RP_ERR_TIMEOUT
+            seen = True
+    assert seen
+    ctx.rp_set_wait_limit(2_000_000_000)
+    got = ctx.rp_contract_chi0(M, w, precision=rp.RP_BF16X3)
+    assert np.all(_rel_fro(got, OC.chi0(M, w)) < 1e-4)
+
+
 # ---- BF16x3 split-precision contraction on tcgen05 ----
 # Each operand is carried as two bf16 (16 significant bits); the dropped lo*lo term and the
 # FP32 accumulation inside each 8192-real window bound the error near 2^-16 per product, which
@@ -360,3 +428,25 @@ def test_batched_q_with_uneven_spheres_tiny():
         T = OL.tail_sphere(wl.cell.lat, q, cut, wl.bands.ecut_psi)
         assert np.allclose(tail, OD.tail(wl.cell.lat, q, T), rtol=1e-14, atol=0)
     assert len(set(sizes)) == 3
+
+
+def test_kset_builds_partition_the_mesh(tiny, tiny_ref):
+    """rp_build_chi0_kset: the chi0 of a k subset is the oracle's sum over those k points' pairs
+    (full-mesh weights), and the subsets of a partition of the mesh add up to the whole build."""
+    q = tiny.q[0]
+    ctx = _ctx(tiny)
+    nk = tiny.bands.kfrac.shape[0]
+    ks = [41, 3, 17, 18, 19, 60]                 # unsorted, with a run of consecutive points
+    G = OL.eps_sphere(tiny.cell.lat, q, tiny.ecut_eps[0])
+    M = OP.pair_density(tiny.bands, tiny.nocc, tiny.nemp, q, G, fft=tiny.fft, k_list=sorted(ks))
+    ref = OC.chi0(M, OC.pair_weights(tiny, q, k_list=sorted(ks)))
+    for p, tol in ((rp.RP_FP64_NATIVE, 1e-11), (rp.RP_BF16X3, BF16X3_TOL)):
+        got = ctx.rp_build_chi0_kset(q, ks, _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, p)
+        assert np.all(_rel_fro(got, ref) < tol)
+    parts = [list(range(0, nk, 2)), list(range(1, nk, 2))]
+    tot = sum(ctx.rp_build_chi0_kset(q, part, _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta,
+                                     rp.RP_FP64_NATIVE) for part in parts)
+    assert np.all(_rel_fro(tot, tiny_ref[0]) < 1e-11)
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_build_chi0_kset(q, [1, 1], _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, rp.RP_FP64_NATIVE)
+    assert e.value.code == rp.RP_ERR_ARG

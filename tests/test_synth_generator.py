@@ -70,3 +70,41 @@ def test_plane_wave_set_is_the_psi_sphere(micro_fresh):
         got = {tuple(g) for g in b.miller[k, :int(b.npw[k])]}
         assert got == want
         assert np.abs(box[e <= b.ecut_psi]).max() < 8     # the box was large enough
+
+
+def test_rotated_band_sets_match_direct_diagonalisation():
+    """Band sets filled by rotating one eigenvector set per orbit of the cube's 48 rotations
+    (the shell potential depends on |G| alone): at every mesh point the energies equal those of
+    a direct diagonalisation, the Miller sets are the same spheres, and the rotated vectors are
+    orthonormal eigenvectors of H_k rebuilt from its definition."""
+    from synth import fcc_cell, make_bands
+    from synth.configs import _mid_gap_cutoff_mesh
+    cell = fcc_cell(10.2)
+    pot = dict(kind="shells", nshell=6, vmin=0.1, vmax=0.3)
+    ec = _mid_gap_cutoff_mesh(cell.recip, (4, 4, 4), 300)
+    direct = make_bands(cell, (4, 4, 4), ec, 16, pot, seed=3, workers=1)
+    rot = make_bands(cell, (4, 4, 4), ec, 16, pot, seed=3, workers=1, symmetry=True)
+    assert rot.meta["irreducible_k"] == 8
+    assert np.abs(direct.energy - rot.energy).max() < 1e-10
+    assert np.array_equal(direct.npw, rot.npw) and np.array_equal(direct.miller, rot.miller)
+    for k in range(rot.kfrac.shape[0]):
+        n = int(rot.npw[k])
+        H = _hamiltonian(rot, k)
+        C = rot.coef[k, :, :n]
+        assert np.abs(H @ C.T - C.T * rot.energy[k][None, :]).max() < 1e-10
+        assert np.abs(C.conj() @ C.T - np.eye(C.shape[0])).max() < 1e-12
+
+
+def test_psi_cutoff_off_every_mesh_sphere():
+    """The wave-function cut-off lies in a gap of 1/2|k+G|^2 over every mesh point, so that no
+    sphere membership depends on the rounding of a value equal to the cut-off."""
+    from synth import fcc_cell
+    from synth.configs import _mid_gap_cutoff_mesh
+    from synth.epm import _miller_box, kmesh_frac
+    cell = fcc_cell(10.2)
+    for mesh, target in (((4, 4, 4), 300), ((3, 3, 3), 110)):
+        ec = _mid_gap_cutoff_mesh(cell.recip, mesh, target)
+        g = _miller_box(cell.recip, np.sqrt(2.0 * ec), (1.0, 1.0, 1.0))
+        for k in kmesh_frac(mesh):
+            e = 0.5 * np.sum(((g + k) @ cell.recip) ** 2, axis=1)
+            assert np.abs(e - ec).min() > 1e-6 * ec

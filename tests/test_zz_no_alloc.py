@@ -41,11 +41,14 @@ def test_static_scratch_contraction_matches_allocating_path():
                                                stream)
             assert code == rp.RP_OK
             outs.append(out)
+        # no device wait gave up in the last call (the status call allocates nothing either)
+        assert lib.rp_contract_chi0_static_status(stream) == rp.RP_OK
         torch.cuda.synchronize()
         for out in outs:
             assert torch.isfinite(out).all()
             assert _rel(out, ref) < BF16X3_TOL
-        assert torch.equal(outs[0], outs[1])
+        # the FP64 flushes are atomic additions, so the summation order may differ between calls
+        assert _rel(outs[0], outs[1]) < 1e-12
 
 
 def test_static_scratch_rejects_oversize():
