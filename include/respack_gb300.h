@@ -201,6 +201,20 @@ int rp_solve_w_batched(rp_ctx* ctx, int nq, const double* q_frac, const double* 
  *   else RP_ERR_NUMERIC if an rp_solve_w met a bad pivot, else RP_OK.  Both flags are cleared. */
 int rp_check_numeric(rp_ctx* ctx);
 
+/* rp_tune_contraction -- tile autotuner of the RP_BF16X3 contraction kernel (no counterpart in the
+ *   paper).  The kernel multiplies tiles of 128 weighted rows by BN rows of M (BN one of 160, 192,
+ *   208, 224, 256); for the shape ng x K pairs x nfreq it times one launch of each BN on seeded
+ *   synthetic operands in library scratch (CUDA events, after a warm-up launch), records the fastest
+ *   for this ng in the context (used by every later RP_BF16X3 contraction with this NG) and
+ *   returns it in *bn_out.  ms_out: NULL or double[5], the times of the candidates in the order
+ *   above.  Synchronous.  Without a tuned or set choice the kernel takes the BN that pads NG
+ *   least (the wider on a tie). */
+int rp_tune_contraction(rp_ctx* ctx, int ng, long long K, int nfreq, int* bn_out, double* ms_out);
+
+/* rp_set_contraction_tile -- records BN for contractions with this ng (a choice cached from an
+ *   earlier rp_tune_contraction); bn = 0 removes the entry.  RP_ERR_ARG for a BN not built. */
+int rp_set_contraction_tile(rp_ctx* ctx, int ng, int bn);
+
 /* rp_set_wait_limit -- testing aid with no counterpart in the paper: the time after which a
  *   bounded device wait of the context's RP_BF16X3 contraction kernel gives up (default 2e9 ns).
  *   A wait that gives up sets the context's timeout flag and the kernel returns through its

@@ -7,9 +7,9 @@ this package only marshals arguments.  Build it with `paper_2001_02351_gb300.bui
 from ._lib import (Context, RPError, context_for, library, EXPORTS, RP_OK, RP_ERR_ARG, RP_ERR_STATE,
                    RP_ERR_OOM, RP_ERR_CUDA, RP_ERR_NUMERIC, RP_ERR_TIMEOUT, RP_ERR_UNSUPPORTED,
                    RP_FP64_NATIVE, RP_FP64_EMULATED, RP_TF32X3, RP_BF16X3, RP_AXIS_REAL, RP_AXIS_IMAG,
-                   RP_TIME_ORDERED, RP_RETARDED)
+                   RP_TIME_ORDERED, RP_RETARDED, TILE_WIDTHS)
 
 __all__ = ["Context", "RPError", "context_for", "library", "EXPORTS", "RP_OK", "RP_ERR_ARG", "RP_ERR_STATE",
            "RP_ERR_OOM", "RP_ERR_CUDA", "RP_ERR_NUMERIC", "RP_ERR_TIMEOUT", "RP_ERR_UNSUPPORTED",
            "RP_FP64_NATIVE", "RP_FP64_EMULATED", "RP_TF32X3", "RP_BF16X3", "RP_AXIS_REAL", "RP_AXIS_IMAG",
-           "RP_TIME_ORDERED", "RP_RETARDED"]
+           "RP_TIME_ORDERED", "RP_RETARDED", "TILE_WIDTHS"]

@@ -16,6 +16,7 @@ RP_OK, RP_ERR_ARG, RP_ERR_STATE, RP_ERR_OOM, RP_ERR_CUDA, RP_ERR_NUMERIC, RP_ERR
     0, -1, -2, -3, -4, -5, -6, -7
 RP_FP64_NATIVE, RP_FP64_EMULATED, RP_TF32X3, RP_BF16X3 = 0, 1, 2, 3
 RP_AXIS_REAL, RP_AXIS_IMAG = 0, 1
+TILE_WIDTHS = (160, 192, 208, 224, 256)     # raw rows per tile of the BF16x3 contraction kernel
 RP_TIME_ORDERED, RP_RETARDED = 0, 1
 
 _STATUS = {0: "RP_OK", -1: "RP_ERR_ARG", -2: "RP_ERR_STATE", -3: "RP_ERR_OOM", -4: "RP_ERR_CUDA",
@@ -26,7 +27,7 @@ EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density"
            "rp_contract_chi0", "rp_build_chi0", "rp_solve_w", "rp_check_numeric", "rp_profile_enable",
            "rp_profile_read", "rp_last_error", "rp_destroy", "rp_contract_chi0_static", "rp_sphere_size_at",
            "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_contract_chi0_static_status",
-           "rp_build_chi0_kset"]
+           "rp_build_chi0_kset", "rp_tune_contraction", "rp_set_contraction_tile"]
 
 
 class RPError(RuntimeError):
@@ -67,6 +68,8 @@ def library():
         "rp_solve_w_batched": (I, [P, I, P, P, I, P, P, P, I, P]),
         "rp_set_wait_limit": (I, [P, LL]),
         "rp_build_chi0_kset": (I, [P, P, I, P, I, I, I, P, D, D, D, I, P, I, P]),
+        "rp_tune_contraction": (I, [P, I, LL, I, ctypes.POINTER(I), P]),
+        "rp_set_contraction_tile": (I, [P, I, I]),
         "rp_contract_chi0_static_status": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -297,6 +300,42 @@ class Context:
 
     def rp_check_numeric(self):
         self._check(self._lib.rp_check_numeric(self._h))
+
+    def rp_tune_contraction(self, ng, K, nfreq):
+        """(chosen BN, {BN: ms}) for BF16x3 contractions of this shape; the choice is kept in the context."""
+        bn = ctypes.c_int()
+        ms = np.zeros(5)
+        self._check(self._lib.rp_tune_contraction(self._h, int(ng), int(K), int(nfreq), ctypes.byref(bn),
+                                                  ms.ctypes.data_as(ctypes.c_void_p)))
+        return bn.value, dict(zip(TILE_WIDTHS, ms.tolist()))
+
+    def rp_set_contraction_tile(self, ng, bn):
+        self._check(self._lib.rp_set_contraction_tile(self._h, int(ng), int(bn)))
+
+    def tuned_tile(self, ng, K, nfreq, cache_path=None):
+        """The contraction tile for this shape from a JSON cache keyed by device and shape, tuned and
+        written back when missing (argument handling only; the timing runs in the library)."""
+        import json
+        import torch
+        key = f"{torch.cuda.get_device_name()}|ng={int(ng)}|K={int(K)}|nf={int(nfreq)}"
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            try:
+                cache = json.load(open(cache_path))
+            except (OSError, ValueError):
+                cache = {}
+        if key in cache:
+            self.rp_set_contraction_tile(ng, cache[key]["bn"])
+            return cache[key]["bn"], cache[key]["ms"]
+        bn, ms = self.rp_tune_contraction(ng, K, nfreq)
+        if cache_path:
+            cache[key] = {"bn": bn, "ms": {str(k): v for k, v in ms.items()}}
+            os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+            tmp = cache_path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, cache_path)
+        return bn, ms
 
     def rp_set_wait_limit(self, limit_ns):
         self._check(self._lib.rp_set_wait_limit(self._h, int(limit_ns)))

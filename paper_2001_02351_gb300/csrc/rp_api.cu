@@ -571,6 +571,13 @@ int rp_tetra_weights(rp_ctx* c, const double q[3], int axis, int ordering, int n
     return finish(c, st, on_device);
 }
 
+// raw rows per tile of the BF16x3 contraction for this NG: the tuned or set choice, else 0 (the
+// launcher's least-padding rule)
+static int tile_for(const rp_ctx* c, int ng) {
+    auto it = c->tile_bn.find(ng);
+    return it == c->tile_bn.end() ? 0 : it->second;
+}
+
 // chi (+)= M[:, col0m .. col0m+K) diag(w[f][col0w ..]) M^H with the selected precision.
 // For RP_BF16X3 the caller zeroes chi before the first block.
 static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, long long ldm, long long col0m,
@@ -602,7 +609,7 @@ static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, lon
     if (e == cudaSuccess) {
         prof_begin(c, 3, st);
         e = launch_contract_bf16x3_core(c->s_hi.p, c->s_lo.p, K, ng, nfreq, c->s_w32.p, chi, (int*)c->d_err.p + 1,
-                                        c->num_sms, c->wait_ns, st);
+                                        c->num_sms, c->wait_ns, st, tile_for(c, ng));
         prof_end(c, 3, st, 1);
     }
     return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "bf16x3 contraction");
@@ -735,6 +742,64 @@ int rp_check_numeric(rp_ctx* c) {
         return fail(c, RP_ERR_TIMEOUT, buf);
     }
     if (flag[0]) return fail(c, RP_ERR_NUMERIC, "zero or non-finite pivot in the Dyson solve");
+    return RP_OK;
+}
+
+int rp_set_contraction_tile(rp_ctx* c, int ng, int bn) {
+    if (!c) return RP_ERR_ARG;
+    if (ng < 1) return fail(c, RP_ERR_ARG, "ng < 1");
+    if (bn == 0) {
+        c->tile_bn.erase(ng);
+        return RP_OK;
+    }
+    if (!tc_bn_supported(bn)) return fail(c, RP_ERR_ARG, "tile width not built");
+    c->tile_bn[ng] = bn;
+    return RP_OK;
+}
+
+int rp_tune_contraction(rp_ctx* c, int ng, long long K, int nfreq, int* bn_out, double* ms_out) {
+    if (!c) return RP_ERR_ARG;
+    if (ng < 1 || K < 1 || nfreq < 1 || !bn_out) return fail(c, RP_ERR_ARG, "bad tuning shape");
+    cudaStream_t st = nullptr;
+    const long long kp2 = tc_kp2(K);
+    int s;
+    if ((s = ensure(c, c->s_hi, (size_t)ng * kp2 * 2)) || (s = ensure(c, c->s_lo, (size_t)ng * kp2 * 2)) ||
+        (s = ensure(c, c->s_w32, (size_t)tc_wrows(nfreq) * (kp2 / 2) * sizeof(float2))) ||
+        (s = ensure(c, c->s_chi, (size_t)nfreq * ng * ng * sizeof(double2))))
+        return s;
+    cudaError_t e = launch_fill_tune_operands(c->s_hi.p, c->s_lo.p, (long long)ng * kp2, c->s_w32.p,
+                                              (long long)tc_wrows(nfreq) * (kp2 / 2), st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tuning operands");
+    int cand[16];
+    const int nc = tc_bn_candidates(cand);
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "events");
+    int best = 0;
+    float best_ms = 0.0f;
+    for (int i = 0; i < nc && e == cudaSuccess; ++i) {
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {      // the first run warms up
+            e = cudaEventRecord(ev[0], st);
+            if (e == cudaSuccess)
+                e = launch_contract_bf16x3_core(c->s_hi.p, c->s_lo.p, K, ng, nfreq, c->s_w32.p, (double2*)c->s_chi.p,
+                                                (int*)c->d_err.p + 1, c->num_sms, c->wait_ns, st, cand[i]);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        }
+        if (ms_out) ms_out[i] = ms;
+        if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
+            best = cand[i];
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tuning run");
+    if ((s = check_timeout(c))) return s;
+    c->tile_bn[ng] = best;
+    *bn_out = best;
     return RP_OK;
 }
 

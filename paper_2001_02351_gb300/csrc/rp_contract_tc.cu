@@ -9,16 +9,20 @@
 // a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs), accumulated in FP32 in tensor memory over a
 // window of TC_FLUSH_STAGES stages and then added into the FP64 result.
 //
-// Tile (one tcgen05.mma M = 128, N = 208, K = 16 per step): the 128 rows of the MMA's A side are
+// Tile (one tcgen05.mma M = 128, N = BN, K = 16 per step): the 128 rows of the MMA's A side are
 // built in shared memory from 32 rows M[G'] and the weights of two frequencies
-// (re f0 | im f0 | re f1 | im f1, 32 rows each); the 208 rows of the B side are raw rows M[G],
-// loaded by TMA.  Padding of NG is to multiples of 32 and 208 only.  A job is a pair of such
+// (re f0 | im f0 | re f1 | im f1, 32 rows each); the BN rows of the B side are raw rows M[G],
+// loaded by TMA.  BN (160 .. 256, a template parameter) is chosen per NG by the launcher (least
+// padding of NG to a multiple of BN, or a measured choice); NG pads to multiples of 32 and BN
+// only.  A job is a pair of such
 // tiles (four frequencies, the same 32 G' and the same 208 G) over one accumulation window: each
 // stage of raw rows, the operand every tile re-reads from L2, feeds both tiles, and one load of
 // M[G'] feeds four frequencies.  The two tiles have their own accumulators in tensor memory and
 // their own built buffer, so the builders make one tile while the tensor core multiplies the
 // other.  The windows of a tile are added into chi with FP64 atomics, so jobs spread evenly over
-// the SMs.
+// the SMs.  A tile whose two frequencies both lie beyond nf (the last group when nf = 4 n + 2, or
+// nf <= 2) is not built, multiplied or flushed; each role counts the stages and jobs of each tile
+// separately, so the barrier phases stay paired.
 //
 // CTA: 14 warps.  warp 0 = TMA producer (raw rows M[G], rows M[G'], the stage's weights of the four
 // frequencies; the stages two ahead are prefetched into L2), warp 1 = MMA issuer, warps 2-9 =
@@ -37,25 +41,34 @@ namespace rp {
 #define TC_NS 2                 // load stages (two, plus L2 prefetch of the stages ahead)
 #define TC_BM 128               // built rows per tile (MMA M)
 #define TC_GN 32                // G' per tile and frequency
-#define TC_BN 208               // raw G rows per tile (MMA N)
 #define TC_BK 64                // reals per stage
 #define TC_FLUSH_STAGES 128     // stages per FP32 accumulation window (8192 reals)
 #define TC_THREADS 448
 #define TC_NBUILD 256           // builder threads (warps 2-9); epilogue = warps 10-13
-#define TC_TMEM_COLS 512        // the accumulators of the two tiles, TC_BN columns each, 256 apart
+#define TC_TMEM_COLS 512        // the accumulators of the two tiles, BN columns each, 256 apart
 #define TC_NF 4                 // frequencies per job (two tiles of two)
 
-#define TC_RAW_BYTES (TC_BN * TC_BK * 2)          // 26 KB (26 swizzle atoms)
 #define TC_R_BYTES (TC_GN * TC_BK * 2)            // 4 KB
 #define TC_W_BYTES (TC_BK / 2 * 8)                // 32 complex float weights = 256 B
-#define TC_OFF_R (2 * TC_RAW_BYTES)
-#define TC_OFF_W (2 * TC_RAW_BYTES + 2 * TC_R_BYTES)
-#define TC_STAGE_LOAD (2 * TC_RAW_BYTES + 2 * TC_R_BYTES + TC_NF * TC_W_BYTES)
-#define TC_STAGE_BYTES (TC_OFF_W + 1024)          // 61 KB, keeps 1024-B alignment
 #define TC_B_BYTES (TC_BM * TC_BK * 2)            // 16 KB (128 built rows)
-#define TC_SMEM_B0 (TC_NS * TC_STAGE_BYTES)
-#define TC_SMEM_BAR (TC_SMEM_B0 + 2 * 2 * TC_B_BYTES)
-#define TC_SMEM_TOTAL (TC_SMEM_BAR + 256 + 1024)
+
+// shared-memory layout for BN raw rows per tile; every swizzled buffer starts on 1024 B
+template <int BN>
+struct TcL {
+    static constexpr int RAW = BN * TC_BK * 2;                       // one bf16 half of the raw rows
+    static constexpr int OFF_R = 2 * RAW;
+    static constexpr int OFF_W = 2 * RAW + 2 * TC_R_BYTES;
+    static constexpr int STAGE_LOAD = 2 * RAW + 2 * TC_R_BYTES + TC_NF * TC_W_BYTES;
+    static constexpr int STAGE = OFF_W + 1024;
+    static constexpr int B0 = TC_NS * STAGE;
+    static constexpr int BAR = B0 + 2 * 2 * TC_B_BYTES;
+    static constexpr int TOTAL = BAR + 256 + 1024;
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N: a multiple of 16 up to 256");
+    static_assert(RAW % 1024 == 0 && OFF_W % 1024 == 0, "swizzle atoms aligned");
+    static_assert(256 + BN <= TC_TMEM_COLS, "two accumulators fit the allocation");
+    static_assert(TOTAL <= 232448, "shared memory per CTA");
+    static_assert(TC_NF * TC_W_BYTES <= STAGE - OFF_W, "weights of a stage fit their region");
+};
 
 #define TC_WAIT_NS 2000000000ULL   // default limit of a wait, and the limit of the teardown's drains
 
@@ -122,16 +135,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// kind::f16 instruction descriptor: D f32, A bf16, B bf16, both K-major, M = 128, N = TC_BN
+// kind::f16 instruction descriptor: D f32, A bf16, B bf16, both K-major, M = 128, N = BN
+template <int BN>
 __host__ __device__ constexpr uint32_t tc_idesc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 }
 
+template <int BN>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(tc_idesc()), "r"(accumulate));
+        "l"(a), "l"(b), "r"(tc_idesc<BN>()), "r"(accumulate));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -161,19 +176,40 @@ struct TcArgs {
     unsigned long long wait_ns;   // limit of the pipeline's waits (the teardown drains use TC_WAIT_NS)
 };
 
-static_assert(TC_BN % 16 == 0 && TC_BN <= 256 && TC_BN % 32 == 16, "epilogue reads TC_BN in 32- and one 16-column load");
-static_assert(TC_BN <= 256 && 256 + TC_BN <= TC_TMEM_COLS, "two accumulators fit the allocation");
-static_assert(TC_SMEM_TOTAL <= 232448, "shared memory per CTA");
-static_assert(TC_NF * TC_W_BYTES <= TC_STAGE_BYTES - TC_OFF_W, "weights of a stage fit their region");
+// tcgen05.ld of 32 or 16 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t src, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(src));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t src, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(src));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 
+template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_contract_bf16x3(const __grid_constant__ CUtensorMap raw_hi, const __grid_constant__ CUtensorMap raw_lo,
                       const __grid_constant__ CUtensorMap row_hi, const __grid_constant__ CUtensorMap row_lo,
                       TcArgs args) {
+    using L = TcL<BN>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar0 = sbase + TC_SMEM_BAR;
+    const uint32_t bar0 = sbase + L::BAR;
     // barriers: full[NS], empty[NS], and per tile t: bready, bfree (its built buffer), accf, acce
     // (its accumulator); done
     auto full = [&](int s) { return bar0 + 8 * s; };
@@ -183,7 +219,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto accf = [&](int t) { return bar0 + 8 * (2 * TC_NS + 4 + t); };
     auto acce = [&](int t) { return bar0 + 8 * (2 * TC_NS + 6 + t); };
     const uint32_t done_bar = bar0 + 8 * (2 * TC_NS + 8);
-    uint32_t* taddr_slot = (uint32_t*)(smem + TC_SMEM_BAR + 8 * (2 * TC_NS + 9));
+    uint32_t* taddr_slot = (uint32_t*)(smem + L::BAR + 8 * (2 * TC_NS + 9));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -218,16 +254,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint64_t lim = args.wait_ns;
     // job -> (accumulation window, group of four frequencies, G' block, G tile); consecutive jobs
     // share a window.  The last block and tile are moved back to end at ng, so that (for ng >=
-    // TC_BN) every box lies inside the arrays; a block or tile writes only the rows from its own
+    // BN) every box lies inside the arrays; a block or tile writes only the rows from its own
     // start (nown, mown) on, so rows covered twice are added once.
+    // tile t of a job in frequency group fq holds frequencies 4 fq + 2 t, + 1: it is live if the first is
+    auto live_tile = [&](int fq, int t) { return TC_NF * fq + 2 * t < args.nf; };
     auto job_tile = [&](int job, int& w0, int& w1, int& fq, int& n0, int& m0, int& nown, int& mown) {
         const int win = job / ntile, t = job % ntile;
         fq = t / (args.nblk * args.mt);
         const int r = t % (args.nblk * args.mt);
         nown = (r / args.mt) * TC_GN;
-        mown = (r % args.mt) * TC_BN;
+        mown = (r % args.mt) * BN;
         n0 = min(nown, max(0, args.ng - TC_GN));
-        m0 = min(mown, max(0, args.ng - TC_BN));
+        m0 = min(mown, max(0, args.ng - BN));
         w0 = win * TC_FLUSH_STAGES;
         w1 = min(nst, w0 + TC_FLUSH_STAGES);
     };
@@ -242,7 +280,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 int w0, w1, fq, n0, m0, nown, mown;
                 job_tile(job, w0, w1, fq, n0, m0, nown, mown);
                 // L2 prefetch only of boxes that lie inside the arrays
-                const bool pf_raw = m0 + TC_BN <= args.ng, pf_row = n0 + TC_GN <= args.ng;
+                const bool pf_raw = m0 + BN <= args.ng, pf_row = n0 + TC_GN <= args.ng;
                 const float2* wrow = args.w32 + (size_t)(TC_NF * fq) * kpad;
                 for (int st = w0; st < w1; ++st, ++sg) {
                     const int s = (int)(sg % TC_NS);
@@ -259,17 +297,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         }
                     }
                     if (!(ok = mbar_wait(empty(s), ph ^ 1, err, 101, lim))) break;
-                    const uint32_t base = sbase + s * TC_STAGE_BYTES;
-                    mbar_expect_tx(full(s), TC_STAGE_LOAD);
+                    const uint32_t base = sbase + s * L::STAGE;
+                    mbar_expect_tx(full(s), L::STAGE_LOAD);
 #pragma unroll
                     for (int fi = 0; fi < TC_NF; ++fi)
-                        bulk_load(base + TC_OFF_W + fi * TC_W_BYTES, wrow + (size_t)fi * kpad + (size_t)st * (TC_BK / 2),
+                        bulk_load(base + L::OFF_W + fi * TC_W_BYTES, wrow + (size_t)fi * kpad + (size_t)st * (TC_BK / 2),
                                   TC_W_BYTES, full(s));
                     const int x = st * TC_BK;
                     tma_load_2d(base, &raw_hi, x, m0, full(s));
-                    tma_load_2d(base + TC_RAW_BYTES, &raw_lo, x, m0, full(s));
-                    tma_load_2d(base + TC_OFF_R, &row_hi, x, n0, full(s));
-                    tma_load_2d(base + TC_OFF_R + TC_R_BYTES, &row_lo, x, n0, full(s));
+                    tma_load_2d(base + L::RAW, &raw_lo, x, m0, full(s));
+                    tma_load_2d(base + L::OFF_R, &row_hi, x, n0, full(s));
+                    tma_load_2d(base + L::OFF_R + TC_R_BYTES, &row_lo, x, n0, full(s));
                 }
             }
             // copies still in flight land before the CTA leaves
@@ -279,42 +317,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            long long sg = 0, cg = 0;
+            long long sg = 0, cs[2] = {0, 0}, cj[2] = {0, 0};   // stages; per tile: live stages, live jobs
             bool ok = true;
-            for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x, ++cg) {
+            for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
                 int w0, w1, fq, n0, m0, nown, mown;
                 job_tile(job, w0, w1, fq, n0, m0, nown, mown);
-                // both accumulators drained by the epilogue of the previous job
+                const bool lv[2] = {live_tile(fq, 0), live_tile(fq, 1)};
+                // the live accumulators drained by the epilogue of their previous job
                 for (int t = 0; t < 2 && ok; ++t)
-                    ok = mbar_wait(acce(t), (uint32_t)((cg & 1) ^ 1), err, 111, lim);
+                    if (lv[t]) ok = mbar_wait(acce(t), (uint32_t)((cj[t] & 1) ^ 1), err, 111, lim);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int st = w0; st < w1; ++st, ++sg) {
                     const int s = (int)(sg % TC_NS);
                     if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 112, lim))) break;
-                    const uint32_t g_hi = sbase + s * TC_STAGE_BYTES, g_lo = g_hi + TC_RAW_BYTES;
+                    const uint32_t g_hi = sbase + s * L::STAGE, g_lo = g_hi + L::RAW;
                     for (int t = 0; t < 2; ++t) {
-                        if (!(ok = mbar_wait(bready(t), (uint32_t)(sg & 1), err, 113, lim))) break;
+                        if (!lv[t]) continue;
+                        if (!(ok = mbar_wait(bready(t), (uint32_t)(cs[t] & 1), err, 113, lim))) break;
+                        ++cs[t];
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t d = tmem + (uint32_t)(t * 256);
-                        const uint32_t b_hi = sbase + TC_SMEM_B0 + t * 2 * TC_B_BYTES, b_lo = b_hi + TC_B_BYTES;
+                        const uint32_t b_hi = sbase + L::B0 + t * 2 * TC_B_BYTES, b_lo = b_hi + TC_B_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < TC_BK / 16; ++kk) {
                             const uint32_t off = kk * 32;
                             const uint32_t first = (st == w0 && kk == 0) ? 0u : 1u;
-                            mma_bf16(d, sw128_desc(b_hi + off), sw128_desc(g_hi + off), first);
-                            mma_bf16(d, sw128_desc(b_hi + off), sw128_desc(g_lo + off), 1u);
-                            mma_bf16(d, sw128_desc(b_lo + off), sw128_desc(g_hi + off), 1u);
+                            mma_bf16<BN>(d, sw128_desc(b_hi + off), sw128_desc(g_hi + off), first);
+                            mma_bf16<BN>(d, sw128_desc(b_hi + off), sw128_desc(g_lo + off), 1u);
+                            mma_bf16<BN>(d, sw128_desc(b_lo + off), sw128_desc(g_hi + off), 1u);
                         }
                         mma_commit(bfree(t));
                     }
                     if (!ok) break;
                     mma_commit(empty(s));
                 }
-                if (ok) {
-                    mma_commit(accf(0));
-                    mma_commit(accf(1));
-                }
+                if (ok)
+                    for (int t = 0; t < 2; ++t)
+                        if (lv[t]) {
+                            mma_commit(accf(t));
+                            ++cj[t];
+                        }
             }
             // all issued MMAs complete before teardown
             mma_commit(done_bar);
@@ -324,16 +367,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- builders of the weighted rows (TC_NBUILD threads, one 16-B chunk each) ----
         const int tid = threadIdx.x - 64;
         const int r = tid >> 3, c = tid & 7;
-        long long sg = 0;
+        long long sg = 0, cs[2] = {0, 0};
         bool ok = true;
         for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
             int w0, w1, fq, n0, m0, nown, mown;
             job_tile(job, w0, w1, fq, n0, m0, nown, mown);
+            const bool lv[2] = {live_tile(fq, 0), live_tile(fq, 1)};
             for (int st = w0; st < w1 && ok; ++st, ++sg) {
                 const int s = (int)(sg % TC_NS);
                 if (!(ok = mbar_wait(full(s), (uint32_t)((sg / TC_NS) & 1), err, 121, lim))) break;
-                const unsigned char* stage = smem + s * TC_STAGE_BYTES;
-                const unsigned char* rhi = stage + TC_OFF_R;
+                const unsigned char* stage = smem + s * L::STAGE;
+                const unsigned char* rhi = stage + L::OFF_R;
                 const unsigned char* rlo = rhi + TC_R_BYTES;
                 const uint32_t o = sw128_off(r, c);
                 const uint4 vh = *reinterpret_cast<const uint4*>(rhi + o);
@@ -349,13 +393,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mi[i] = hh.y + ll.y;
                 }
                 for (int t = 0; t < 2; ++t) {
-                    if (!(ok = mbar_wait(bfree(t), (uint32_t)((sg & 1) ^ 1), err, 122, lim))) break;
-                    unsigned char* bhi = smem + TC_SMEM_B0 + t * 2 * TC_B_BYTES;
+                    if (!lv[t]) continue;
+                    if (!(ok = mbar_wait(bfree(t), (uint32_t)((cs[t] & 1) ^ 1), err, 122, lim))) break;
+                    ++cs[t];
+                    unsigned char* bhi = smem + L::B0 + t * 2 * TC_B_BYTES;
                     unsigned char* blo = bhi + TC_B_BYTES;
 #pragma unroll
                     for (int fq2 = 0; fq2 < 2; ++fq2) {
                         const float2* ws =
-                            reinterpret_cast<const float2*>(stage + TC_OFF_W + (2 * t + fq2) * TC_W_BYTES);
+                            reinterpret_cast<const float2*>(stage + L::OFF_W + (2 * t + fq2) * TC_W_BYTES);
                         const float4 w01 = *reinterpret_cast<const float4*>(ws + 4 * c);
                         const float4 w23 = *reinterpret_cast<const float4*>(ws + 4 * c + 2);
                         const float wr[4] = {w01.x, w01.z, w23.x, w23.z};
@@ -389,37 +435,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else {
         // ---------------- epilogue (128 threads, TMEM lanes by warp % 4) ----------------
         // lane quarter q4: 0 = Re f0, 1 = Im f0, 2 = Re f1, 3 = Im f1 of a tile; lane = G' - n0
+        constexpr int NCH = BN / 32;                 // 32-column loads, then one of 16 if BN % 32 = 16
+        constexpr bool REM = (BN % 32) == 16;
+        static_assert(BN % 32 == 0 || REM, "BN is a multiple of 16");
         const int q4 = warp & 3;
-        long long cg = 0;
+        long long cj[2] = {0, 0};
         bool ok = true;
         double* chi = reinterpret_cast<double*>(args.chi);
-        for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x, ++cg) {
+        for (int job = blockIdx.x; job < njobs && ok; job += gridDim.x) {
             int w0, w1, fq, n0, m0, nown, mown;
             job_tile(job, w0, w1, fq, n0, m0, nown, mown);
             const int gp = n0 + lane;
             const size_t ldo = (size_t)args.ng * 2;
             const int gmin = mown - m0;
-            const int gmax = min(TC_BN, args.ng - m0);   // columns [gmin, gmax) are this tile's
+            const int gmax = min(BN, args.ng - m0);   // columns [gmin, gmax) are this tile's
             for (int t = 0; t < 2 && ok; ++t) {
+                if (!live_tile(fq, t)) continue;
                 const int f = TC_NF * fq + 2 * t + (q4 >> 1), comp = q4 & 1;
                 const bool live = f < args.nf && gp >= nown && gp < args.ng;
                 double* out = chi + (((size_t)f * args.ng + m0) * args.ng + gp) * 2 + comp;
-                if (!(ok = mbar_wait(accf(t), (uint32_t)(cg & 1), err, 131, lim))) break;
+                if (!(ok = mbar_wait(accf(t), (uint32_t)(cj[t] & 1), err, 131, lim))) break;
+                ++cj[t];
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * 256);
 #pragma unroll 1
-                for (int ch = 0; ch < TC_BN / 32; ++ch) {
+                for (int ch = 0; ch < NCH; ++ch) {
                     uint32_t v[32];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-                          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-                          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                        : "r"(src + (uint32_t)(ch * 32)));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    tmem_ld32(src + (uint32_t)(ch * 32), v);
+                    if (!REM && ch == NCH - 1) {
+                        // the accumulator is read: the MMA of the next job may overwrite it
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        mbar_arrive(acce(t));
+                    }
                     if (live) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
@@ -427,17 +474,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 atomicAdd(out + (size_t)(ch * 32 + j) * ldo, (double)__uint_as_float(v[j]));
                     }
                 }
-                {
-                    constexpr int ch = TC_BN / 32;
+                if constexpr (REM) {
+                    constexpr int ch = NCH;
                     uint32_t v[16];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                        "[%16];"
-                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                          "=r"(v[14]), "=r"(v[15])
-                        : "r"(src + (uint32_t)(ch * 32)));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    tmem_ld16(src + (uint32_t)(ch * 32), v);
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     mbar_arrive(acce(t));
                     if (live) {
@@ -560,16 +600,79 @@ cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, 
                                    int num_sms, cudaStream_t st) {
     cudaError_t e = launch_weights32(K, w, ldw, col0, nf, w32, st);
     if (e != cudaSuccess) return e;
-    return launch_contract_bf16x3_core(hi, lo, K, ng, nf, w32, chi, err, num_sms, TC_WAIT_NS, st);
+    return launch_contract_bf16x3_core(hi, lo, K, ng, nf, w32, chi, err, num_sms, TC_WAIT_NS, st, 0);
+}
+
+// tile widths the kernel is built for
+static const int kTcBn[] = {160, 192, 208, 224, 256};
+
+bool tc_bn_supported(int bn) {
+    for (int b : kTcBn)
+        if (b == bn) return true;
+    return false;
+}
+
+int tc_bn_candidates(int* out) {
+    const int n = (int)(sizeof(kTcBn) / sizeof(kTcBn[0]));
+    if (out)
+        for (int i = 0; i < n; ++i) out[i] = kTcBn[i];
+    return n;
+}
+
+__global__ void k_fill_tune(__nv_bfloat16* hi, __nv_bfloat16* lo, long long n, float2* w, long long nw) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n + nw; i += (long long)gridDim.x * blockDim.x) {
+        // a hash of the index, scaled into [-1, 1)
+        unsigned x = (unsigned)(i * 2654435761ull) ^ (unsigned)(i >> 29);
+        x ^= x >> 15; x *= 2246822519u; x ^= x >> 13;
+        const float v = (float)(x & 0xffffff) * (2.0f / 16777216.0f) - 1.0f;
+        if (i < n) {
+            hi[i] = __float2bfloat16_rn(v);
+            lo[i] = __float2bfloat16_rn(v * (1.0f / 512.0f));
+        } else {
+            w[i - n] = make_float2(v, -0.5f * v);
+        }
+    }
+}
+
+cudaError_t launch_fill_tune_operands(void* hi, void* lo, long long n_bf16, void* w32, long long n_w32,
+                                      cudaStream_t st) {
+    k_fill_tune<<<1024, 256, 0, st>>>((__nv_bfloat16*)hi, (__nv_bfloat16*)lo, n_bf16, (float2*)w32, n_w32);
+    return cudaGetLastError();
+}
+
+// least padded rows ceil(ng / BN) BN; on a tie the wider tile (fewer raw-row reloads per flop)
+int tc_pick_bn(int ng) {
+    int best = 208;
+    long long best_rows = -1;
+    for (int b : kTcBn) {
+        const long long rows = (long long)((ng + b - 1) / b) * b;
+        if (best_rows < 0 || rows < best_rows || (rows == best_rows && b > best)) {
+            best = b;
+            best_rows = rows;
+        }
+    }
+    return best;
+}
+
+template <int BN>
+static cudaError_t launch_bn(const CUtensorMap& mraw_hi, const CUtensorMap& mraw_lo, const CUtensorMap& mrow_hi,
+                             const CUtensorMap& mrow_lo, const TcArgs& a, int grid, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_contract_bf16x3<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcL<BN>::TOTAL);
+    if (e != cudaSuccess) return e;
+    k_contract_bf16x3<BN><<<grid, TC_THREADS, TcL<BN>::TOTAL, st>>>(mraw_hi, mraw_lo, mrow_hi, mrow_lo, a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long long K, int ng, int nf,
                                         const void* w32, double2* chi, int* err, int num_sms,
-                                        unsigned long long wait_ns, cudaStream_t st) {
+                                        unsigned long long wait_ns, cudaStream_t st, int bn) {
+    if (bn <= 0) bn = tc_pick_bn(ng);
+    if (!tc_bn_supported(bn)) return cudaErrorInvalidValue;
     const long long kp2 = tc_kp2(K);
     CUtensorMap mraw_hi, mraw_lo, mrow_hi, mrow_lo;
-    if (!make_map(&mraw_hi, const_cast<void*>(hi), ng, kp2, TC_BN) ||
-        !make_map(&mraw_lo, const_cast<void*>(lo), ng, kp2, TC_BN) ||
+    if (!make_map(&mraw_hi, const_cast<void*>(hi), ng, kp2, bn) ||
+        !make_map(&mraw_lo, const_cast<void*>(lo), ng, kp2, bn) ||
         !make_map(&mrow_hi, const_cast<void*>(hi), ng, kp2, TC_GN) ||
         !make_map(&mrow_lo, const_cast<void*>(lo), ng, kp2, TC_GN))
         return cudaErrorInvalidValue;
@@ -577,18 +680,21 @@ cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long lon
     a.w32 = (const float2*)w32; a.K = K;
     a.ng = ng; a.nf = nf; a.nfq = tc_wrows(nf) / TC_NF;
     a.nblk = (ng + TC_GN - 1) / TC_GN;
-    a.mt = (ng + TC_BN - 1) / TC_BN;
+    a.mt = (ng + bn - 1) / bn;
     a.nst = (int)(kp2 / TC_BK);
     a.nwin = (a.nst + TC_FLUSH_STAGES - 1) / TC_FLUSH_STAGES;
     a.chi = chi; a.err = err;
     a.wait_ns = wait_ns;
     const long long njobs = (long long)a.nfq * a.nblk * a.mt * a.nwin;
     if (njobs > 0x7fffffffLL) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_contract_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_TOTAL);
-    if (e != cudaSuccess) return e;
     const int grid = njobs < num_sms ? (int)njobs : num_sms;
-    k_contract_bf16x3<<<grid, TC_THREADS, TC_SMEM_TOTAL, st>>>(mraw_hi, mraw_lo, mrow_hi, mrow_lo, a);
-    return cudaGetLastError();
+    switch (bn) {
+        case 160: return launch_bn<160>(mraw_hi, mraw_lo, mrow_hi, mrow_lo, a, grid, st);
+        case 192: return launch_bn<192>(mraw_hi, mraw_lo, mrow_hi, mrow_lo, a, grid, st);
+        case 208: return launch_bn<208>(mraw_hi, mraw_lo, mrow_hi, mrow_lo, a, grid, st);
+        case 224: return launch_bn<224>(mraw_hi, mraw_lo, mrow_hi, mrow_lo, a, grid, st);
+        default: return launch_bn<256>(mraw_hi, mraw_lo, mrow_hi, mrow_lo, a, grid, st);
+    }
 }
 
 }  // namespace rp

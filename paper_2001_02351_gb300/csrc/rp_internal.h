@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -88,6 +89,8 @@ struct rp_ctx {
     rp::DevBuf s_queue;               // FP64 work list of the FP32 weight pass (count + items)
     int num_sms = 0;
     unsigned long long wait_ns = 2000000000ULL;   // limit of a bounded device wait (rp_set_wait_limit)
+    std::map<int, int> tile_bn;                   // NG -> raw rows per tile of the BF16x3 contraction
+                                                  // (rp_tune_contraction / rp_set_contraction_tile)
     std::vector<double> freq_stage;               // host copy of the frequencies of the last weight pass
 
     rp::QPlan plan;
@@ -143,10 +146,17 @@ cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, 
 // the two halves of launch_contract_bf16x3: float copy of the weights, then the tensor-core kernel
 cudaError_t launch_weights32(long long K, const double2* w, long long ldw, long long col0, int nf, void* w32,
                              cudaStream_t st);
-// (wait_ns: limit of the kernel's pipeline waits; a wait that gives up sets *err and the kernel returns)
+// (wait_ns: limit of the kernel's pipeline waits; a wait that gives up sets *err and the kernel returns;
+// bn: raw rows per tile, one of tc_bn_supported, or <= 0 for tc_pick_bn(ng))
 cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long long K, int ng, int nf,
                                         const void* w32, double2* chi, int* err, int num_sms,
-                                        unsigned long long wait_ns, cudaStream_t st);
+                                        unsigned long long wait_ns, cudaStream_t st, int bn);
+bool tc_bn_supported(int bn);
+int tc_pick_bn(int ng);
+int tc_bn_candidates(int* out);     // the supported tile widths (returns their count, out may be NULL)
+// seeded finite bf16 operands and float weights for timing runs of the contraction
+cudaError_t launch_fill_tune_operands(void* hi, void* lo, long long n_bf16, void* w32, long long n_w32,
+                                      cudaStream_t st);
 // TF32x3 contraction (mma.sync, FP32 accumulation added into FP64): chi (+)= over K pairs of M
 // (complex float when m32, else complex double) from column 0 of the given pointer
 cudaError_t launch_contract_tf32x3(const void* M, bool m32, long long ldm, long long K, const double2* w,

@@ -123,14 +123,35 @@ def _cache_dir():
     return d
 
 
-def make_workload(name, crpa=False, cache=True, workers=None, **overrides):
+def workload_shape(name, **overrides):
+    """Everything of a workload but its bands: cell, mesh, grid, cut-offs, q points, band counts and
+    frequencies (cheap; used where only the sizes matter)."""
     spec = dict(CONFIGS[name])
     spec.update(overrides)
     seed = BASE_SEED + list(CONFIGS).index(name) if name in CONFIGS else BASE_SEED
     kind, a = spec["cell"]
     cell = fcc_cell(a) if kind == "fcc" else sc_cell(a)
-    nband = spec["nocc"] + spec["nemp"]
     ecut_psi = _mid_gap_cutoff_mesh(cell.recip, spec["kmesh"], spec["npw"])
+    rng = np.random.default_rng(seed + 7)
+    kmesh = np.array(spec["kmesh"])
+    if spec["q"] == "all":
+        from .epm import kmesh_frac
+        q = kmesh_frac(kmesh)
+    else:
+        q = np.array(spec["q"], dtype=np.float64).reshape(-1, 3)
+    ng = spec["ng"]
+    ecut_eps = []
+    for qi in q:
+        target = int(rng.integers(ng[0], ng[1] + 1)) if isinstance(ng, tuple) else int(ng)
+        ecut_eps.append(_mid_gap_cutoff(cell.recip, qi, target, exclude_zero=True))
+    return dict(spec=spec, seed=seed, cell=cell, kind=kind, a=a, ecut_psi=ecut_psi, q=q,
+                ecut_eps=np.array(ecut_eps), rng=rng)
+
+
+def make_workload(name, crpa=False, cache=True, workers=None, **overrides):
+    sh = workload_shape(name, **overrides)
+    spec, seed, cell, kind, a, ecut_psi = sh["spec"], sh["seed"], sh["cell"], sh["kind"], sh["a"], sh["ecut_psi"]
+    nband = spec["nocc"] + spec["nemp"]
     symmetry = bool(spec.get("symmetry", False))
     key = hashlib.sha1(repr((name, seed, spec["kmesh"], ecut_psi, nband, spec["pot"], a, kind,
                              symmetry)).encode()).hexdigest()[:16]
@@ -152,21 +173,9 @@ def make_workload(name, crpa=False, cache=True, workers=None, **overrides):
             np.savez(tmp, kfrac=bands.kfrac, npw=bands.npw, miller=bands.miller,
                      coef=bands.coef, energy=bands.energy)
             os.replace(tmp, path)
-    rng = np.random.default_rng(seed + 7)
-    kmesh = np.array(spec["kmesh"])
-    if spec["q"] == "all":
-        from .epm import kmesh_frac
-        q = kmesh_frac(kmesh)
-    else:
-        q = np.array(spec["q"], dtype=np.float64).reshape(-1, 3)
-    ng = spec["ng"]
-    ecut_eps = []
-    for qi in q:
-        target = int(rng.integers(ng[0], ng[1] + 1)) if isinstance(ng, tuple) else int(ng)
-        ecut_eps.append(_mid_gap_cutoff(cell.recip, qi, target, exclude_zero=True))
     T = None
     if crpa:
-        T = rng.uniform(0.0, 1.0, size=bands.energy.shape)
+        T = sh["rng"].uniform(0.0, 1.0, size=bands.energy.shape)
     return Workload(name=name, bands=bands, fft=tuple(spec["fft"]), nocc=spec["nocc"], nemp=spec["nemp"],
-                    q=q, ecut_eps=np.array(ecut_eps), axis=spec["axis"], freq=np.asarray(spec["freq"], dtype=np.float64),
-                    delta=float(spec["delta"]), T=T)
+                    q=sh["q"], ecut_eps=sh["ecut_eps"], axis=spec["axis"],
+                    freq=np.asarray(spec["freq"], dtype=np.float64), delta=float(spec["delta"]), T=T)

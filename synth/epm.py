@@ -141,8 +141,8 @@ def _solve_k(args):
     h = vtab[d[..., 0], d[..., 1], d[..., 2]]
     h[np.diag_indices_from(h)] += kin
     if np.all(h.imag == 0):
+        # real symmetric H (the shell potential): real eigenvectors, widened when stored
         e, v = sl.eigh(h.real, subset_by_index=[0, nband - 1], driver="evr")
-        v = v.astype(np.complex128)
     else:
         e, v = sl.eigh(h, subset_by_index=[0, nband - 1], driver="evr")
     return m.astype(np.int32), e, v.T.copy()
@@ -249,7 +249,7 @@ def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None, symmetry=F
         try:
             with cf.ProcessPoolExecutor(max_workers=workers,
                                         mp_context=mp.get_context("spawn" if cuda_up else "fork")) as ex:
-                res = list(ex.map(_solve_k, jobs, chunksize=max(1, nk // (4 * workers))))
+                res = list(ex.map(_solve_k, jobs, chunksize=max(1, len(jobs) // (4 * workers))))
         finally:
             for v, val in saved.items():
                 if val is None:
@@ -259,20 +259,10 @@ def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None, symmetry=F
     else:
         res = [_solve_k(j) for j in jobs]
     if symmetry:
-        # rotate each orbit representative's eigenvectors onto the other points of its orbit
         by_rep = {int(r): res[i] for i, r in enumerate(reps)}
-        full = []
-        for k in range(nk):
-            m, e, v = by_rep[int(rep[k])]
-            if rep[k] == k:
-                full.append((m, e, v))
-                continue
-            mk = m.astype(np.int64) @ rot[k] + gshift[k]      # G S + G_s
-            order = np.lexsort((mk[:, 2], mk[:, 1], mk[:, 0]))
-            full.append((mk[order].astype(np.int32), e, v[:, order]))
-        res = full
         meta.update({"irreducible_k": int(len(reps))})
-    npw = np.array([r_[0].shape[0] for r_ in res], dtype=np.int32)
+    npw = np.array([by_rep[int(rep[k])][0].shape[0] for k in range(nk)] if symmetry
+                   else [r_[0].shape[0] for r_ in res], dtype=np.int32)
     if np.any(npw < nband):
         raise ValueError("plane-wave set smaller than the number of bands")
     pmax = int(npw.max())
@@ -280,7 +270,17 @@ def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None, symmetry=F
     coef = np.zeros((nk, nband, pmax), dtype=np.complex128)
     energy = np.zeros((nk, nband), dtype=np.float64)
     phase = np.exp(2j * np.pi * rng.uniform(size=(nk, nband)))
-    for i, (m, e, v) in enumerate(res):
+    for i in range(nk):
+        if symmetry:
+            # rotate the orbit representative's eigenvectors onto this point: C(G S + G_s) = C_rep(G)
+            m, e, v = by_rep[int(rep[i])]
+            if rep[i] != i:
+                mk = m.astype(np.int64) @ rot[i] + gshift[i]
+                order = np.lexsort((mk[:, 2], mk[:, 1], mk[:, 0]))
+                m = mk[order].astype(np.int32)
+                v = v[:, order]
+        else:
+            m, e, v = res[i]
         miller[i, : m.shape[0]] = m
         coef[i, :, : m.shape[0]] = v
         coef[i, :, : m.shape[0]] *= phase[i][:, None]

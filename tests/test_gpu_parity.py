@@ -322,6 +322,40 @@ def test_contract_bf16x3(ng, K, nf):
     assert np.array_equal(got, got2)
 
 
+@pytest.mark.parametrize("bn", list(rp.TILE_WIDTHS))
+@pytest.mark.parametrize("ng,K,nf", [(300, 3000, 6), (150, 2000, 5), (37, 700, 2), (520, 1500, 1)])
+def test_contract_bf16x3_every_tile_width(bn, ng, K, nf):
+    """Each built tile width BN of the BF16x3 kernel (set through rp_set_contraction_tile) against the
+    oracle: NG below, across and above BN (the last tile moved back to end at NG), and frequency
+    counts whose last group has only one live tile (nf = 6, 5, 2, 1: the other tile is skipped)."""
+    rng = np.random.default_rng(13 * ng + K + bn)
+    M = rng.standard_normal((ng, K)) + 1j * rng.standard_normal((ng, K))
+    w = rng.standard_normal((nf, K)) + 1j * rng.standard_normal((nf, K))
+    ctx = _ctx(workload("micro"))
+    ctx.rp_set_contraction_tile(ng, bn)
+    got = ctx.rp_contract_chi0(M, w, precision=rp.RP_BF16X3)
+    assert np.all(_rel_fro(got, OC.chi0(M, w)) < BF16X3_TOL)
+
+
+def test_contraction_tile_tuner():
+    """rp_tune_contraction times every tile width on synthetic operands, keeps the fastest for this
+    NG, and later contractions with that NG use it and stay correct; a width that is not built is
+    refused."""
+    ctx = _ctx(workload("micro"))
+    ng, K, nf = 400, 20000, 4
+    bn, ms = ctx.rp_tune_contraction(ng, K, nf)
+    assert bn in rp.TILE_WIDTHS
+    assert all(v > 0 for v in ms.values()) and ms[bn] == min(ms.values())
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((ng, 3000)) + 1j * rng.standard_normal((ng, 3000))
+    w = rng.standard_normal((nf, 3000)) + 1j * rng.standard_normal((nf, 3000))
+    got = ctx.rp_contract_chi0(M, w, precision=rp.RP_BF16X3)
+    assert np.all(_rel_fro(got, OC.chi0(M, w)) < BF16X3_TOL)
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_set_contraction_tile(ng, 100)
+    assert e.value.code == rp.RP_ERR_ARG
+
+
 def test_build_chi0_bf16x3_tiny(tiny, tiny_ref):
     chi_ref, W_ref = tiny_ref
     ctx = _ctx(tiny)
