@@ -475,7 +475,12 @@ static int pair_density_device(rp_ctx* c, int k0, int k1, void* M, bool fp32, lo
     const int W = fp32 ? P.zyw : 0;
     const size_t wyz = W > 0 ? (size_t)(2 * W + 1) * (2 * W + 1) : (size_t)P.nset[1] * P.nset[2];
     const size_t t2_k = (size_t)c->nemp * c->nocc * P.nfft[0] * wyz * (fp32 ? sizeof(float2) : sizeof(double2));
-    const size_t kb_t2 = std::max<size_t>(1, ((size_t)16 << 30) / std::max<size_t>(1, t2_k));
+    size_t kb_t2 = std::max<size_t>(1, ((size_t)16 << 30) / std::max<size_t>(1, t2_k));
+    if (!fp32) {
+        // the FP64 tier's fused path keeps z-transformed planes of every pair within 12 GB
+        const size_t t1_k = (size_t)c->nemp * c->nocc * P.nfft[0] * P.nfft[1] * P.nset[2] * sizeof(double2);
+        kb_t2 = std::min<size_t>(kb_t2, std::max<size_t>(1, ((size_t)12 << 30) / std::max<size_t>(1, t1_k)));
+    }
     const int kb = (int)std::max<size_t>(
         1, std::min<size_t>(std::min<size_t>((size_t)(k1 - k0), ((size_t)2 << 30) / (3 * per_k)), kb_t2));
     for (int k = k0; k < k1; k += kb) {

@@ -45,7 +45,8 @@ def oracle_sample(prec):
     G = OL.eps_sphere(prec.cell.lat, q, prec.ecut_eps[0])
     M0 = OP.pair_density(prec.bands, prec.nocc, prec.nemp, q, G, fft=prec.fft, k_list=[0])
     w = OC.pair_weights(replace(prec, freq=prec.freq[FI]), q, k_list=KS)
-    return G, M0, w
+    w0 = np.ascontiguousarray(w[:, :M0.shape[1]])            # the k = 0 columns
+    return G, M0, w, OC.chi0(M0, w0)
 
 
 def _rel_fro(a, b):
@@ -64,7 +65,7 @@ def test_workload_shape(prec, pctx):
 
 def test_pair_density_full_size_one_k(prec, pctx, oracle_sample):
     q = prec.q[0]
-    G, ref, _ = oracle_sample
+    G, ref, _, _ = oracle_sample
     got = pctx.rp_pair_density(q, 0, 1)
     assert got.shape == ref.shape == (len(G), prec.nocc * prec.nemp)
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
@@ -88,9 +89,8 @@ def test_weights_full_size_sampled(prec, pctx, oracle_sample, precision, tol):
 @pytest.mark.parametrize("precision,tol", [(rp.RP_FP64_NATIVE, 1e-12), (rp.RP_BF16X3, BF16X3_TOL),
                                            (rp.RP_TF32X3, TF32X3_TOL)])
 def test_contraction_full_ng_on_oracle_inputs(pctx, oracle_sample, precision, tol):
-    _, M, w2 = oracle_sample
+    _, M, w2, ref = oracle_sample
     w = np.ascontiguousarray(w2[:, :M.shape[1]])            # the k = 0 columns
-    ref = OC.chi0(M, w)
     got = pctx.rp_contract_chi0(M, w, precision=precision)
     err = _rel_fro(got, ref)
     print("precision-size contraction rel err", precision, err)
