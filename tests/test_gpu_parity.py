@@ -484,3 +484,24 @@ def test_kset_builds_partition_the_mesh(tiny, tiny_ref):
     with pytest.raises(rp.RPError) as e:
         ctx.rp_build_chi0_kset(q, [1, 1], _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, rp.RP_FP64_NATIVE)
     assert e.value.code == rp.RP_ERR_ARG
+
+
+def test_gamma_point_build_and_w(tiny):
+    """q = 0: k' = k with no umklapp, and the epsilon sphere leaves out G = 0 (its Coulomb factor
+    diverges; the analytic head is not part of this path).  chi0 (FP64 and BF16x3) and W against
+    the oracle with the same convention, and the sphere lists against the oracle's."""
+    q = np.zeros(3)
+    ctx = _ctx(tiny)
+    g, t = ctx.rp_sphere_size(q)
+    G = OL.eps_sphere(tiny.cell.lat, q, tiny.ecut_eps[0])
+    assert np.array_equal(g, G) and not np.any(np.all(G == 0, axis=1))
+    assert np.array_equal(t, OL.tail_sphere(tiny.cell.lat, q, tiny.ecut_eps[0], tiny.bands.ecut_psi))
+    M = OP.pair_density(tiny.bands, tiny.nocc, tiny.nemp, q, G, fft=tiny.fft)
+    chi_ref = OC.chi0(M, OC.pair_weights(tiny, q))
+    W_ref = OD.screened(chi_ref, OD.coulomb_sqrt(tiny.cell.lat, q, G))
+    chi = ctx.rp_build_chi0(q, _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, rp.RP_FP64_NATIVE)
+    assert np.all(_rel_fro(chi, chi_ref) < 1e-11)
+    W, _ = ctx.rp_solve_w(q, chi)
+    assert np.all(_rel_fro(W, W_ref) < 1e-11)
+    chi = ctx.rp_build_chi0(q, _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, rp.RP_BF16X3)
+    assert np.all(_rel_fro(chi, chi_ref) < BF16X3_TOL)
