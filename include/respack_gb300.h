@@ -195,6 +195,31 @@ int rp_solve_w_batched(rp_ctx* ctx, int nq, const double* q_frac, const double* 
                        const double* const* chi0, double* const* W_out, double* const* tail_out,
                        int on_device, void* cuda_stream);
 
+/* rp_load_wannier -- Wannier functions of the interaction step (Sec. 2.4): coef c128
+ *   [nk][nw][npw_max] (host) holds, for each mesh point k, the plane-wave coefficients of the Bloch
+ *   orbitals phi~_ik = sum over lattice vectors R of phi_iR e^{ik.R}, normalised on the crystal like the
+ *   bands and given in the plane-wave sets of rp_load_bands (the same Miller lists).  1 <= nw <= 16.
+ *   Copied to device memory.  RP_ERR_STATE without bands. */
+int rp_load_wannier(rp_ctx* ctx, int nw, const double* coef);
+
+/* rp_interaction -- the term of one q of the screened direct and exchange integrals (Eq. matrix_U,
+ *   Eq. matrix_J), or of the bare ones (Eq. matrix_V, Eq. matrix_X) when W is NULL:
+ *     U_{i0jR} += (1/N_q) e^{-iq.R} [ sum_{G,G' in eps} n_i(q+G) W_GG' n_j(q+G')^* + sum_{tail} n_i v_G n_j^* ]
+ *     J_{i0jR} += (1/N_q)           [ sum_{G,G' in eps} p(q+G) W_GG' p(q+G')^*      + sum_{tail} |p|^2 v_G ]
+ *   with n_i(q+G) = (1/N_k) sum_k <phi~_{i,k+q}|e^{i(q+G).r}|phi~_{i,k}> (the Fourier component of
+ *   Wannier function i's density), p = p_ijR(q+G) = (1/N_k) sum_k e^{-ik.R} <phi~_{i,k+q}|e^{i(q+G).r}|
+ *   phi~_{j,k}> and v_G = 4 pi/(Omega |q+G|^2); W = v^1/2 eps^-1 v^1/2 of rp_solve_w on the epsilon
+ *   sphere of q, the tail the rest of the wave-function sphere (bare: the whole sphere with v).
+ *   Summing the calls over every q of the mesh gives the integrals.  q = 0, G = 0 is left out.
+ *   W [io] c128 [nfreq][NG][NG] or NULL;  R_list int [nR][3] lattice vectors (host, reduced
+ *   coordinates);  U_out, J_out [io] c128 [nfreq][nR][nw][nw] ([1][nR][nw][nw] when W is NULL),
+ *   overwritten with this q's term (accumulate = 0) or added to (accumulate = 1).  The pair
+ *   densities are formed on a transform grid on which nothing folds onto the sphere (the requested
+ *   grid, enlarged when needed).  FP64.  nw + nR nw^2 <= 192, else RP_ERR_ARG; RP_ERR_STATE without
+ *   rp_load_wannier. */
+int rp_interaction(rp_ctx* ctx, const double q_frac[3], int nfreq, const double* W, int nR, const int* R_list,
+                   double* U_out, double* J_out, int accumulate, int on_device, void* cuda_stream);
+
 /* rp_check_numeric -- synchronises the context's last stream and reports what the asynchronous
  *   (on_device = 1) calls since the previous check left in the context's device flags:
  *   RP_ERR_TIMEOUT if a bounded device wait of a contraction gave up (its chi0 is unspecified),

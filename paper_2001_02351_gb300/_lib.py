@@ -27,7 +27,8 @@ EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density"
            "rp_contract_chi0", "rp_build_chi0", "rp_solve_w", "rp_check_numeric", "rp_profile_enable",
            "rp_profile_read", "rp_last_error", "rp_destroy", "rp_contract_chi0_static", "rp_sphere_size_at",
            "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_contract_chi0_static_status",
-           "rp_build_chi0_kset", "rp_tune_contraction", "rp_set_contraction_tile"]
+           "rp_build_chi0_kset", "rp_tune_contraction", "rp_set_contraction_tile",
+           "rp_load_wannier", "rp_interaction"]
 
 
 class RPError(RuntimeError):
@@ -70,6 +71,8 @@ def library():
         "rp_build_chi0_kset": (I, [P, P, I, P, I, I, I, P, D, D, D, I, P, I, P]),
         "rp_tune_contraction": (I, [P, I, LL, I, ctypes.POINTER(I), P]),
         "rp_set_contraction_tile": (I, [P, I, I]),
+        "rp_load_wannier": (I, [P, I, P]),
+        "rp_interaction": (I, [P, P, I, P, I, P, P, P, I, I, P]),
         "rp_contract_chi0_static_status": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -300,6 +303,36 @@ class Context:
 
     def rp_check_numeric(self):
         self._check(self._lib.rp_check_numeric(self._h))
+
+    def rp_load_wannier(self, coef):
+        """coef [nk][nw][npw_max]: plane-wave coefficients of the Wannier functions' Bloch orbitals."""
+        coef = np.ascontiguousarray(coef, dtype=np.complex128)
+        self._check(self._lib.rp_load_wannier(self._h, int(coef.shape[1]), coef.ctypes.data_as(ctypes.c_void_p)))
+        self.nw = int(coef.shape[1])
+
+    def rp_interaction(self, q, R_list, W=None, U=None, J=None, accumulate=False):
+        """This q's term of U_{i0jR}, J_{i0jR} [nfreq][nR][nw][nw] (bare when W is None); host arrays, or
+        CUDA tensors when W (or U) is one.  With accumulate the term is added to the given U, J."""
+        R_, pR = _host(np.asarray(R_list).reshape(-1, 3), np.int32)
+        nR = R_.shape[0]
+        dev = 1 if (_is_torch(W) or _is_torch(U)) else 0
+        nf = 1 if W is None else W.shape[0]
+        shape = (nf, nR, self.nw, self.nw)
+        if dev:
+            import torch
+            U = torch.zeros(shape, dtype=torch.complex128, device="cuda") if U is None else U
+            J = torch.zeros(shape, dtype=torch.complex128, device="cuda") if J is None else J
+            pW = None if W is None else _dev_ptr(W)
+        else:
+            U = np.zeros(shape, dtype=np.complex128) if U is None else U
+            J = np.zeros(shape, dtype=np.complex128) if J is None else J
+            if W is not None:
+                W = np.ascontiguousarray(W, dtype=np.complex128)
+            pW = None if W is None else W.ctypes.data_as(ctypes.c_void_p)
+        q_, pq = _host(q, np.float64)
+        self._check(self._lib.rp_interaction(self._h, pq, int(nf), pW, nR, pR, self._ptr(U, dev), self._ptr(J, dev),
+                                             1 if accumulate else 0, dev, _stream() if dev else None))
+        return U, J
 
     def rp_tune_contraction(self, ng, K, nfreq):
         """(chosen BN, {BN: ms}) for BF16x3 contractions of this shape; the choice is kept in the context."""

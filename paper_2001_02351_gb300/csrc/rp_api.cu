@@ -100,9 +100,10 @@ static void search_box(const rp_ctx* c, double ecut, const double q[3], int nmax
 
 int plan_q(rp_ctx* c, const double q[3]) { return plan_q_cut(c, q, c->ecut_eps); }
 
-int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps) {
+int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps, bool exact) {
     QPlan& P = c->plan;
-    if (P.valid && P.q[0] == q[0] && P.q[1] == q[1] && P.q[2] == q[2] && P.ecut == ecut_eps) return RP_OK;
+    if (P.valid && P.q[0] == q[0] && P.q[1] == q[1] && P.q[2] == q[2] && P.ecut == ecut_eps && P.exact == exact)
+        return RP_OK;
     P.valid = false;
     if (!(ecut_eps > 0.0) || !(ecut_eps <= c->ecut_psi)) return fail(c, RP_ERR_ARG, "need 0 < Ecut_eps <= Ecut_psi");
     for (int i = 0; i < 3; ++i) {
@@ -178,6 +179,22 @@ int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps) {
                 for (int a = 0; a < 3; ++a) P.nfft[a] = cand;
                 break;
             }
+    }
+    if (exact && c->lb > 0) {
+        // a grid on which the transforms are the plain convolution: the requested one if nothing folds
+        // onto the sphere there, else the smallest size (of 2s and 3s) on which nothing does
+        int need = 0;
+        for (int a = 0; a < 3; ++a) {
+            int lg = 0;
+            for (int v : P.setv[a]) lg = std::max(lg, std::abs(v));
+            need = std::max(need, 2 * c->mu[a] + 2 + lg);
+        }
+        if (P.nfft[0] < need || P.nfft[1] < need || P.nfft[2] < need) {
+            int n = need;
+            while (!good_fft(n)) ++n;
+            if (n > 128) return fail(c, RP_ERR_UNSUPPORTED, "exact transform grid above 128");
+            for (int a = 0; a < 3; ++a) P.nfft[a] = n;
+        }
     }
     P.nr = (long long)P.nfft[0] * P.nfft[1] * P.nfft[2];
     for (int a = 0; a < 3; ++a) {
@@ -280,6 +297,7 @@ int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps) {
     if ((st = upload(c, P.d_vs, P.vs.data(), P.vs.size() * sizeof(double)))) return st;
     for (int i = 0; i < 3; ++i) P.q[i] = q[i];
     P.ecut = ecut_eps;
+    P.exact = exact;
     P.valid = true;
     return RP_OK;
 }
@@ -915,6 +933,136 @@ int rp_solve_w_batched(rp_ctx* c, int nq, const double* q_frac, const double* ec
     return RP_OK;
 }
 
+int rp_load_wannier(rp_ctx* c, int nw, const double* coef) {
+    if (!c) return RP_ERR_ARG;
+    if (!c->loaded) return fail(c, RP_ERR_STATE, "bands not loaded");
+    if (nw < 1 || nw > 16 || !coef) return fail(c, RP_ERR_ARG, "need 1 <= nw <= 16 and coefficients");
+    const size_t row = (size_t)nw * c->npw_max * sizeof(double2);      // one k point's orbitals
+    int st = ensure(c, c->d_wcoef, 2 * row * c->nk);
+    if (st) return st;
+    // each orbital twice: [k][0, nw) is the "occupied" copy at k, [k][nw, 2 nw) the "empty" one at k + q
+    for (int half = 0; half < 2; ++half) {
+        cudaError_t e = cudaMemcpy2D((char*)c->d_wcoef.p + half * row, 2 * row, coef, row, row, c->nk,
+                                     cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "upload Wannier coefficients");
+    }
+    c->nw = nw;
+    return RP_OK;
+}
+
+int rp_interaction(rp_ctx* c, const double q[3], int nfreq, const double* W, int nR, const int* R_list, double* U_out,
+                   double* J_out, int accumulate, int on_device, void* stream) {
+    if (!c) return RP_ERR_ARG;
+    if (!c->loaded || c->nw < 1) return fail(c, RP_ERR_STATE, "bands and Wannier functions not loaded");
+    if (!q || nR < 1 || !R_list || !U_out || !J_out || (W && nfreq < 1))
+        return fail(c, RP_ERR_ARG, "bad interaction arguments");
+    const int nw = c->nw, nw2 = nw * nw, nb = nw + nR * nw2;
+    if (nb > 192) return fail(c, RP_ERR_ARG, "nw + nR nw^2 above 192");
+    cudaStream_t st = (cudaStream_t)stream;
+    int s;
+    // the epsilon sphere of W (the context's cut-off), then the whole wave-function sphere of q
+    if ((s = check_ready(c, q))) return s;
+    const std::vector<int> eps_m = c->plan.gm;
+    const int ng = c->plan.ng;
+    if ((s = plan_q_cut(c, q, c->ecut_psi, true))) return s;
+    const QPlan& P = c->plan;
+    const int ngp = P.ng;
+    // positions of the epsilon-sphere members in the (lexicographic) wave-function sphere
+    std::vector<int> pe(std::max(ng, 1));
+    std::vector<unsigned char> in_eps(ngp, 0);
+    {
+        int e = 0;
+        for (int g = 0; g < ngp && e < ng; ++g)
+            if (P.gm[3 * g] == eps_m[3 * e] && P.gm[3 * g + 1] == eps_m[3 * e + 1] && P.gm[3 * g + 2] == eps_m[3 * e + 2]) {
+                pe[e++] = g;
+                in_eps[g] = 1;
+            }
+        if (e != ng) return fail(c, RP_ERR_STATE, "epsilon sphere not inside the wave-function sphere");
+    }
+    // e^{-i k.R} of every mesh point and e^{-i q.R}, v of the sphere
+    std::vector<double2> tab((size_t)nR * c->nk + nR);
+    for (int r = 0; r < nR; ++r) {
+        for (int k = 0; k < c->nk; ++k) {
+            const int i1 = k / (c->kmesh[1] * c->kmesh[2]), i2 = (k / c->kmesh[2]) % c->kmesh[1], i3 = k % c->kmesh[2];
+            const double t = (double)i1 * R_list[3 * r] / c->kmesh[0] + (double)i2 * R_list[3 * r + 1] / c->kmesh[1] +
+                             (double)i3 * R_list[3 * r + 2] / c->kmesh[2];
+            tab[(size_t)r * c->nk + k] = make_double2(std::cos(2.0 * M_PI * t), -std::sin(2.0 * M_PI * t));
+        }
+        const double t = q[0] * R_list[3 * r] + q[1] * R_list[3 * r + 1] + q[2] * R_list[3 * r + 2];
+        tab[(size_t)nR * c->nk + r] = make_double2(std::cos(2.0 * M_PI * t), -std::sin(2.0 * M_PI * t));
+    }
+    std::vector<double> v(ngp);
+    for (int g = 0; g < ngp; ++g) v[g] = P.vs[g] * P.vs[g];
+    const size_t tab_b = tab.size() * sizeof(double2), v_b = ngp * sizeof(double), pe_b = pe.size() * sizeof(int);
+    const size_t aux = tab_b + v_b + pe_b + ngp + 256 * 4;
+    const long long ldm = (long long)c->nk * nw2;
+    const int nf = W ? nfreq : 1;
+    const size_t nout = (size_t)nf * nR * nw2;
+    if ((s = ensure(c, c->s_wm, (size_t)ngp * ldm * sizeof(double2))) ||
+        (s = ensure(c, c->s_wb, (size_t)nb * ngp * sizeof(double2))) ||
+        (s = ensure(c, c->s_wtab, aux)) || (s = ensure(c, c->s_wout, 2 * nout * sizeof(double2))))
+        return s;
+    char* ax = (char*)c->s_wtab.p;
+    double2* d_tab = (double2*)ax;
+    double* d_v = (double*)(ax + ((tab_b + 255) / 256) * 256);
+    int* d_pe = (int*)((char*)d_v + ((v_b + 255) / 256) * 256);
+    unsigned char* d_in = (unsigned char*)((char*)d_pe + ((pe_b + 255) / 256) * 256);
+    // pageable sources: staged before each call returns
+    cudaError_t e = cudaMemcpyAsync(d_tab, tab.data(), tab_b, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_v, v.data(), v_b, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_pe, pe.data(), pe_b, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_in, in_eps.data(), ngp, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "interaction tables");
+    // orbital pair densities through the band kernels, on a band view of the Wannier functions
+    {
+        rp::DevBuf coef = c->d_coef;
+        const int nband = c->nband, nocc = c->nocc, nemp = c->nemp;
+        c->d_coef = c->d_wcoef;
+        c->nband = 2 * nw; c->nocc = nw; c->nemp = nw;
+        s = pair_density_device(c, 0, c->nk, c->s_wm.p, false, ldm, 0, st);
+        c->d_coef = coef;
+        c->nband = nband; c->nocc = nocc; c->nemp = nemp;
+        if (s) return s;
+    }
+    e = launch_wan_density((const double2*)c->s_wm.p, ldm, c->nk, nw, nR, d_tab, (double2*)c->s_wb.p, ngp, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Wannier densities");
+    const double2* dW = (const double2*)W;
+    double2* Y = nullptr;
+    if (W) {
+        const size_t wb = (size_t)nfreq * ng * ng * sizeof(double2);
+        if ((s = ensure(c, c->s_wy, (size_t)nfreq * nb * ng * sizeof(double2)))) return s;
+        if (!on_device) {
+            if ((s = ensure(c, c->s_io1, wb))) return s;
+            if ((e = cudaMemcpyAsync(c->s_io1.p, W, wb, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(c, e, "copy W");
+            dW = (const double2*)c->s_io1.p;
+        }
+        Y = (double2*)c->s_wy.p;
+        e = launch_wan_wrhs(dW, ng, nfreq, (const double2*)c->s_wb.p, ngp, d_pe, nb, Y, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "W times the densities");
+    }
+    double2* dU = (double2*)U_out;
+    double2* dJ = (double2*)J_out;
+    if (!on_device) {
+        dU = (double2*)c->s_wout.p;
+        dJ = dU + nout;
+        if (accumulate) {
+            if ((e = cudaMemcpyAsync(dU, U_out, nout * sizeof(double2), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(dJ, J_out, nout * sizeof(double2), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(c, e, "copy U, J");
+        }
+    }
+    e = launch_wan_reduce((const double2*)c->s_wb.p, ngp, d_v, d_in, d_pe, ng, Y, nw, nR, nf, d_tab + (size_t)nR * c->nk,
+                          1.0 / c->nk, accumulate, dU, dJ, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "interaction sums");
+    if (!on_device) {
+        if ((e = cudaMemcpyAsync(U_out, dU, nout * sizeof(double2), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(J_out, dJ, nout * sizeof(double2), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(c, e, "copy U, J");
+    }
+    return finish(c, st, on_device);
+}
+
 int rp_profile_enable(rp_ctx* c, int enable) {
     if (!c) return RP_ERR_ARG;
     c->prof = enable != 0;
@@ -953,7 +1101,8 @@ void rp_destroy(rp_ctx* c) {
                       &c->s_io3, &c->s_hi, &c->s_lo, &c->s_w32, &c->s_queue, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
                       &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_zmap, &c->plan.d_ymap,
-                      &c->plan.d_gpos_r, &c->plan.d_gpos_w, &c->plan.d_colg};
+                      &c->plan.d_gpos_r, &c->plan.d_gpos_w, &c->plan.d_colg, &c->d_wcoef, &c->s_wm, &c->s_wb,
+                      &c->s_wy, &c->s_wtab, &c->s_wout};
     for (DevBuf* b : bufs) release(*b);
     for (int i = 0; i < RP_NSTAGE; ++i)
         for (cudaEvent_t e : c->prof_ev[i]) cudaEventDestroy(e);

@@ -25,6 +25,7 @@ struct QPlan {
     bool valid = false;
     double q[3] = {0, 0, 0};
     double ecut = 0;                 // epsilon-sphere cut-off the plan was made for (Ha)
+    bool exact = false;              // transform grid chosen so that nothing folds onto the sphere
     int qi[3] = {0, 0, 0};           // q * kmesh (integers)
     int ng = 0, ntail = 0;
     std::vector<int> gm;             // [ng][3]
@@ -87,6 +88,10 @@ struct rp_ctx {
     rp::DevBuf s_hi, s_lo;            // bf16 hi/lo split of a block of pair densities
     rp::DevBuf s_w32;                 // complex float weights of that block
     rp::DevBuf s_queue;               // FP64 work list of the FP32 weight pass (count + items)
+    // Wannier functions of the interaction step: coefficients [nk][2 nw][npw_max] (each orbital twice,
+    // a band view with nocc = nemp = nw), and the scratch of rp_interaction
+    int nw = 0;
+    rp::DevBuf d_wcoef, s_wm, s_wb, s_wy, s_wtab, s_wout;
     int num_sms = 0;
     unsigned long long wait_ns = 2000000000ULL;   // limit of a bounded device wait (rp_set_wait_limit)
     std::map<int, int> tile_bn;                   // NG -> raw rows per tile of the BF16x3 contraction
@@ -112,7 +117,9 @@ int cuda_fail(rp_ctx* c, cudaError_t e, const char* where);
 int ensure(rp_ctx* c, DevBuf& b, size_t bytes);
 void release(DevBuf& b);
 int plan_q(rp_ctx* c, const double q[3]);                  // with the context's cut-off
-int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps);
+// (exact: enlarge a requested grid on which the product folds onto the sphere, so that the transforms
+// give the plain convolution of Eq. ism)
+int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps, bool exact = false);
 
 // ---- kernel launchers (each returns cudaError_t of the launch) ----
 // gather + inverse transform of nb bands into u[nb][N1][N2][N3] (complex double)
@@ -165,5 +172,13 @@ cudaError_t launch_contract_tf32x3(const void* M, bool m32, long long ldm, long 
 // Dyson step
 cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W,
                          int* err_flag, cudaStream_t st);
+// interaction step (Sec. 2.4): densities of the Wannier functions, W times their conjugates, bilinear forms
+cudaError_t launch_wan_density(const double2* M, long long ldm, int nk, int nw, int nR, const double2* phase,
+                               double2* B, int ngp, cudaStream_t st);
+cudaError_t launch_wan_wrhs(const double2* W, int ng, int nf, const double2* B, int ngp, const int* pe, int nb,
+                            double2* Y, cudaStream_t st);
+cudaError_t launch_wan_reduce(const double2* B, int ngp, const double* v, const unsigned char* in_eps, const int* pe,
+                              int ng, const double2* Y, int nw, int nR, int nf, const double2* qph, double inv_nq,
+                              int accumulate, double2* U, double2* J, cudaStream_t st);
 
 }  // namespace rp
