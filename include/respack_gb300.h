@@ -195,6 +195,35 @@ int rp_solve_w_batched(rp_ctx* ctx, int nq, const double* q_frac, const double* 
                        const double* const* chi0, double* const* W_out, double* const* tail_out,
                        int on_device, void* cuda_stream);
 
+/* rp_build_chi0_q0 -- chi0 in the limit q -> 0 along the direction qhat[3] (Cartesian, any length > 0)
+ *   for an insulator (band-index occupations), with its head and wings (Sec. 2.3, Eq. eps00 without
+ *   the intraband term, Eq. momentum).  The long-wavelength limit of the G = 0 pair density is taken
+ *   from k.p: M^0_ao(k+q, k) / |q| -> u_b = qhat.p_ao(k) / (E_ak - E_ok), p_ao = sum_G C_a(k+G)^*
+ *   (k+G) C_o(k+G) (exact for a local potential; a pair with E_ak = E_ok is not allowed).
+ *   chi0_out [io] c128 [nfreq][NG+1][NG+1], NG of the epsilon sphere of q = 0 (G != 0): index 0 holds
+ *   lim chi_00 / q^2 at [0][0], lim chi_G0 / |q| at [G][0] and lim chi_0G / |q| at [0][G]; indices
+ *   1..NG the body, equal to rp_build_chi0 at q = 0.  Other arguments and errors as rp_build_chi0. */
+int rp_build_chi0_q0(rp_ctx* ctx, const double qhat[3], int axis, int ordering, int nfreq, const double* freq_ha,
+                     double delta_ha, double delta_a, double delta_r, int precision, double* chi0_out,
+                     int on_device, void* cuda_stream);
+
+/* rp_solve_w_q0 -- the Dyson step of rp_solve_w for the extended q -> 0 matrix of rp_build_chi0_q0:
+ *   eps_00 = 1 - (4 pi/Omega) chi_00/q^2, eps_G0 = -(4 pi/Omega) (chi_G0/|q|) / |G| and its transpose
+ *   partner, the body as at q = 0, inverted as one (NG+1) matrix.  W_out [io] c128 [nfreq][NG+1][NG+1]
+ *   = v^1/2 eps^-1 v^1/2 with v^1/2 = sqrt(4 pi/Omega) for index 0, so that W_out[f][0][0] is
+ *   q^2 W_00 = (4 pi/Omega) eps^-1_00 and W_out[f][G][0] is |q| W_G0 (the q -> 0 divergences taken
+ *   out).  tail_out as rp_solve_w at q = 0.  Errors as rp_solve_w. */
+int rp_solve_w_q0(rp_ctx* ctx, int nfreq, const double* chi0, double* W_out, double* tail_out, int on_device,
+                  void* cuda_stream);
+
+/* rp_optics -- macroscopic optical quantities (Eqs. epsilonM, eels, optical-conductivity,
+ *   reflectance) from W00 c128 [nfreq] (host): the elements W_out[f][0][0] of rp_solve_w_q0, i.e.
+ *   (4 pi/Omega) eps^-1_00.  out double [nfreq][5] (host): Re eps_M, Im eps_M (eps_M = 1/eps^-1_00),
+ *   the loss function -Im eps^-1_00, Re sigma = w Im eps_M / (4 pi) (atomic units; freq_ha[f] real
+ *   frequencies) and the normal-incidence reflectivity |(1 - sqrt(eps^-1_00))/(1 + sqrt(eps^-1_00))|^2.
+ *   RP_ERR_NUMERIC for a zero or non-finite eps^-1_00.  Host arithmetic only. */
+int rp_optics(rp_ctx* ctx, int nfreq, const double* freq_ha, const double* W00, double* out);
+
 /* rp_load_wannier -- Wannier functions of the interaction step (Sec. 2.4): coef c128
  *   [nk][nw][npw_max] (host) holds, for each mesh point k, the plane-wave coefficients of the Bloch
  *   orbitals phi~_ik = sum over lattice vectors R of phi_iR e^{ik.R}, normalised on the crystal like the

@@ -28,7 +28,7 @@ EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density"
            "rp_profile_read", "rp_last_error", "rp_destroy", "rp_contract_chi0_static", "rp_sphere_size_at",
            "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_contract_chi0_static_status",
            "rp_build_chi0_kset", "rp_tune_contraction", "rp_set_contraction_tile",
-           "rp_load_wannier", "rp_interaction"]
+           "rp_load_wannier", "rp_interaction", "rp_build_chi0_q0", "rp_solve_w_q0", "rp_optics"]
 
 
 class RPError(RuntimeError):
@@ -72,6 +72,9 @@ def library():
         "rp_tune_contraction": (I, [P, I, LL, I, ctypes.POINTER(I), P]),
         "rp_set_contraction_tile": (I, [P, I, I]),
         "rp_load_wannier": (I, [P, I, P]),
+        "rp_build_chi0_q0": (I, [P, P, I, I, I, P, D, D, D, I, P, I, P]),
+        "rp_solve_w_q0": (I, [P, I, P, P, P, I, P]),
+        "rp_optics": (I, [P, I, P, P, P]),
         "rp_interaction": (I, [P, P, I, P, I, P, P, P, I, I, P]),
         "rp_contract_chi0_static_status": (I, [P]),
     }
@@ -303,6 +306,41 @@ class Context:
 
     def rp_check_numeric(self):
         self._check(self._lib.rp_check_numeric(self._h))
+
+    def rp_build_chi0_q0(self, qhat, axis, ordering, freq, delta, precision=RP_FP64_NATIVE, delta_a=1e-8,
+                         delta_r=1e-8, out=None):
+        """Extended chi0 [nfreq][NG+1][NG+1] at q -> 0 along qhat (index 0: head and wings)."""
+        g, _ = self.rp_sphere_size(np.zeros(3))
+        fr, pf = _host(freq, np.float64)
+        out, dev = self._out(out, (len(fr), len(g) + 1, len(g) + 1))
+        qh, pq = _host(qhat, np.float64)
+        self._check(self._lib.rp_build_chi0_q0(self._h, pq, int(axis), int(ordering), len(fr), pf, float(delta),
+                                               float(delta_a), float(delta_r), int(precision), self._ptr(out, dev),
+                                               dev, _stream() if dev else None))
+        return out
+
+    def rp_solve_w_q0(self, chi0, out=None):
+        """W of the extended q -> 0 matrix (W[f][0][0] = (4 pi/Omega) eps^-1_00)."""
+        dev = 1 if _is_torch(chi0) else 0
+        if dev:
+            import torch
+            out = torch.empty_like(chi0) if out is None else out
+            pc = _dev_ptr(chi0)
+        else:
+            chi0 = np.ascontiguousarray(chi0, dtype=np.complex128)
+            out = np.zeros_like(chi0) if out is None else out
+            pc = chi0.ctypes.data_as(ctypes.c_void_p)
+        self._check(self._lib.rp_solve_w_q0(self._h, int(chi0.shape[0]), pc, self._ptr(out, dev), None, dev,
+                                            _stream() if dev else None))
+        return out
+
+    def rp_optics(self, freq, W00):
+        """[nfreq][5]: Re eps_M, Im eps_M, loss function, Re sigma, reflectivity."""
+        fr, pf = _host(freq, np.float64)
+        w_, pw = _host(W00, np.complex128)
+        out = np.zeros((len(fr), 5))
+        self._check(self._lib.rp_optics(self._h, len(fr), pf, pw, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
 
     def rp_load_wannier(self, coef):
         """coef [nk][nw][npw_max]: plane-wave coefficients of the Wannier functions' Bloch orbitals."""

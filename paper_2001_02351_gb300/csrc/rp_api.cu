@@ -2,6 +2,7 @@
 // order of kernel launches for each entry point.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <set>
@@ -684,11 +685,15 @@ int rp_contract_chi0(rp_ctx* c, int ng, long long K, int nfreq, const double* M,
 
 // chi0 of q summed over the pairs of the k points in klist[nks] (all k when klist is NULL), with
 // weights from the whole mesh's tetrahedra
+// With qhat (q = 0 only) the block of pair densities gets a head row u_b = qhat.p_b / D_b above the
+// sphere rows, and chi0_out is the extended [nfreq][NG+1][NG+1] matrix (index 0: head and wings).
 static int build_chi0(rp_ctx* c, const double q[3], double ecut_eps, int axis, int ordering, int nfreq,
                       const double* freq, double delta, double da, double dr, int precision, double* chi0_out,
-                      int on_device, void* stream, int nks = 0, const int* klist = nullptr) {
+                      int on_device, void* stream, int nks = 0, const int* klist = nullptr,
+                      const double* qhat = nullptr) {
     int s = check_ready_cut(c, q, ecut_eps);
     if (s) return s;
+    if (qhat && (q[0] != 0.0 || q[1] != 0.0 || q[2] != 0.0)) return fail(c, RP_ERR_ARG, "the head row needs q = 0");
     if ((s = check_freq(c, axis, ordering, nfreq, freq, delta, da, dr))) return s;
     if (!chi0_out) return fail(c, RP_ERR_ARG, "chi0_out is NULL");
     // runs of consecutive k points: [runs[2i], runs[2i+1])
@@ -709,7 +714,8 @@ static int build_chi0(rp_ctx* c, const double q[3], double ecut_eps, int axis, i
     if (precision != RP_FP64_NATIVE && precision != RP_BF16X3 && precision != RP_TF32X3)
         return fail(c, RP_ERR_UNSUPPORTED, "precision not built");
     cudaStream_t st = (cudaStream_t)stream;
-    const int ng = c->plan.ng;
+    const int ngs = c->plan.ng;                       // sphere rows
+    const int ng = qhat ? ngs + 1 : ngs;               // rows of the contraction
     const long long K = (long long)c->nk * c->nemp * c->nocc;
     const long long kcols = (long long)c->nemp * c->nocc;
     // k points per contraction launch: about 64k pair columns
@@ -737,7 +743,13 @@ static int build_chi0(rp_ctx* c, const double q[3], double ecut_eps, int axis, i
         for (int k0 = runs[r]; k0 < runs[r + 1]; k0 += kb) {
             const int k1 = std::min(runs[r + 1], k0 + kb);
             const long long cols = (long long)(k1 - k0) * kcols;
-            if ((s = pair_density_device(c, k0, k1, M, m32, cols, 0, st))) return s;
+            // sphere rows from row 1 when the head row is there
+            void* Ms = !qhat ? M : (m32 ? (void*)((float2*)M + cols) : (void*)((double2*)M + cols));
+            if ((s = pair_density_device(c, k0, k1, Ms, m32, cols, 0, st))) return s;
+            if (qhat) {
+                cudaError_t e = launch_head_row(c, k0, k1 - k0, qhat, m32, M, 0, st);
+                if (e != cudaSuccess) return cuda_fail(c, e, "head row");
+            }
             if ((s = contract_block(c, precision, M, m32, cols, 0, cols, w, K, (long long)k0 * kcols, nfreq, ng, chi,
                                     first ? 0 : 1, st)))
                 return s;
@@ -888,6 +900,86 @@ int rp_build_chi0(rp_ctx* c, const double q[3], int axis, int ordering, int nfre
     if (!c) return RP_ERR_ARG;
     return build_chi0(c, q, c->ecut_eps, axis, ordering, nfreq, freq, delta, da, dr, precision, chi0_out, on_device,
                       stream);
+}
+
+int rp_build_chi0_q0(rp_ctx* c, const double qhat[3], int axis, int ordering, int nfreq, const double* freq,
+                     double delta, double da, double dr, int precision, double* chi0_out, int on_device,
+                     void* stream) {
+    if (!c) return RP_ERR_ARG;
+    if (!qhat) return fail(c, RP_ERR_ARG, "qhat is NULL");
+    const double n = std::sqrt(qhat[0] * qhat[0] + qhat[1] * qhat[1] + qhat[2] * qhat[2]);
+    if (!(n > 0.0) || !std::isfinite(n)) return fail(c, RP_ERR_ARG, "qhat must be a nonzero direction");
+    const double u[3] = {qhat[0] / n, qhat[1] / n, qhat[2] / n};
+    const double q0[3] = {0.0, 0.0, 0.0};
+    return build_chi0(c, q0, c->ecut_eps, axis, ordering, nfreq, freq, delta, da, dr, precision, chi0_out, on_device,
+                      stream, 0, nullptr, u);
+}
+
+int rp_solve_w_q0(rp_ctx* c, int nfreq, const double* chi0, double* W_out, double* tail_out, int on_device,
+                  void* stream) {
+    const double q0[3] = {0.0, 0.0, 0.0};
+    int s = check_ready(c, q0);
+    if (s) return s;
+    if (nfreq < 1 || !chi0 || !W_out) return fail(c, RP_ERR_ARG, "bad Dyson arguments");
+    const int n = c->plan.ng + 1;
+    if (n > 4096) return fail(c, RP_ERR_UNSUPPORTED, "NG above 4096");
+    cudaStream_t st = (cudaStream_t)stream;
+    // v^1/2 of the extended rows: sqrt(4 pi/Omega) for the head (its 1/|q| is carried by the head row)
+    std::vector<double> vx(n);
+    vx[0] = std::sqrt(4.0 * M_PI / c->omega);
+    for (int g = 1; g < n; ++g) vx[g] = c->plan.vs[g - 1];
+    const size_t bc = (size_t)nfreq * n * n * sizeof(double2);
+    if ((s = ensure(c, c->s_io3, n * sizeof(double)))) return s;
+    cudaError_t e = cudaMemcpyAsync(c->s_io3.p, vx.data(), n * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "v^1/2");
+    const double2* dchi = (const double2*)chi0;
+    double2* dW = (double2*)W_out;
+    if (!on_device) {
+        if ((s = ensure(c, c->s_io1, bc)) || (s = ensure(c, c->s_io2, bc))) return s;
+        if ((e = cudaMemcpyAsync(c->s_io1.p, chi0, bc, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(c, e, "copy chi0");
+        dchi = (const double2*)c->s_io1.p;
+        dW = (double2*)c->s_io2.p;
+    }
+    prof_begin(c, 4, st);
+    e = launch_dyson(dchi, (const double*)c->s_io3.p, n, nfreq, dW, (int*)c->d_err.p, st);
+    prof_end(c, 4, st, 1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Dyson solve");
+    if (tail_out && c->plan.ntail > 0) {
+        if (on_device) {
+            e = cudaMemcpyAsync(tail_out, c->plan.tailv.data(), c->plan.ntail * sizeof(double), cudaMemcpyHostToDevice,
+                                st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "tail");
+        } else {
+            std::memcpy(tail_out, c->plan.tailv.data(), c->plan.ntail * sizeof(double));
+        }
+    }
+    if (!on_device) {
+        if ((e = cudaMemcpyAsync(W_out, dW, bc, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(c, e, "copy W");
+        if ((s = finish(c, st, 0))) return s;
+        return rp_check_numeric(c);
+    }
+    return finish(c, st, 1);
+}
+
+int rp_optics(rp_ctx* c, int nfreq, const double* freq_ha, const double* W00, double* out) {
+    if (!c) return RP_ERR_ARG;
+    if (nfreq < 1 || !freq_ha || !W00 || !out) return fail(c, RP_ERR_ARG, "bad optics arguments");
+    const double s = c->omega / (4.0 * M_PI);
+    for (int f = 0; f < nfreq; ++f) {
+        const std::complex<double> einv(W00[2 * f] * s, W00[2 * f + 1] * s);
+        if (!(std::abs(einv) > 0.0) || !std::isfinite(std::abs(einv))) return fail(c, RP_ERR_NUMERIC, "eps^-1_00 zero or not finite");
+        const std::complex<double> em = 1.0 / einv;
+        const std::complex<double> r = (1.0 - std::sqrt(einv)) / (1.0 + std::sqrt(einv));
+        double* o = out + 5 * f;
+        o[0] = em.real();
+        o[1] = em.imag();
+        o[2] = -einv.imag();
+        o[3] = freq_ha[f] / (4.0 * M_PI) * em.imag();
+        o[4] = std::norm(r);
+    }
+    return RP_OK;
 }
 
 int rp_build_chi0_kset(rp_ctx* c, const double q[3], int nks, const int* k_list, int axis, int ordering, int nfreq,

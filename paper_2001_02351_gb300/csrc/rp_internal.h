@@ -172,6 +172,10 @@ cudaError_t launch_contract_tf32x3(const void* M, bool m32, long long ldm, long 
 // Dyson step
 cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W,
                          int* err_flag, cudaStream_t st);
+// head row at q -> 0: u_b = qhat.p_b / D_b of the pairs of k in [k0, k0 + nkb) into M[col0 + b] (complex
+// float when fp32, else complex double)
+cudaError_t launch_head_row(rp_ctx* c, int k0, int nkb, const double qhat[3], bool fp32, void* M, long long col0,
+                            cudaStream_t st);
 // interaction step (Sec. 2.4): densities of the Wannier functions, W times their conjugates, bilinear forms
 cudaError_t launch_wan_density(const double2* M, long long ldm, int nk, int nw, int nR, const double2* phase,
                                double2* B, int ngp, cudaStream_t st);
