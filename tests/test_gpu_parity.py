@@ -505,3 +505,25 @@ def test_gamma_point_build_and_w(tiny):
     assert np.all(_rel_fro(W, W_ref) < 1e-11)
     chi = ctx.rp_build_chi0(q, _axis(tiny), _ordering(tiny), tiny.freq, tiny.delta, rp.RP_BF16X3)
     assert np.all(_rel_fro(chi, chi_ref) < BF16X3_TOL)
+
+
+def test_constrained_chi0_with_wannier_weights():
+    """cRPA (Eq. chi with T of Eq. tak from the Wannier construction): a window of two occupied and two
+    empty bands and two projected Gaussians, so 0 < T < 1 on the window and pairs inside it are
+    partly removed; FP64 and BF16x3 against the oracle on the small workload."""
+    from dataclasses import replace
+    from synth.wannier import gaussian_wannier
+    wl = workload("small")
+    _, T = gaussian_wannier(wl.bands, 4, np.array([(0.1, 0.2, 0.0), (0.5, 0.4, 0.3)]), 1.6, first=wl.nocc - 2,
+                            with_T=True)
+    wl = replace(wl, T=T)
+    ctx = _ctx(wl)
+    q = wl.q[0]
+    G = OL.eps_sphere(wl.cell.lat, q, wl.ecut_eps[0])
+    M = OP.pair_density(wl.bands, wl.nocc, wl.nemp, q, G, fft=wl.fft)
+    chi_ref = OC.chi0(M, OC.pair_weights(wl, q))
+    chi_rpa = OC.chi0(M, OC.pair_weights(replace(wl, T=None), q))
+    assert np.all(_rel_fro(chi_ref, chi_rpa) > 1e-3)         # the constraint changes chi0
+    for p, tol in ((rp.RP_FP64_NATIVE, 1e-11), (rp.RP_BF16X3, BF16X3_TOL)):
+        chi = ctx.rp_build_chi0(q, _axis(wl), _ordering(wl), wl.freq, wl.delta, p)
+        assert np.all(_rel_fro(chi, chi_ref) < tol)

@@ -304,3 +304,32 @@ def test_crpa_factor_indices(small):
     assert np.abs(w0[:, cols]).min() > 0
     assert np.all(w1[:, cols] == 0)
     assert np.array_equal(w1[:, rest], w0[:, rest])
+
+
+def test_crpa_weights_from_the_wannier_construction(small):
+    """Eq. tak with the projected-Gaussian stand-in: 0 <= T <= 1, the weights of a k point sum to the
+    number of Wannier functions, and when the orbitals span the whole window (as many orbitals as
+    window bands) T is 1 there, so the constrained chi0 is the full chi0 less the chi0 of the
+    window-to-window transitions alone."""
+    from synth.wannier import gaussian_wannier
+    wl = replace(small, axis="imag", delta=0.0, freq=np.array([0.05, 0.4]))
+    b = wl.bands
+    first, nwin = wl.nocc - 2, 4                  # two occupied and two empty bands
+    centers = np.array([(0.1, 0.2, 0.0), (0.5, 0.4, 0.3)])
+    _, T = gaussian_wannier(b, nwin, centers, 1.6, first=first, with_T=True)
+    assert T.min() >= -1e-14 and T.max() <= 1 + 1e-12
+    assert np.allclose(T.sum(axis=1), 2.0, atol=1e-10)
+    centers4 = np.array([(0.1, 0.2, 0.0), (0.5, 0.4, 0.3), (0.7, 0.1, 0.6), (0.3, 0.8, 0.9)])
+    _, T4 = gaussian_wannier(b, nwin, centers4, 1.6, first=first, with_T=True)
+    assert np.allclose(T4[:, first:first + nwin], 1.0, atol=1e-10)
+    q = wl.q[0]
+    w_full = C.pair_weights(wl, q)
+    w_crpa = C.pair_weights(replace(wl, T=T4), q)
+    # pairs (a, o) with both bands in the window: a < first + nwin (empty index a + nocc), o >= first
+    nk = b.kfrac.shape[0]
+    a = np.arange(wl.nemp)[:, None] + wl.nocc
+    o = np.arange(wl.nocc)[None, :]
+    inside = ((a < first + nwin) & (o >= first)).reshape(-1)
+    mask = np.tile(inside, nk)
+    assert np.abs(w_crpa[:, mask]).max() <= 1e-9 * np.abs(w_full).max()      # T = 1 up to rounding
+    assert np.array_equal(w_crpa[:, ~mask], w_full[:, ~mask])
