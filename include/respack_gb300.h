@@ -199,7 +199,8 @@ int rp_solve_w_batched(rp_ctx* ctx, int nq, const double* q_frac, const double* 
  *   for an insulator (band-index occupations), with its head and wings (Sec. 2.3, Eq. eps00 without
  *   the intraband term, Eq. momentum).  The long-wavelength limit of the G = 0 pair density is taken
  *   from k.p: M^0_ao(k+q, k) / |q| -> u_b = qhat.p_ao(k) / (E_ak - E_ok), p_ao = sum_G C_a(k+G)^*
- *   (k+G) C_o(k+G) (exact for a local potential; a pair with E_ak = E_ok is not allowed).
+ *   (k+G) C_o(k+G) (exact for a local potential).  RP_ERR_ARG unless the lowest empty band lies above
+ *   the highest occupied one at every k.
  *   chi0_out [io] c128 [nfreq][NG+1][NG+1], NG of the epsilon sphere of q = 0 (G != 0): index 0 holds
  *   lim chi_00 / q^2 at [0][0], lim chi_G0 / |q| at [G][0] and lim chi_0G / |q| at [0][G]; indices
  *   1..NG the body, equal to rp_build_chi0 at q = 0.  Other arguments and errors as rp_build_chi0. */
@@ -215,6 +216,16 @@ int rp_build_chi0_q0(rp_ctx* ctx, const double qhat[3], int axis, int ordering, 
  *   out).  tail_out as rp_solve_w at q = 0.  Errors as rp_solve_w. */
 int rp_solve_w_q0(rp_ctx* ctx, int nfreq, const double* chi0, double* W_out, double* tail_out, int on_device,
                   void* cuda_stream);
+
+/* rp_rotate_q -- a q matrix at a reducible q from the one at its irreducible q_irr (Sec. 3.1,
+ *   Eq. symeps, symmorphic crystal): S int[9] is the rotation as an integer matrix acting on fractional
+ *   row vectors (row i holds the image of the i-th reciprocal basis vector), q_irr S = q + G_s with G_s
+ *   integer; then X_{G,G'}(q) = X_{G*,G'*}(q_irr) for G = G* S + G_s.  Valid for chi0 (when the k sum
+ *   is invariant under S), eps^-1 and W (|q+G| = |q_irr+G*|).  X_irr, X_out [io] c128 [nfreq][NG][NG]
+ *   on the epsilon spheres of q_irr and q.  RP_ERR_ARG if S is not a rotation of the lattice, q is
+ *   not the image of q_irr or the spheres do not map onto each other. */
+int rp_rotate_q(rp_ctx* ctx, const double q_irr[3], const double q_frac[3], const int S[9], int nfreq,
+                const double* X_irr, double* X_out, int on_device, void* cuda_stream);
 
 /* rp_optics -- macroscopic optical quantities (Eqs. epsilonM, eels, optical-conductivity,
  *   reflectance) from W00 c128 [nfreq] (host): the elements W_out[f][0][0] of rp_solve_w_q0, i.e.

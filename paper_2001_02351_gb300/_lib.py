@@ -28,7 +28,8 @@ EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density"
            "rp_profile_read", "rp_last_error", "rp_destroy", "rp_contract_chi0_static", "rp_sphere_size_at",
            "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_contract_chi0_static_status",
            "rp_build_chi0_kset", "rp_tune_contraction", "rp_set_contraction_tile",
-           "rp_load_wannier", "rp_interaction", "rp_build_chi0_q0", "rp_solve_w_q0", "rp_optics"]
+           "rp_load_wannier", "rp_interaction", "rp_build_chi0_q0", "rp_solve_w_q0", "rp_optics",
+           "rp_rotate_q"]
 
 
 class RPError(RuntimeError):
@@ -75,6 +76,7 @@ def library():
         "rp_build_chi0_q0": (I, [P, P, I, I, I, P, D, D, D, I, P, I, P]),
         "rp_solve_w_q0": (I, [P, I, P, P, P, I, P]),
         "rp_optics": (I, [P, I, P, P, P]),
+        "rp_rotate_q": (I, [P, P, P, P, I, P, P, I, P]),
         "rp_interaction": (I, [P, P, I, P, I, P, P, P, I, I, P]),
         "rp_contract_chi0_static_status": (I, [P]),
     }
@@ -332,6 +334,24 @@ class Context:
             pc = chi0.ctypes.data_as(ctypes.c_void_p)
         self._check(self._lib.rp_solve_w_q0(self._h, int(chi0.shape[0]), pc, self._ptr(out, dev), None, dev,
                                             _stream() if dev else None))
+        return out
+
+    def rp_rotate_q(self, q_irr, q, S, X_irr, out=None):
+        """X at q from X_irr at q_irr under the integer rotation S (k -> k S)."""
+        qi, pqi = _host(q_irr, np.float64)
+        q_, pq = _host(q, np.float64)
+        S_, pS = _host(np.asarray(S).reshape(9), np.int32)
+        dev = 1 if _is_torch(X_irr) else 0
+        if dev:
+            import torch
+            out = torch.empty_like(X_irr) if out is None else out
+            px = _dev_ptr(X_irr)
+        else:
+            X_irr = np.ascontiguousarray(X_irr, dtype=np.complex128)
+            out = np.zeros_like(X_irr) if out is None else out
+            px = X_irr.ctypes.data_as(ctypes.c_void_p)
+        self._check(self._lib.rp_rotate_q(self._h, pqi, pq, pS, int(X_irr.shape[0]), px, self._ptr(out, dev), dev,
+                                          _stream() if dev else None))
         return out
 
     def rp_optics(self, freq, W00):

@@ -5,6 +5,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <set>
 #include <string>
 #include <vector>
@@ -911,6 +912,11 @@ int rp_build_chi0_q0(rp_ctx* c, const double qhat[3], int axis, int ordering, in
     if (!(n > 0.0) || !std::isfinite(n)) return fail(c, RP_ERR_ARG, "qhat must be a nonzero direction");
     const double u[3] = {qhat[0] / n, qhat[1] / n, qhat[2] / n};
     const double q0[3] = {0.0, 0.0, 0.0};
+    // u = qhat.p / (E_ak - E_ok) needs the lowest empty band above the highest occupied one at every k
+    if (c->loaded)
+        for (int k = 0; k < c->nk; ++k)
+            if (!(c->energy[(size_t)k * c->nband + c->nocc] > c->energy[(size_t)k * c->nband + c->nocc - 1]))
+                return fail(c, RP_ERR_ARG, "the q -> 0 head needs a gap between occupied and empty bands at every k");
     return build_chi0(c, q0, c->ecut_eps, axis, ordering, nfreq, freq, delta, da, dr, precision, chi0_out, on_device,
                       stream, 0, nullptr, u);
 }
@@ -961,6 +967,70 @@ int rp_solve_w_q0(rp_ctx* c, int nfreq, const double* chi0, double* W_out, doubl
         return rp_check_numeric(c);
     }
     return finish(c, st, 1);
+}
+
+int rp_rotate_q(rp_ctx* c, const double q_irr[3], const double q[3], const int S[9], int nfreq, const double* X_irr,
+                double* X_out, int on_device, void* stream) {
+    if (!c) return RP_ERR_ARG;
+    if (!q_irr || !q || !S || nfreq < 1 || !X_irr || !X_out) return fail(c, RP_ERR_ARG, "bad rotation arguments");
+    // q* S = q + G_s with G_s integer
+    int gs[3];
+    for (int j = 0; j < 3; ++j) {
+        const double v = q_irr[0] * S[0 * 3 + j] + q_irr[1] * S[1 * 3 + j] + q_irr[2] * S[2 * 3 + j] - q[j];
+        gs[j] = (int)llround(v);
+        if (std::fabs(v - gs[j]) > 1e-9) return fail(c, RP_ERR_ARG, "q is not the image of q_irr under S");
+    }
+    // S must be a rotation of the lattice: |(m S) B| = |m B| on the reciprocal basis vectors
+    for (int i = 0; i < 3; ++i) {
+        double f[3] = {0, 0, 0}, g[3] = {0, 0, 0}, a[3], b[3];
+        f[i] = 1.0;
+        for (int j = 0; j < 3; ++j) g[j] = S[i * 3 + j];
+        cart(c, f, a);
+        cart(c, g, b);
+        const double na = a[0] * a[0] + a[1] * a[1] + a[2] * a[2], nb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        if (std::fabs(na - nb) > 1e-9 * na) return fail(c, RP_ERR_ARG, "S is not a rotation of the lattice");
+    }
+    int s = plan_q(c, q_irr);
+    if (s) return s;
+    const std::vector<int> gi = c->plan.gm;
+    if ((s = plan_q(c, q))) return s;
+    const QPlan& P = c->plan;
+    const int n = P.ng;
+    if ((int)gi.size() != 3 * n) return fail(c, RP_ERR_ARG, "the spheres of q_irr and q differ in size");
+    std::map<long long, int> pos;
+    auto key = [](long long a, long long b, long long d) { return ((a + 4096) * 8192 + (b + 4096)) * 8192 + (d + 4096); };
+    for (int g = 0; g < n; ++g) {
+        long long m[3];
+        for (int j = 0; j < 3; ++j)
+            m[j] = (long long)gi[3 * g] * S[0 * 3 + j] + (long long)gi[3 * g + 1] * S[1 * 3 + j] +
+                   (long long)gi[3 * g + 2] * S[2 * 3 + j] + gs[j];
+        pos[key(m[0], m[1], m[2])] = g;
+    }
+    std::vector<int> perm(n);
+    for (int g = 0; g < n; ++g) {
+        auto it = pos.find(key(P.gm[3 * g], P.gm[3 * g + 1], P.gm[3 * g + 2]));
+        if (it == pos.end()) return fail(c, RP_ERR_ARG, "S does not map the sphere of q_irr onto that of q");
+        perm[g] = it->second;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bc = (size_t)nfreq * n * n * sizeof(double2);
+    if ((s = ensure(c, c->s_io3, n * sizeof(int)))) return s;
+    cudaError_t e = cudaMemcpyAsync(c->s_io3.p, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "permutation");
+    const double2* din = (const double2*)X_irr;
+    double2* dout = (double2*)X_out;
+    if (!on_device) {
+        if ((s = ensure(c, c->s_io1, bc)) || (s = ensure(c, c->s_io2, bc))) return s;
+        if ((e = cudaMemcpyAsync(c->s_io1.p, X_irr, bc, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(c, e, "copy X");
+        din = (const double2*)c->s_io1.p;
+        dout = (double2*)c->s_io2.p;
+    }
+    if ((e = launch_rotate(din, (const int*)c->s_io3.p, n, nfreq, dout, c->num_sms, st)) != cudaSuccess)
+        return cuda_fail(c, e, "rotation");
+    if (!on_device && (e = cudaMemcpyAsync(X_out, dout, bc, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "copy X");
+    return finish(c, st, on_device);
 }
 
 int rp_optics(rp_ctx* c, int nfreq, const double* freq_ha, const double* W00, double* out) {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -176,6 +177,9 @@ cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, d
 // float when fp32, else complex double)
 cudaError_t launch_head_row(rp_ctx* c, int k0, int nkb, const double qhat[3], bool fp32, void* M, long long col0,
                             cudaStream_t st);
+// rotation of a q matrix: out[f][i][j] = in[f][perm[i]][perm[j]]
+cudaError_t launch_rotate(const double2* in, const int* perm, int n, int nf, double2* out, int num_sms,
+                          cudaStream_t st);
 // interaction step (Sec. 2.4): densities of the Wannier functions, W times their conjugates, bilinear forms
 cudaError_t launch_wan_density(const double2* M, long long ldm, int nk, int nw, int nR, const double2* phase,
                                double2* B, int ngp, cudaStream_t st);

@@ -22,9 +22,16 @@ def _rel_fro(a, b):
     return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
 
 
+# band counts whose occupied set ends in a gap at every mesh point (the k.p head divides by the
+# transition energy at q = 0)
+INSULATING = {"tiny": dict(nocc=6, nemp=6), "small": dict(nocc=3, nemp=8)}
+
+
 @pytest.mark.parametrize("name", ["tiny", "small"])
 def test_head_and_wings_against_oracle(name):
-    wl = workload(name)
+    wl = workload(name, **INSULATING[name])
+    E = wl.bands.energy
+    assert (E[:, wl.nocc] - E[:, wl.nocc - 1]).min() > 1e-3
     q = np.zeros(3)
     G = OL.eps_sphere(wl.cell.lat, q, wl.ecut_eps[0])
     M = OP.pair_density(wl.bands, wl.nocc, wl.nemp, q, G, fft=wl.fft)
@@ -53,4 +60,13 @@ def test_head_and_wings_against_oracle(name):
     assert np.all(_rel_fro(chi, chi_ref) < 1e-4)
     with pytest.raises(rp.RPError) as e:
         ctx.rp_build_chi0_q0(np.zeros(3), axis, rp.RP_TIME_ORDERED, wl.freq, wl.delta, rp.RP_FP64_NATIVE)
+    assert e.value.code == rp.RP_ERR_ARG
+
+
+def test_head_refuses_a_band_set_without_gap():
+    wl = workload("tiny")                       # 8 + 8 bands: bands 8 and 9 touch at some k
+    assert (wl.bands.energy[:, 8] - wl.bands.energy[:, 7]).min() < 1e-9
+    ctx = rp.context_for(wl)
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_build_chi0_q0(QHAT, rp.RP_AXIS_IMAG, rp.RP_TIME_ORDERED, wl.freq, wl.delta, rp.RP_FP64_NATIVE)
     assert e.value.code == rp.RP_ERR_ARG

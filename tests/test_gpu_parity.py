@@ -527,3 +527,32 @@ def test_constrained_chi0_with_wannier_weights():
     for p, tol in ((rp.RP_FP64_NATIVE, 1e-11), (rp.RP_BF16X3, BF16X3_TOL)):
         chi = ctx.rp_build_chi0(q, _axis(wl), _ordering(wl), wl.freq, wl.delta, p)
         assert np.all(_rel_fro(chi, chi_ref) < tol)
+
+
+def test_rotation_to_reducible_q():
+    """rp_rotate_q against the oracle's rotation of the same matrix, and the rotated GPU chi0 and W of
+    q* against the GPU's direct build at q (6 + 6 bands of the 4^3 cell: both ends of the band list in
+    gaps; Lorentz-exact k sums are checked by the oracle pin, the tetrahedron sum agrees to its
+    integration error)."""
+    from oracle import symmetry as SY
+    from synth.epm import cubic_rotations
+    wl = workload("tiny", nocc=6, nemp=6)
+    ctx = _ctx(wl)
+    qs = np.array([0.25, 0.0, 0.0])
+    S = next(S for S in cubic_rotations(wl.cell.recip) if not np.allclose(np.mod(qs @ S, 1.0), qs))
+    img = qs @ S
+    q = np.mod(img, 1.0)
+    g_s = np.rint(img - q).astype(np.int64)
+    chi_s = ctx.rp_build_chi0(qs, _axis(wl), _ordering(wl), wl.freq, wl.delta, rp.RP_FP64_NATIVE)
+    got = ctx.rp_rotate_q(qs, q, S, chi_s)
+    Gs = OL.eps_sphere(wl.cell.lat, qs, wl.ecut_eps[0])
+    G = OL.eps_sphere(wl.cell.lat, q, wl.ecut_eps[0])
+    assert np.array_equal(got, SY.rotate(chi_s, SY.image_index(Gs, G, S, g_s)))
+    direct = ctx.rp_build_chi0(q, _axis(wl), _ordering(wl), wl.freq, wl.delta, rp.RP_FP64_NATIVE)
+    assert np.all(_rel_fro(got, direct) < 5e-2)
+    W_s, _ = ctx.rp_solve_w(qs, chi_s)
+    W_q, _ = ctx.rp_solve_w(q, got)
+    assert np.all(_rel_fro(ctx.rp_rotate_q(qs, q, S, W_s), W_q) < 1e-12)
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_rotate_q(qs, np.array([0.0, 0.5, 0.0]), S, chi_s)
+    assert e.value.code == rp.RP_ERR_ARG
