@@ -280,6 +280,13 @@ int rp_tune_contraction(rp_ctx* ctx, int ng, long long K, int nfreq, int* bn_out
  *   earlier rp_tune_contraction); bn = 0 removes the entry.  RP_ERR_ARG for a BN not built. */
 int rp_set_contraction_tile(rp_ctx* ctx, int ng, int bn);
 
+/* rp_probe_peaks -- measurement aid with no counterpart in the paper: the device's FP64 FMA rate,
+ *   FP64 tensor (mma.sync m8n8k4) rate and bf16 tcgen05 (M 128, N 256, f32 accumulation) rate in
+ *   TFLOP/s, out double[3] (host), each from a small register- or shared-memory-only kernel timed
+ *   with CUDA events after a warm-up launch on the current device.  Synchronous.  RP_ERR_TIMEOUT if
+ *   the tcgen05 probe's bounded wait gave up. */
+int rp_probe_peaks(double* out);
+
 /* rp_set_wait_limit -- testing aid with no counterpart in the paper: the time after which a
  *   bounded device wait of the context's RP_BF16X3 contraction kernel gives up (default 2e9 ns).
  *   A wait that gives up sets the context's timeout flag and the kernel returns through its

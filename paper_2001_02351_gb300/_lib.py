@@ -29,7 +29,7 @@ EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density"
            "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_contract_chi0_static_status",
            "rp_build_chi0_kset", "rp_tune_contraction", "rp_set_contraction_tile",
            "rp_load_wannier", "rp_interaction", "rp_build_chi0_q0", "rp_solve_w_q0", "rp_optics",
-           "rp_rotate_q"]
+           "rp_rotate_q", "rp_probe_peaks"]
 
 
 class RPError(RuntimeError):
@@ -77,6 +77,7 @@ def library():
         "rp_solve_w_q0": (I, [P, I, P, P, P, I, P]),
         "rp_optics": (I, [P, I, P, P, P]),
         "rp_rotate_q": (I, [P, P, P, P, I, P, P, I, P]),
+        "rp_probe_peaks": (I, [P]),
         "rp_interaction": (I, [P, P, I, P, I, P, P, P, I, I, P]),
         "rp_contract_chi0_static_status": (I, [P]),
     }
@@ -264,11 +265,22 @@ class Context:
             _stream() if dev else None))
         return outs
 
-    def rp_solve_w_batched(self, qs, chi0s, ecut_eps=None):
-        """W of every member of a batch (host arrays): list of (W, tail)."""
+    def rp_solve_w_batched(self, qs, chi0s, ecut_eps=None, outs=None):
+        """W of every member of a batch: list of (W, tail) for host arrays; for CUDA tensors W is
+        written into the tensors of `outs` (no tails) and those are returned."""
         qs_, pq = _host(np.asarray(qs, dtype=np.float64).reshape(-1, 3), np.float64)
         nq = qs_.shape[0]
         cuts = None if ecut_eps is None else np.ascontiguousarray(ecut_eps, dtype=np.float64)
+        if _is_torch(chi0s[0]):
+            import torch
+            outs = [torch.empty_like(c) for c in chi0s] if outs is None else outs
+            P = ctypes.c_void_p
+            pc = (P * nq)(*[_dev_ptr(c).value for c in chi0s])
+            pw = (P * nq)(*[_dev_ptr(w).value for w in outs])
+            self._check(self._lib.rp_solve_w_batched(self._h, nq, pq,
+                                                     None if cuts is None else cuts.ctypes.data_as(P),
+                                                     int(chi0s[0].shape[0]), pc, pw, None, 1, _stream()))
+            return outs
         chis = [np.ascontiguousarray(c, dtype=np.complex128) for c in chi0s]
         Ws = [np.zeros_like(c) for c in chis]
         tails = []
@@ -442,6 +454,16 @@ class Context:
         self._check(self._lib.rp_profile_read(self._h, ms.ctypes.data_as(ctypes.c_void_p),
                                               nl.ctypes.data_as(ctypes.c_void_p)))
         return ms, nl
+
+
+def probe_peaks():
+    """Measured TFLOP/s of the current device: FP64 FMA, FP64 mma.sync, bf16 tcgen05 (rp_probe_peaks)."""
+    lib = library()
+    out = np.zeros(3)
+    code = lib.rp_probe_peaks(out.ctypes.data_as(ctypes.c_void_p))
+    if code != RP_OK:
+        raise RPError(code, "rp_probe_peaks failed")
+    return {"fp64_fma": float(out[0]), "fp64_mma": float(out[1]), "bf16_tcgen05": float(out[2])}
 
 
 def context_for(wl, q_index=0):

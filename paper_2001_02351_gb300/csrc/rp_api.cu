@@ -1033,6 +1033,14 @@ int rp_rotate_q(rp_ctx* c, const double q_irr[3], const double q[3], const int S
     return finish(c, st, on_device);
 }
 
+int rp_probe_peaks(double* out) {
+    if (!out) return RP_ERR_ARG;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RP_ERR_CUDA;
+    return probe_peaks(out, nsm, nullptr);
+}
+
 int rp_optics(rp_ctx* c, int nfreq, const double* freq_ha, const double* W00, double* out) {
     if (!c) return RP_ERR_ARG;
     if (nfreq < 1 || !freq_ha || !W00 || !out) return fail(c, RP_ERR_ARG, "bad optics arguments");

@@ -556,3 +556,12 @@ def test_rotation_to_reducible_q():
     with pytest.raises(rp.RPError) as e:
         ctx.rp_rotate_q(qs, np.array([0.0, 0.5, 0.0]), S, chi_s)
     assert e.value.code == rp.RP_ERR_ARG
+
+
+def test_peak_probes_run():
+    """rp_probe_peaks: the three probe kernels return and give rates of the right order for a GB300
+    (FP64 about 1 TFLOP/s on both paths, bf16 tcgen05 some 1-2.5 PFLOP/s)."""
+    p = rp.probe_peaks()
+    assert 0.1 < p["fp64_fma"] < 20 and 0.1 < p["fp64_mma"] < 20
+    assert 300 < p["bf16_tcgen05"] < 3000
+    print("probes", p)
