@@ -97,9 +97,24 @@ __device__ __forceinline__ uint64_t gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// bounded wait: false (and err_flag set to `code`) if the phase does not complete within limit_ns
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false (and err_flag set to `code`) if the phase does not complete within limit_ns;
+// a zero limit makes one non-blocking test
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code,
                                           uint64_t limit_ns = TC_WAIT_NS) {
+    if (limit_ns == 0) {
+        if (mbar_test(bar, parity)) return true;
+        atomicExch(err, code);
+        return false;
+    }
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
@@ -174,6 +189,7 @@ struct TcArgs {
     double2* chi;
     int* err;
     unsigned long long wait_ns;   // limit of the pipeline's waits (the teardown drains use TC_WAIT_NS)
+    float* stage;                 // per-CTA staging of the accumulators, [grid][2][BN][128], or NULL
 };
 
 // tcgen05.ld of 32 or 16 consecutive accumulator columns of this warp's 32 lanes
@@ -458,6 +474,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ++cj[t];
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * 256);
+                if (args.stage) {
+                    // staged: the accumulator goes to this CTA's slice of the staging buffer with plain
+                    // coalesced stores ([col][lane of the 128]), the accumulator is released, and the FP64
+                    // additions into chi run from the (L2-resident) copy while the next job multiplies
+                    float* stg = args.stage + ((size_t)blockIdx.x * 2 + t) * BN * 128 + (threadIdx.x - 320);
+#pragma unroll 1
+                    for (int ch = 0; ch < NCH; ++ch) {
+                        uint32_t v[32];
+                        tmem_ld32(src + (uint32_t)(ch * 32), v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) stg[(size_t)(ch * 32 + j) * 128] = __uint_as_float(v[j]);
+                    }
+                    if constexpr (REM) {
+                        uint32_t v[16];
+                        tmem_ld16(src + (uint32_t)(NCH * 32), v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) stg[(size_t)(NCH * 32 + j) * 128] = __uint_as_float(v[j]);
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(acce(t));
+                    if (live) {
+#pragma unroll 4
+                        for (int col = gmin; col < gmax; ++col)
+                            atomicAdd(out + (size_t)col * ldo, (double)stg[(size_t)col * 128]);
+                    }
+                    continue;
+                }
 #pragma unroll 1
                 for (int ch = 0; ch < NCH; ++ch) {
                     uint32_t v[32];
@@ -600,7 +643,7 @@ cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, 
                                    int num_sms, cudaStream_t st) {
     cudaError_t e = launch_weights32(K, w, ldw, col0, nf, w32, st);
     if (e != cudaSuccess) return e;
-    return launch_contract_bf16x3_core(hi, lo, K, ng, nf, w32, chi, err, num_sms, TC_WAIT_NS, st, 0);
+    return launch_contract_bf16x3_core(hi, lo, K, ng, nf, w32, chi, err, num_sms, TC_WAIT_NS, st, 0, nullptr);
 }
 
 // tile widths the kernel is built for
@@ -664,9 +707,11 @@ static cudaError_t launch_bn(const CUtensorMap& mraw_hi, const CUtensorMap& mraw
     return cudaGetLastError();
 }
 
+size_t tc_stage_bytes(int num_sms) { return (size_t)num_sms * 2 * 256 * 128 * sizeof(float); }
+
 cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long long K, int ng, int nf,
                                         const void* w32, double2* chi, int* err, int num_sms,
-                                        unsigned long long wait_ns, cudaStream_t st, int bn) {
+                                        unsigned long long wait_ns, cudaStream_t st, int bn, float* stage) {
     if (bn <= 0) bn = tc_pick_bn(ng);
     if (!tc_bn_supported(bn)) return cudaErrorInvalidValue;
     const long long kp2 = tc_kp2(K);
@@ -685,6 +730,7 @@ cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long lon
     a.nwin = (a.nst + TC_FLUSH_STAGES - 1) / TC_FLUSH_STAGES;
     a.chi = chi; a.err = err;
     a.wait_ns = wait_ns;
+    a.stage = stage;
     const long long njobs = (long long)a.nfq * a.nblk * a.mt * a.nwin;
     if (njobs > 0x7fffffffLL) return cudaErrorInvalidValue;
     const int grid = njobs < num_sms ? (int)njobs : num_sms;
