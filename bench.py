@@ -265,6 +265,56 @@ def run_kernel(args):
     return 0
 
 
+def run_interaction(args):
+    """The interaction step (screened direct and exchange integrals of Wannier functions) for the q
+    points of a workload's mesh, timed per q on the device with a seeded W = v^1/2 (1 + X) v^1/2 per
+    q: the Wannier pair densities on the wave-function sphere, the density rows, one pass over W and
+    the bilinear forms."""
+    import torch
+    import paper_2001_02351_gb300 as rp
+    from synth import make_workload
+    from synth.wannier import gaussian_wannier
+    wl = make_workload(args.workload)
+    torch.cuda.set_device(0)
+    b = wl.bands
+    nw = 3
+    coef_w = gaussian_wannier(b, wl.nocc, np.array([(0.1, 0.2, 0.0), (0.5, 0.4, 0.3), (0.7, 0.1, 0.6)]), 1.6)
+    ctx = rp.context_for(wl)
+    ctx.rp_load_wannier(coef_w)
+    R = np.array([(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, -1, 1)])
+    nf = len(wl.freq)
+    rng = np.random.default_rng(5)
+    qs = b.kfrac[rng.choice(len(b.kfrac), size=min(8, len(b.kfrac)), replace=False)]
+    Ws = []
+    for q in qs:
+        g, _ = ctx.rp_sphere_size(q)
+        vs = np.sqrt(4 * np.pi / b.cell.omega) / np.linalg.norm((g + q) @ b.cell.recip, axis=1)
+        X = 0.05 * (rng.standard_normal((len(g), len(g))) + 1j * rng.standard_normal((len(g), len(g))))
+        W1 = (np.eye(len(g)) + X + X.conj().T) * vs[:, None] * vs[None, :]
+        Ws.append(torch.from_numpy(np.repeat(W1[None], nf, axis=0)).cuda())
+    U = J = None
+    for i, q in enumerate(qs):                    # warm-up pass
+        U, J = ctx.rp_interaction(q, R, W=Ws[i], U=U, J=J, accumulate=i > 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i, q in enumerate(qs):
+        U, J = ctx.rp_interaction(q, R, W=Ws[i], U=U, J=J, accumulate=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / len(qs)
+    ng = [W.shape[1] for W in Ws]
+    nb = nw + len(R) * nw * nw
+    wbytes = np.mean([nf * n * n * 16 for n in ng])
+    flop = np.mean([8.0 * nf * n * n * nb for n in ng])
+    print(json.dumps({"kernel": "interaction", "workload": args.workload, "nq_timed": len(qs), "nw": nw, "nR": len(R),
+                      "nfreq": nf, "ng_mean": float(np.mean(ng)), "ms_per_q": ms,
+                      "W_read_GBps": wbytes / (ms * 1e-3) / 1e9, "W_rows_fp64_TFLOPs": flop / (ms * 1e-3) / 1e12,
+                      "note": "per q: Wannier pair densities on the wave-function sphere, density rows, one pass over "
+                              "W against nw + nR nw^2 rows, bilinear forms"}), flush=True)
+    return 0
+
+
 def run_batched(args):
     """Every q of the batched workload's mesh (uneven epsilon spheres) in one batched build and one
     batched Dyson call per step; the metric's count summed over the q points."""
@@ -337,7 +387,7 @@ def main():
     ap.add_argument("--workload", default="precision")
     ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--shard", default="replica", choices=["replica", "k"])
-    ap.add_argument("--kernel", default=None, choices=[None, "contraction"])
+    ap.add_argument("--kernel", default=None, choices=[None, "contraction", "interaction"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -348,6 +398,8 @@ def main():
         return run_reference(args)
     if args.kernel == "contraction":
         return run_kernel(args)
+    if args.kernel == "interaction":
+        return run_interaction(args)
     if args.workload == "batched":
         return run_batched(args)
 

@@ -227,6 +227,16 @@ int rp_solve_w_q0(rp_ctx* ctx, int nfreq, const double* chi0, double* W_out, dou
 int rp_rotate_q(rp_ctx* ctx, const double q_irr[3], const double q_frac[3], const int S[9], int nfreq,
                 const double* X_irr, double* X_out, int on_device, void* cuda_stream);
 
+/* rp_plasma -- the intraband plasma frequency of the usual RPA (Sec. 2.3, Eq. plasma), a Fermi-surface
+ *   integral over every loaded band:
+ *     (w_pl^2)^{mu nu} = (4 pi/Omega)(2/N_k) sum_{k,a} (1 - T_ak^2) p^mu_aa(k) p^nu_aa(k) delta(E_ak - E_F),
+ *   p_aa = sum_G |C_a(k+G)|^2 (k+G) (Eq. momentum, local potential), the delta function integrated with
+ *   the tetrahedra of the frequency weights (linear interpolation of E_a over each).  omega2_out
+ *   double[9] (host, Cartesian, row-major; Ha^2): w_pl^2 for each pair of directions, so that the
+ *   Drude term of Eq. eps00 along qhat is qhat.w_pl^2.qhat / (w (w + i delta)).  The bands that cross
+ *   E_F must be among the loaded ones.  Synchronous. */
+int rp_plasma(rp_ctx* ctx, double fermi_ha, double* omega2_out);
+
 /* rp_optics -- macroscopic optical quantities (Eqs. epsilonM, eels, optical-conductivity,
  *   reflectance) from W00 c128 [nfreq] (host): the elements W_out[f][0][0] of rp_solve_w_q0, i.e.
  *   (4 pi/Omega) eps^-1_00.  out double [nfreq][5] (host): Re eps_M, Im eps_M (eps_M = 1/eps^-1_00),

@@ -29,7 +29,7 @@ EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density"
            "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_contract_chi0_static_status",
            "rp_build_chi0_kset", "rp_tune_contraction", "rp_set_contraction_tile",
            "rp_load_wannier", "rp_interaction", "rp_build_chi0_q0", "rp_solve_w_q0", "rp_optics",
-           "rp_rotate_q", "rp_probe_peaks"]
+           "rp_rotate_q", "rp_probe_peaks", "rp_plasma"]
 
 
 class RPError(RuntimeError):
@@ -78,6 +78,7 @@ def library():
         "rp_optics": (I, [P, I, P, P, P]),
         "rp_rotate_q": (I, [P, P, P, P, I, P, P, I, P]),
         "rp_probe_peaks": (I, [P]),
+        "rp_plasma": (I, [P, D, P]),
         "rp_interaction": (I, [P, P, I, P, I, P, P, P, I, I, P]),
         "rp_contract_chi0_static_status": (I, [P]),
     }
@@ -365,6 +366,12 @@ class Context:
         self._check(self._lib.rp_rotate_q(self._h, pqi, pq, pS, int(X_irr.shape[0]), px, self._ptr(out, dev), dev,
                                           _stream() if dev else None))
         return out
+
+    def rp_plasma(self, fermi):
+        """(w_pl^2)^{mu nu} [3, 3] of Eq. plasma at the Fermi energy `fermi` (Ha)."""
+        out = np.zeros(9)
+        self._check(self._lib.rp_plasma(self._h, float(fermi), out.ctypes.data_as(ctypes.c_void_p)))
+        return out.reshape(3, 3)
 
     def rp_optics(self, freq, W00):
         """[nfreq][5]: Re eps_M, Im eps_M, loss function, Re sigma, reflectivity."""

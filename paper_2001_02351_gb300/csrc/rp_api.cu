@@ -1036,6 +1036,23 @@ int rp_rotate_q(rp_ctx* c, const double q_irr[3], const double q[3], const int S
     return finish(c, st, on_device);
 }
 
+int rp_plasma(rp_ctx* c, double fermi_ha, double* omega2_out) {
+    if (!c) return RP_ERR_ARG;
+    if (!c->loaded) return fail(c, RP_ERR_STATE, "bands not loaded");
+    if (!omega2_out || !std::isfinite(fermi_ha)) return fail(c, RP_ERR_ARG, "bad plasma arguments");
+    int s = ensure(c, c->s_io3, 16 * sizeof(double));
+    if (s) return s;
+    cudaError_t e = cudaMemset(c->s_io3.p, 0, 16 * sizeof(double));
+    if (e == cudaSuccess) e = launch_plasma(c, fermi_ha, (double*)c->s_io3.p, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    double t[9];
+    if (e == cudaSuccess) e = cudaMemcpy(t, c->s_io3.p, 9 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "plasma frequency");
+    t[3] = t[1]; t[6] = t[2]; t[7] = t[5];
+    std::memcpy(omega2_out, t, sizeof(t));
+    return RP_OK;
+}
+
 int rp_probe_peaks(double* out) {
     if (!out) return RP_ERR_ARG;
     int dev = 0, nsm = 0;

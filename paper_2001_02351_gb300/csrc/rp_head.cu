@@ -120,4 +120,111 @@ cudaError_t launch_head_row(rp_ctx* c, int k0, int nkb, const double qhat[3], bo
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// Intraband plasma frequency (Sec. 2.3, Eq. plasma), a Fermi-surface integral over all loaded bands:
+//   (w_pl^2)^{mu nu} = (4 pi / Omega) (2 / N_k) sum_k sum_a (1 - T_ak^2) x_ak p^mu_aa(k) p^nu_aa(k),
+// p_aa(k) = sum_G |C_a(k+G)|^2 (k+G) and x_ak the delta(E_F - E) weight of mesh point k over the 24
+// tetrahedra around it: each tetrahedron adds (1/6) g[d1, d2, d3, d4, d_j], g(x) = (x - E_F)^3_+ , which
+// is a quarter of the cubic B-spline on those five knots evaluated at E_F (Curry-Schoenberg; the
+// Cox-de Boor recursion below has only non-negative terms).  One warp per (k, band): lanes over the
+// plane waves for p, lane 0 for the weight; the six tensor components are added with FP64 atomics.
+
+__device__ double bspline4_at(double t, const double* xs) {
+    // normalised cubic B-spline on the sorted knots xs[0..4] at t
+    double m[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double w = xs[i + 1] - xs[i];
+        m[i] = (w > 0.0 && t >= xs[i] && t < xs[i + 1]) ? 1.0 / w : 0.0;
+    }
+#pragma unroll
+    for (int k = 2; k <= 4; ++k) {
+#pragma unroll
+        for (int i = 0; i + k <= 4; ++i) {
+            const double w = xs[i + k] - xs[i];
+            m[i] = w > 0.0 ? (double)k / ((k - 1) * w) * ((t - xs[i]) * m[i] + (xs[i + k] - t) * m[i + 1]) : 0.0;
+        }
+    }
+    return m[0];
+}
+
+__global__ void __launch_bounds__(256) k_plasma(const double2* __restrict__ coef, const int* __restrict__ miller,
+                                                const int* __restrict__ npw, int npw_max, int nband,
+                                                const double* __restrict__ energy, const double* __restrict__ T,
+                                                const int* __restrict__ tets, const int* __restrict__ tetk, int nk,
+                                                int n1, int n2, int n3, double r00, double r01, double r02,
+                                                double r10, double r11, double r12, double r20, double r21,
+                                                double r22, double ef, double scale, double* __restrict__ out) {
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (wid >= nk * nband) return;
+    const int k = wid / nband, a = wid % nband;
+    // delta weight (lane 0)
+    double x = 0.0;
+    if (lane == 0) {
+        for (int s = 0; s < 24; ++s) {
+            const int e = tetk[24 * k + s];
+            if (e < 0) continue;
+            const int t = e >> 2, j = e & 3;
+            double d[5];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d[i] = energy[(size_t)tets[4 * t + i] * nband + a];
+            d[4] = d[j];
+            // sort five values (insertion)
+#pragma unroll
+            for (int i = 1; i < 5; ++i) {
+                const double v = d[i];
+                int p = i - 1;
+                while (p >= 0 && d[p] > v) { d[p + 1] = d[p]; --p; }
+                d[p + 1] = v;
+            }
+            x += bspline4_at(ef, d) * 0.25 / 6.0;
+        }
+        if (T) {
+            const double tt = T[(size_t)k * nband + a];
+            x *= 1.0 - tt * tt;
+        }
+    }
+    x = __shfl_sync(0xffffffffu, x, 0);
+    if (x == 0.0) return;                       // the whole warp: nothing on the Fermi surface here
+    const int i1 = k / (n2 * n3), i2 = (k / n3) % n2, i3 = k % n3;
+    const double kf0 = (double)i1 / n1, kf1 = (double)i2 / n2, kf2 = (double)i3 / n3;
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    const double2* c = coef + ((size_t)k * nband + a) * npw_max;
+    for (int g = lane; g < npw[k]; g += 32) {
+        const int* m = miller + ((size_t)k * npw_max + g) * 3;
+        const double f0 = m[0] + kf0, f1 = m[1] + kf1, f2 = m[2] + kf2;
+        const double w = c[g].x * c[g].x + c[g].y * c[g].y;
+        p0 += w * (f0 * r00 + f1 * r10 + f2 * r20);
+        p1 += w * (f0 * r01 + f1 * r11 + f2 * r21);
+        p2 += w * (f0 * r02 + f1 * r12 + f2 * r22);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        p0 += __shfl_down_sync(0xffffffffu, p0, off);
+        p1 += __shfl_down_sync(0xffffffffu, p1, off);
+        p2 += __shfl_down_sync(0xffffffffu, p2, off);
+    }
+    if (lane == 0) {
+        const double s = scale * x;
+        atomicAdd(out + 0, s * p0 * p0);
+        atomicAdd(out + 1, s * p0 * p1);
+        atomicAdd(out + 2, s * p0 * p2);
+        atomicAdd(out + 4, s * p1 * p1);
+        atomicAdd(out + 5, s * p1 * p2);
+        atomicAdd(out + 8, s * p2 * p2);
+    }
+}
+
+cudaError_t launch_plasma(rp_ctx* c, double ef, double* out, cudaStream_t st) {
+    const double* b = c->recip;
+    const long long warps = (long long)c->nk * c->nband;
+    const double scale = (4.0 * M_PI / c->omega) * (2.0 / c->nk);
+    k_plasma<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+        (const double2*)c->d_coef.p, (const int*)c->d_miller.p, (const int*)c->d_npw.p, c->npw_max, c->nband,
+        (const double*)c->d_energy.p, c->T.empty() ? nullptr : (const double*)c->d_T.p, (const int*)c->d_tets.p,
+        (const int*)c->d_tetk.p, c->nk, c->kmesh[0], c->kmesh[1], c->kmesh[2], b[0], b[1], b[2], b[3], b[4], b[5], b[6],
+        b[7], b[8], ef, scale, out);
+    return cudaGetLastError();
+}
+
 }  // namespace rp

@@ -182,6 +182,8 @@ cudaError_t launch_head_row(rp_ctx* c, int k0, int nkb, const double qhat[3], bo
                             cudaStream_t st);
 // peak probes: out[0] FP64 FMA, out[1] FP64 mma.sync, out[2] bf16 tcgen05 (TFLOP/s); an rp_status
 int probe_peaks(double* out, int num_sms, cudaStream_t st);
+// plasma tensor of Eq. plasma added into out[9] (device, zeroed by the caller)
+cudaError_t launch_plasma(rp_ctx* c, double ef, double* out, cudaStream_t st);
 // rotation of a q matrix: out[f][i][j] = in[f][perm[i]][perm[j]]
 cudaError_t launch_rotate(const double2* in, const int* perm, int n, int nf, double2* out, int num_sms,
                           cudaStream_t st);
