@@ -512,6 +512,12 @@ def main():
             "traffic": traffic, "traffic_note": traffic_note, "launches_per_step": nlaunch,
             "ms_per_launch": float(stage_ms[3]) / max(1, int(launches[3])), "tile_bn": tile,
             "algorithmic_flop_per_launch": F_rank / max(1, nlaunch), "peak_source": peak_note}
+    # the sustained peak was measured at its own median SM clock: the fraction at this run's clock too
+    peak_mhz = (pk.get("clocks_under_load") or {}).get("sm_mhz_median")
+    if achieved and peak_mhz and clk.get("sm_mhz"):
+        roof["frac_at_run_clock"] = achieved / (peak * clk["sm_mhz"] / peak_mhz)
+        roof["clock_note"] = (f"peak scaled from its measured median {peak_mhz:.0f} MHz to this run's median "
+                              f"{clk['sm_mhz']:.0f} MHz")
 
     res = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

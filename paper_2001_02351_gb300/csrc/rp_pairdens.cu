@@ -657,7 +657,7 @@ static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int 
 
 // half-widths of the symmetric residue windows the FP32 plane kernel is built for, per plane
 // length 16, 24, 32 (ascending; the plan takes the narrowest that holds the sphere)
-static constexpr int kZyWin[3][4] = {{2, 3, 5, 7}, {3, 5, 7, 11}, {5, 7, 11, 15}};
+static constexpr int kZyWin[3][5] = {{2, 3, 4, 5, 7}, {3, 5, 6, 7, 11}, {5, 7, 8, 11, 15}};
 
 int zy_window(int n, int m) {
     const int i = n == 16 ? 0 : n == 24 ? 1 : n == 32 ? 2 : -1;
@@ -675,6 +675,7 @@ static bool launch_zy_win(int w, const float2* u, int nkb, int nband, int nocc, 
     if (w == kZyWin[i][1]) return launch_zy_n<float2, N, kZyWin[i][1]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
     if (w == kZyWin[i][2]) return launch_zy_n<float2, N, kZyWin[i][2]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
     if (w == kZyWin[i][3]) return launch_zy_n<float2, N, kZyWin[i][3]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
+    if (w == kZyWin[i][4]) return launch_zy_n<float2, N, kZyWin[i][4]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
     return false;
 }
 
@@ -686,6 +687,7 @@ static bool launch_x_win_n(int w, const float2* T2, long long npair, const int* 
     if (w == kZyWin[i][1]) return launch_x_w_n<N, kZyWin[i][1], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
     if (w == kZyWin[i][2]) return launch_x_w_n<N, kZyWin[i][2], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
     if (w == kZyWin[i][3]) return launch_x_w_n<N, kZyWin[i][3], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
+    if (w == kZyWin[i][4]) return launch_x_w_n<N, kZyWin[i][4], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
     return false;
 }
 

@@ -82,18 +82,19 @@ def test_pair_density_on_a_smaller_exact_grid(name, fft):
 
 
 # wide epsilon spheres (E_cut^eps just below E_cut^psi): on the 24-point grid the sphere reaches 6
-# (window of half-width 7), on the 32-point grid it reaches 8 (half-width 11, a window of 529
-# points that the x read-out takes in passes of 256)
+# (window of half-width 6), on the 32-point grid it reaches 8 (half-width 8, 289 points, taken in
+# passes of 256 by the x read-out) and 10 (half-width 11, 529 points)
 WIDE = {
     "w24": ("small", dict(npw=700, ng=600, fft=(32, 32, 32)), 6),
     "w32": ("micro", dict(kmesh=(2, 2, 2), npw=1600, ng=1400, fft=(48, 48, 48)), 8),
+    "w32b": ("micro", dict(kmesh=(2, 2, 2), npw=3000, ng=2600, fft=(48, 48, 48)), 10),
 }
 
 
 @pytest.mark.parametrize("case", sorted(WIDE))
 def test_wide_sphere_window(case):
     """Pair densities and the split-tier chi0 on wide epsilon spheres: the FP32 pair kernels take
-    the windows of half-width 7 (24-point grid) and 11 (32-point grid).  chi0 of the split tier
+    the windows of half-width 6 (24-point grid), 8 and 11 (32-point grid).  chi0 of the split tier
     against the oracle, and the FP64 pair densities (residue masks) of two k points."""
     from dataclasses import replace
     base, kw, reach = WIDE[case]
