@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(DY_THREADS) k_dyson(const double2* __restrict_
 }
 
 
-// Cooperative form: P CTAs per frequency (grid = nf * P, all resident), the columns of each
+// Cooperative form: P CTAs per frequency (grid = frequencies of the launch * P, all resident; the
+// launcher groups frequencies so that a launch's matrices stay within L2), the columns of each
 // frequency's matrix split among its P CTAs.  Per pivot j every CTA finds the same pivot row
 // (identical scan of column j), copies column j and the pivot row into shared memory, then after a
 // grid-wide sync applies the interchange and the elimination to its own columns; a second sync
@@ -265,16 +266,26 @@ cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, d
             cudaFuncSetAttribute(k_dyson_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dyson_coop, DC_THREADS, smem) == cudaSuccess &&
             per_sm > 0) {
-            const int P = std::min(std::max(1, ng / 32), (per_sm * nsm) / nf);
+            // frequencies per launch: as many as keep their matrices within ~96 MB of L2, since every
+            // pivot step updates the whole of each matrix (rank one); the columns of a matrix are
+            // split over P CTAs of at least 16 columns
+            const size_t mat = (size_t)ng * ng * sizeof(double2);
+            const int g = (int)std::max<size_t>(1, std::min<size_t>((size_t)nf, ((size_t)96 << 20) / mat));
+            const int P = std::min(std::max(1, ng / 16), (per_sm * nsm) / g);
             if (P >= 2) {
-                int P_ = P, n_ = ng;
-                const double2* chi_ = chi;
-                const double* vs_ = vs;
-                double2* W_ = W;
-                int* err_ = err_flag;
-                void* args[] = {(void*)&chi_, (void*)&vs_, (void*)&n_, (void*)&P_, (void*)&W_, (void*)&err_};
-                cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_dyson_coop, dim3(nf * P), dim3(DC_THREADS),
-                                                            args, smem, st);
+                cudaError_t e = cudaSuccess;
+                for (int f0 = 0; f0 < nf && e == cudaSuccess; f0 += g) {
+                    const int fg = std::min(g, nf - f0);
+                    int P_ = P, n_ = ng;
+                    const double2* chi_ = chi + (size_t)f0 * ng * ng;
+                    const double* vs_ = vs;
+                    double2* W_ = W + (size_t)f0 * ng * ng;
+                    int* err_ = err_flag;
+                    void* args[] = {(void*)&chi_, (void*)&vs_, (void*)&n_, (void*)&P_, (void*)&W_, (void*)&err_};
+                    e = cudaLaunchCooperativeKernel((const void*)k_dyson_coop, dim3(fg * P), dim3(DC_THREADS), args, smem,
+                                                    st);
+                    if (e != cudaSuccess && f0 > 0) return e;     // a group already ran: report, no fallback
+                }
                 if (e == cudaSuccess) return cudaSuccess;
                 cudaGetLastError();
             }
