@@ -625,8 +625,7 @@ static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, lon
     const size_t sb = (size_t)ng * tc_kp2(K) * 2;
     int s;
     if ((s = ensure(c, c->s_hi, sb)) || (s = ensure(c, c->s_lo, sb)) ||
-        (s = ensure(c, c->s_w32, (size_t)tc_wrows(nfreq) * (tc_kp2(K) / 2) * sizeof(float2))) ||
-        (s = ensure(c, c->s_stage, tc_stage_bytes(c->num_sms))))
+        (s = ensure(c, c->s_w32, (size_t)tc_wrows(nfreq) * (tc_kp2(K) / 2) * sizeof(float2))))
         return s;
     prof_begin(c, 5, st);
     e = launch_split_bf16(M, m32, ldm, col0m, K, ng, c->s_hi.p, c->s_lo.p, st);
@@ -635,7 +634,7 @@ static int contract_block(rp_ctx* c, int precision, const void* M, bool m32, lon
     if (e == cudaSuccess) {
         prof_begin(c, 3, st);
         e = launch_contract_bf16x3_core(c->s_hi.p, c->s_lo.p, K, ng, nfreq, c->s_w32.p, chi, (int*)c->d_err.p + 1,
-                                        c->num_sms, c->wait_ns, st, tile_for(c, ng), (float*)c->s_stage.p);
+                                        c->num_sms, c->wait_ns, st, tile_for(c, ng));
         prof_end(c, 3, st, 1);
     }
     return e == cudaSuccess ? RP_OK : cuda_fail(c, e, "bf16x3 contraction");
@@ -802,8 +801,7 @@ int rp_tune_contraction(rp_ctx* c, int ng, long long K, int nfreq, int* bn_out, 
     int s;
     if ((s = ensure(c, c->s_hi, (size_t)ng * kp2 * 2)) || (s = ensure(c, c->s_lo, (size_t)ng * kp2 * 2)) ||
         (s = ensure(c, c->s_w32, (size_t)tc_wrows(nfreq) * (kp2 / 2) * sizeof(float2))) ||
-        (s = ensure(c, c->s_chi, (size_t)nfreq * ng * ng * sizeof(double2))) ||
-        (s = ensure(c, c->s_stage, tc_stage_bytes(c->num_sms))))
+        (s = ensure(c, c->s_chi, (size_t)nfreq * ng * ng * sizeof(double2))))
         return s;
     cudaError_t e = launch_fill_tune_operands(c->s_hi.p, c->s_lo.p, (long long)ng * kp2, c->s_w32.p,
                                               (long long)tc_wrows(nfreq) * (kp2 / 2), st);
@@ -821,8 +819,7 @@ int rp_tune_contraction(rp_ctx* c, int ng, long long K, int nfreq, int* bn_out, 
             e = cudaEventRecord(ev[0], st);
             if (e == cudaSuccess)
                 e = launch_contract_bf16x3_core(c->s_hi.p, c->s_lo.p, K, ng, nfreq, c->s_w32.p, (double2*)c->s_chi.p,
-                                                (int*)c->d_err.p + 1, c->num_sms, c->wait_ns, st, cand[i],
-                                                (float*)c->s_stage.p);
+                                                (int*)c->d_err.p + 1, c->num_sms, c->wait_ns, st, cand[i]);
             if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
             if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
@@ -1288,7 +1285,7 @@ void rp_destroy(rp_ctx* c) {
                       &c->plan.d_einv[0], &c->plan.d_einv[1], &c->plan.d_einv[2], &c->plan.d_einv32[0],
                       &c->plan.d_einv32[1], &c->plan.d_einv32[2], &c->d_err, &c->s_box, &c->s_u1, &c->s_u2,
                       &c->s_u, &c->s_p, &c->s_t1, &c->s_t2, &c->s_m, &c->s_w, &c->s_chi, &c->s_io1, &c->s_io2,
-                      &c->s_io3, &c->s_hi, &c->s_lo, &c->s_w32, &c->s_stage, &c->s_queue, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
+                      &c->s_io3, &c->s_hi, &c->s_lo, &c->s_w32, &c->s_queue, &c->plan.d_gpos, &c->plan.d_kp, &c->plan.d_g0, &c->plan.d_vs,
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
                       &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_zmap, &c->plan.d_ymap,
                       &c->plan.d_gpos_r, &c->plan.d_gpos_w, &c->plan.d_colg, &c->d_wcoef, &c->s_wm, &c->s_wb,

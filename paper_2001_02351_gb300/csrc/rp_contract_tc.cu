@@ -189,7 +189,6 @@ struct TcArgs {
     double2* chi;
     int* err;
     unsigned long long wait_ns;   // limit of the pipeline's waits (the teardown drains use TC_WAIT_NS)
-    float* stage;                 // per-CTA staging of the accumulators, [grid][2][BN][128], or NULL
 };
 
 // tcgen05.ld of 32 or 16 consecutive accumulator columns of this warp's 32 lanes
@@ -482,33 +481,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ++cj[t];
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * 256);
-                if (args.stage) {
-                    // staged: the accumulator goes to this CTA's slice of the staging buffer with plain
-                    // coalesced stores ([col][lane of the 128]), the accumulator is released, and the FP64
-                    // additions into chi run from the (L2-resident) copy while the next job multiplies
-                    float* stg = args.stage + ((size_t)blockIdx.x * 2 + t) * BN * 128 + (threadIdx.x - 320);
-#pragma unroll 1
-                    for (int ch = 0; ch < NCH; ++ch) {
-                        uint32_t v[32];
-                        tmem_ld32(src + (uint32_t)(ch * 32), v);
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) stg[(size_t)(ch * 32 + j) * 128] = __uint_as_float(v[j]);
-                    }
-                    if constexpr (REM) {
-                        uint32_t v[16];
-                        tmem_ld16(src + (uint32_t)(NCH * 32), v);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) stg[(size_t)(NCH * 32 + j) * 128] = __uint_as_float(v[j]);
-                    }
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    mbar_arrive(acce(t));
-                    if (live) {
-#pragma unroll 4
-                        for (int col = gmin; col < gmax; ++col)
-                            atomicAdd(out + (size_t)col * ldo, (double)stg[(size_t)col * 128]);
-                    }
-                    continue;
-                }
 #pragma unroll 1
                 for (int ch = 0; ch < NCH; ++ch) {
                     uint32_t v[32];
@@ -651,7 +623,7 @@ cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, 
                                    int num_sms, cudaStream_t st) {
     cudaError_t e = launch_weights32(K, w, ldw, col0, nf, w32, st);
     if (e != cudaSuccess) return e;
-    return launch_contract_bf16x3_core(hi, lo, K, ng, nf, w32, chi, err, num_sms, TC_WAIT_NS, st, 0, nullptr);
+    return launch_contract_bf16x3_core(hi, lo, K, ng, nf, w32, chi, err, num_sms, TC_WAIT_NS, st, 0);
 }
 
 // tile widths the kernel is built for
@@ -715,11 +687,9 @@ static cudaError_t launch_bn(const CUtensorMap& mraw_hi, const CUtensorMap& mraw
     return cudaGetLastError();
 }
 
-size_t tc_stage_bytes(int num_sms) { return (size_t)num_sms * 2 * 256 * 128 * sizeof(float); }
-
 cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long long K, int ng, int nf,
                                         const void* w32, double2* chi, int* err, int num_sms,
-                                        unsigned long long wait_ns, cudaStream_t st, int bn, float* stage) {
+                                        unsigned long long wait_ns, cudaStream_t st, int bn) {
     if (bn <= 0) bn = tc_pick_bn(ng);
     if (!tc_bn_supported(bn)) return cudaErrorInvalidValue;
     const long long kp2 = tc_kp2(K);
@@ -738,7 +708,6 @@ cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long lon
     a.nwin = (a.nst + TC_FLUSH_STAGES - 1) / TC_FLUSH_STAGES;
     a.chi = chi; a.err = err;
     a.wait_ns = wait_ns;
-    a.stage = stage;
     const long long njobs = (long long)a.nfq * a.nblk * a.mt * a.nwin;
     if (njobs > 0x7fffffffLL) return cudaErrorInvalidValue;
     const int grid = njobs < num_sms ? (int)njobs : num_sms;

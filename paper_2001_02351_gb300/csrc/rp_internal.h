@@ -88,7 +88,6 @@ struct rp_ctx {
     rp::DevBuf s_box, s_u1, s_u2, s_u, s_p, s_t1, s_t2, s_m, s_w, s_chi, s_io1, s_io2, s_io3;
     rp::DevBuf s_hi, s_lo;            // bf16 hi/lo split of a block of pair densities
     rp::DevBuf s_w32;                 // complex float weights of that block
-    rp::DevBuf s_stage;               // staging of the contraction's accumulators (per CTA)
     rp::DevBuf s_queue;               // FP64 work list of the FP32 weight pass (count + items)
     // Wannier functions of the interaction step: coefficients [nk][2 nw][npw_max] (each orbital twice,
     // a band view with nocc = nemp = nw), and the scratch of rp_interaction
@@ -156,12 +155,10 @@ cudaError_t launch_contract_bf16x3(const void* hi, const void* lo, long long K, 
 cudaError_t launch_weights32(long long K, const double2* w, long long ldw, long long col0, int nf, void* w32,
                              cudaStream_t st);
 // (wait_ns: limit of the kernel's pipeline waits; a wait that gives up sets *err and the kernel returns;
-// bn: raw rows per tile, one of tc_bn_supported, or <= 0 for tc_pick_bn(ng);
-// stage: tc_stage_bytes(num_sms) of scratch for the staged accumulator flush, or NULL for direct atomics)
-size_t tc_stage_bytes(int num_sms);
+// bn: raw rows per tile, one of tc_bn_supported, or <= 0 for tc_pick_bn(ng))
 cudaError_t launch_contract_bf16x3_core(const void* hi, const void* lo, long long K, int ng, int nf,
                                         const void* w32, double2* chi, int* err, int num_sms,
-                                        unsigned long long wait_ns, cudaStream_t st, int bn, float* stage);
+                                        unsigned long long wait_ns, cudaStream_t st, int bn);
 bool tc_bn_supported(int bn);
 int tc_pick_bn(int ng);
 int tc_bn_candidates(int* out);     // the supported tile widths (returns their count, out may be NULL)

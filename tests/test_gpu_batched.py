@@ -64,7 +64,8 @@ def test_sampled_parity_on_six_q(batched, picks):
         cols = np.concatenate([np.arange(k * npk, (k + 1) * npk) for k in (7, 150)])
         assert np.abs(w[:, cols] - wref).max() <= 1e-11 * np.abs(wref).max()
         ctx.close()
-    assert min(ngs) >= 300 and max(ngs) <= 900 and len(set(ngs)) > 3
+    # sphere sizes drawn from 300..900 and placed at the nearest gap of |q+G|^2 (a few G either way)
+    assert min(ngs) >= 280 and max(ngs) <= 950 and len(set(ngs)) > 3
 
 
 def test_batched_build_and_dyson_against_single_q(batched, picks):
