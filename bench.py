@@ -37,7 +37,7 @@ CONTRACT_SRC = os.path.join(ROOT, "paper_2001_02351_gb300", "csrc", "rp_contract
 # contraction kernel at each workload's launch shape, from one ncu capture of
 # `python bench.py --kernel contraction --workload <w>`, valid for the kernel source whose
 # sha256 starts with the given prefix (null traffic otherwise).
-TRAFFIC = {}
+TRAFFIC = {("precision", "bf16x3"): (43_461_647_000, "27be8a6ecd3bb6e2")}
 
 
 def measured_traffic(workload, precision):
@@ -171,8 +171,10 @@ def subset_k(nk, n=4, seed=2001_02351):
 
 
 def sample_emp(wl, pairs=8192):
-    """Empty bands of a bounded oracle sample: the lowest ones, about `pairs` pairs per k point."""
-    return int(min(wl.nemp, max(8, pairs // wl.nocc)))
+    """Empty bands of a bounded oracle sample: the lowest ones, about `pairs` pairs per k point on a
+    48^3 grid (fewer on larger grids: the oracle's cost per pair grows with the grid)."""
+    scaled = pairs * 48 ** 3 // int(np.prod(wl.fft))
+    return int(min(wl.nemp, max(8, scaled // wl.nocc)))
 
 
 def oracle_sample(wl, k_list, f_idx, nemp=None):
@@ -532,7 +534,14 @@ def main():
            "stages_ms_per_step": {n: stage_ms[i] / args.steps for i, n in enumerate(STAGES)},
            "gpu_launches": int(launches.sum()), "roofline": roof, "clocks": clk}
 
-    if prec != rp.RP_FP64_NATIVE and not args.no_fp64 and rank == 0:
+    # the native-FP64 reference needs the FP64 plane kernels (residue masks of at most 32 points per
+    # axis); on larger grids its pair stage takes the generic line passes, far too slow at these sizes
+    fp64_ref = ctx.rp_transform_grid(q)[0][0] <= 32
+    if prec != rp.RP_FP64_NATIVE and not args.no_fp64 and rank == 0 and not fp64_ref:
+        res["fp64_reference"] = {"skipped": "transform grid above 32 points: the FP64 pair stage has no plane "
+                                            "kernel there (the split tier is checked against the oracle in "
+                                            "tests/test_gpu_large.py)"}
+    if prec != rp.RP_FP64_NATIVE and not args.no_fp64 and rank == 0 and fp64_ref:
         # native FP64 and the timed tier on the same inputs: the sum over four seeded k points
         # (full-mesh weights) at three frequencies; W errors from the Dyson step applied to each
         # subset chi0 scaled by N_k / 4 (the subset's estimate of the whole sum, of the right size

@@ -106,6 +106,14 @@ int rp_load_bands(rp_ctx* ctx, int nk, int nband, int nocc, const int* npw, int 
 int rp_sphere_size(rp_ctx* ctx, const double q_frac[3], int* ng, int* n_tail,
                    int* miller_out, int* tail_out);
 
+/* rp_transform_grid -- the transform grid the pair densities of q run on (bands loaded, else
+ *   RP_ERR_STATE): n_out int[3] (host).  It is the smallest grid with dedicated kernels (16, 24, 32
+ *   or 48 points per axis) on which the transforms give the convolution of Eq. ism exactly
+ *   (N >= 2 mu + 2 + Lg, mu the bands' largest |Miller| component, Lg the sphere's), when that is
+ *   smaller than the cubic grid of rp_setup_cell; else the grid of rp_setup_cell.  window_out:
+ *   NULL or the half-width of the residue window of the split tiers' plane kernels (0: none). */
+int rp_transform_grid(rp_ctx* ctx, const double q_frac[3], int* n_out, int* window_out);
+
 /* rp_sphere_size_at -- rp_sphere_size for a given epsilon cut-off ecut_eps_ha (0 < ecut_eps_ha
  *   <= Ecut_psi, else RP_ERR_ARG) instead of the context's: the sizes of one member of a batch
  *   with per-q cut-offs (rp_build_chi0_batched). */
@@ -296,6 +304,12 @@ int rp_set_contraction_tile(rp_ctx* ctx, int ng, int bn);
  *   with CUDA events after a warm-up launch on the current device.  Synchronous.  RP_ERR_TIMEOUT if
  *   the tcgen05 probe's bounded wait gave up. */
 int rp_probe_peaks(double* out);
+
+/* rp_set_pair_budget -- bytes of device scratch the pair-density stage may give to the plane sums of
+ *   its pair kernels (default 16 GiB).  The k points are taken in sub-blocks whose plane sums fit;
+ *   when one k point's do not, its empty bands are taken in chunks that fit (the pair densities are
+ *   the same either way).  bytes >= 1, else RP_ERR_ARG. */
+int rp_set_pair_budget(rp_ctx* ctx, long long bytes);
 
 /* rp_set_wait_limit -- testing aid with no counterpart in the paper: the time after which a
  *   bounded device wait of the context's RP_BF16X3 contraction kernel gives up (default 2e9 ns).

@@ -26,10 +26,10 @@ _STATUS = {0: "RP_OK", -1: "RP_ERR_ARG", -2: "RP_ERR_STATE", -3: "RP_ERR_OOM", -
 EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density", "rp_tetra_weights",
            "rp_contract_chi0", "rp_build_chi0", "rp_solve_w", "rp_check_numeric", "rp_profile_enable",
            "rp_profile_read", "rp_last_error", "rp_destroy", "rp_contract_chi0_static", "rp_sphere_size_at",
-           "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_contract_chi0_static_status",
+           "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_set_pair_budget", "rp_contract_chi0_static_status",
            "rp_build_chi0_kset", "rp_tune_contraction", "rp_set_contraction_tile",
            "rp_load_wannier", "rp_interaction", "rp_build_chi0_q0", "rp_solve_w_q0", "rp_optics",
-           "rp_rotate_q", "rp_probe_peaks", "rp_plasma"]
+           "rp_rotate_q", "rp_probe_peaks", "rp_plasma", "rp_transform_grid"]
 
 
 class RPError(RuntimeError):
@@ -54,6 +54,7 @@ def library():
         "rp_setup_cell": (I, [P, P, P, D, D, ctypes.POINTER(P)]),
         "rp_load_bands": (I, [P, I, I, I, P, I, P, P, P, P]),
         "rp_sphere_size": (I, [P, P, ctypes.POINTER(I), ctypes.POINTER(I), P, P]),
+        "rp_transform_grid": (I, [P, P, P, ctypes.POINTER(I)]),
         "rp_pair_density": (I, [P, P, I, I, P, I, P]),
         "rp_tetra_weights": (I, [P, P, I, I, I, P, D, D, D, I, P, I, P]),
         "rp_contract_chi0": (I, [P, I, LL, I, P, P, I, P, I, P]),
@@ -69,6 +70,7 @@ def library():
         "rp_build_chi0_batched": (I, [P, I, P, P, I, I, I, P, D, D, D, I, P, I, P]),
         "rp_solve_w_batched": (I, [P, I, P, P, I, P, P, P, I, P]),
         "rp_set_wait_limit": (I, [P, LL]),
+        "rp_set_pair_budget": (I, [P, LL]),
         "rp_build_chi0_kset": (I, [P, P, I, P, I, I, I, P, D, D, D, I, P, I, P]),
         "rp_tune_contraction": (I, [P, I, LL, I, ctypes.POINTER(I), P]),
         "rp_set_contraction_tile": (I, [P, I, I]),
@@ -172,6 +174,14 @@ class Context:
         return g, t[:nt.value]
 
     rp_sphere_size_at = rp_sphere_size
+
+    def rp_transform_grid(self, q):
+        """((N1, N2, N3), window half-width) of the pair transforms of q."""
+        q_, pq = _host(q, np.float64)
+        n = np.zeros(3, dtype=np.int32)
+        w = ctypes.c_int()
+        self._check(self._lib.rp_transform_grid(self._h, pq, n.ctypes.data_as(ctypes.c_void_p), ctypes.byref(w)))
+        return tuple(int(x) for x in n), w.value
 
     def _out(self, out, shape, dtype=np.complex128):
         if out is None:
@@ -449,6 +459,9 @@ class Context:
 
     def rp_set_wait_limit(self, limit_ns):
         self._check(self._lib.rp_set_wait_limit(self._h, int(limit_ns)))
+
+    def rp_set_pair_budget(self, nbytes):
+        self._check(self._lib.rp_set_pair_budget(self._h, int(nbytes)))
 
     def rp_profile_enable(self, enable=True):
         self._check(self._lib.rp_profile_enable(self._h, 1 if enable else 0))

@@ -176,7 +176,7 @@ int plan_q_cut(rp_ctx* c, const double q[3], double ecut_eps, bool exact) {
             for (int v : P.setv[a]) lg = std::max(lg, std::abs(v));
             need = std::max(need, 2 * c->mu[a] + 2 + lg);
         }
-        for (int cand : {16, 24, 32})
+        for (int cand : {16, 24, 32, 48})
             if (cand >= need && cand < c->fft[0]) {
                 for (int a = 0; a < 3; ++a) P.nfft[a] = cand;
                 break;
@@ -472,6 +472,15 @@ static int check_ready_cut(rp_ctx* c, const double q[3], double ecut_eps) {
 }
 static int check_ready(rp_ctx* c, const double q[3]) { return check_ready_cut(c, q, c ? c->ecut_eps : 0.0); }
 
+int rp_transform_grid(rp_ctx* c, const double q[3], int* n_out, int* window_out) {
+    int s = check_ready(c, q);
+    if (s) return s;
+    if (!n_out) return fail(c, RP_ERR_ARG, "n_out is NULL");
+    for (int a = 0; a < 3; ++a) n_out[a] = c->plan.nfft[a];
+    if (window_out) *window_out = c->plan.zyw;
+    return RP_OK;
+}
+
 static int finish(rp_ctx* c, cudaStream_t st, int on_device) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
@@ -490,12 +499,13 @@ static int pair_density_device(rp_ctx* c, int k0, int k1, void* M, bool fp32, lo
                                cudaStream_t st) {
     const size_t per_k = (size_t)c->nband * c->plan.nr * (fp32 ? sizeof(float2) : sizeof(double2));
     // plane sums of one k point in the windowed (FP32) or residue-set (FP64) layout of the plane-wise
-    // pair kernels: the sub-block keeps them within those kernels' 16 GB budget
+    // pair kernels: the sub-block keeps them within those kernels' budget (one k point at least;
+    // its empty bands are then taken in chunks)
     const QPlan& P = c->plan;
     const int W = fp32 ? P.zyw : 0;
     const size_t wyz = W > 0 ? (size_t)(2 * W + 1) * (2 * W + 1) : (size_t)P.nset[1] * P.nset[2];
     const size_t t2_k = (size_t)c->nemp * c->nocc * P.nfft[0] * wyz * (fp32 ? sizeof(float2) : sizeof(double2));
-    size_t kb_t2 = std::max<size_t>(1, ((size_t)16 << 30) / std::max<size_t>(1, t2_k));
+    size_t kb_t2 = std::max<size_t>(1, c->pair_budget / std::max<size_t>(1, t2_k));
     if (!fp32) {
         // the FP64 tier's fused path keeps z-transformed planes of every pair within 12 GB
         const size_t t1_k = (size_t)c->nemp * c->nocc * P.nfft[0] * P.nfft[1] * P.nset[2] * sizeof(double2);
@@ -839,6 +849,13 @@ int rp_tune_contraction(rp_ctx* c, int ng, long long K, int nfreq, int* bn_out, 
     return RP_OK;
 }
 
+int rp_set_pair_budget(rp_ctx* c, long long bytes) {
+    if (!c) return RP_ERR_ARG;
+    if (bytes < 1) return fail(c, RP_ERR_ARG, "pair budget must be positive");
+    c->pair_budget = (size_t)bytes;
+    return RP_OK;
+}
+
 int rp_set_wait_limit(rp_ctx* c, long long limit_ns) {
     if (!c) return RP_ERR_ARG;
     if (limit_ns < 0) return fail(c, RP_ERR_ARG, "negative wait limit");
@@ -873,8 +890,9 @@ static int solve_w(rp_ctx* c, const double q[3], double ecut_eps, int nfreq, con
         dchi = (const double2*)c->s_io1.p;
         dW = (double2*)c->s_io2.p;
     }
+    if ((s = ensure(c, c->s_dy, dyson_scratch_bytes(ng, nfreq)))) return s;
     prof_begin(c, 4, st);
-    cudaError_t e = launch_dyson(dchi, (const double*)c->plan.d_vs.p, ng, nfreq, dW, (int*)c->d_err.p, st);
+    cudaError_t e = launch_dyson(dchi, (const double*)c->plan.d_vs.p, ng, nfreq, dW, c->s_dy.p, (int*)c->d_err.p, st);
     prof_end(c, 4, st, 1);
     if (e != cudaSuccess) return cuda_fail(c, e, "Dyson solve");
     if (tail_out && c->plan.ntail > 0) {
@@ -947,8 +965,9 @@ int rp_solve_w_q0(rp_ctx* c, int nfreq, const double* chi0, double* W_out, doubl
         dchi = (const double2*)c->s_io1.p;
         dW = (double2*)c->s_io2.p;
     }
+    if ((s = ensure(c, c->s_dy, dyson_scratch_bytes(n, nfreq)))) return s;
     prof_begin(c, 4, st);
-    e = launch_dyson(dchi, (const double*)c->s_io3.p, n, nfreq, dW, (int*)c->d_err.p, st);
+    e = launch_dyson(dchi, (const double*)c->s_io3.p, n, nfreq, dW, c->s_dy.p, (int*)c->d_err.p, st);
     prof_end(c, 4, st, 1);
     if (e != cudaSuccess) return cuda_fail(c, e, "Dyson solve");
     if (tail_out && c->plan.ntail > 0) {
@@ -1289,7 +1308,7 @@ void rp_destroy(rp_ctx* c) {
                       &c->plan.d_efwd[0], &c->plan.d_efwd[1], &c->plan.d_efwd[2], &c->plan.d_efwd32[0],
                       &c->plan.d_efwd32[1], &c->plan.d_efwd32[2], &c->plan.d_zmap, &c->plan.d_ymap,
                       &c->plan.d_gpos_r, &c->plan.d_gpos_w, &c->plan.d_colg, &c->d_wcoef, &c->s_wm, &c->s_wb,
-                      &c->s_wy, &c->s_wtab, &c->s_wout};
+                      &c->s_wy, &c->s_wtab, &c->s_wout, &c->s_dy};
     for (DevBuf* b : bufs) release(*b);
     for (int i = 0; i < RP_NSTAGE; ++i)
         for (cudaEvent_t e : c->prof_ev[i]) cudaEventDestroy(e);

@@ -267,22 +267,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nst = args.nst;
     int* err = args.err;
     const uint64_t lim = args.wait_ns;
-    // job -> (group of tiles, accumulation window, tile of the group) -> (group of four frequencies,
-    // G' block, G tile).  A group is gridDim.x consecutive tiles and runs all its windows before the
-    // next group starts: the CTAs share each window's raw rows (the group spans every G tile) and
-    // each tile's part of chi is flushed window after window while it is still in L2.  The last
-    // block and tile are moved back to end at ng, so that (for ng >= BN) every box lies inside the
-    // arrays; a block or tile writes only the rows from its own start (nown, mown) on, so rows covered
-    // twice are added once.
+    // job -> (accumulation window, group of four frequencies, G' block, G tile); consecutive jobs
+    // share a window.  The last block and tile are moved back to end at ng, so that (for ng >=
+    // BN) every box lies inside the arrays; a block or tile writes only the rows from its own
+    // start (nown, mown) on, so rows covered twice are added once.
     // tile t of a job in frequency group fq holds frequencies 4 fq + 2 t, + 1: it is live if the first is
     auto live_tile = [&](int fq, int t) { return TC_NF * fq + 2 * t < args.nf; };
-    const int gs = (int)gridDim.x;
     auto job_tile = [&](int job, int& w0, int& w1, int& fq, int& n0, int& m0, int& nown, int& mown) {
-        const int grp = job / (gs * args.nwin);
-        const int gsz = min(gs, ntile - grp * gs);                      // tiles in this group
-        const int gbase = grp * gs * args.nwin;
-        const int jl = job - gbase;                                      // job within the group
-        const int win = jl / gsz, t = grp * gs + jl % gsz;
+        const int win = job / ntile, t = job % ntile;
         fq = t / (args.nblk * args.mt);
         const int r = t % (args.nblk * args.mt);
         nown = (r / args.mt) * TC_GN;

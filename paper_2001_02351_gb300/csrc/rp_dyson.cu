@@ -15,6 +15,33 @@ namespace rp {
 
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
+// a - f r as four fused multiply-adds (the FP64 pipe is the bound: no separate products or sums)
+__device__ __forceinline__ double2 cfms(double2 a, double2 f, double2 r) {
+    a.x = fma(-f.x, r.x, a.x);
+    a.x = fma(f.y, r.y, a.x);
+    a.y = fma(-f.x, r.y, a.y);
+    a.y = fma(-f.y, r.x, a.y);
+    return a;
+}
+
+// largest v (then smallest i) over the CTA; every thread gets the result (two barriers)
+template <int NT>
+__device__ __forceinline__ void block_argmax(double& v, int& i, double* red_v, int* red_i) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, v, off);
+        const int oi = __shfl_down_sync(0xffffffffu, i, off);
+        if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+    }
+    if (lane == 0) { red_v[warp] = v; red_i[warp] = i; }
+    __syncthreads();
+    v = red_v[0];
+    i = red_i[0];
+    for (int q = 1; q < NT / 32; ++q)
+        if (red_v[q] > v || (red_v[q] == v && red_i[q] < i)) { v = red_v[q]; i = red_i[q]; }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(DY_THREADS) k_dyson(const double2* __restrict__ chi, const double* __restrict__ vs,
                                                       int n, double2* __restrict__ Wout, int* err_flag) {
     extern __shared__ unsigned char smem[];
@@ -90,15 +117,15 @@ __global__ void __launch_bounds__(DY_THREADS) k_dyson(const double2* __restrict_
             A[(size_t)j * n + c] = r;
         }
         __syncthreads();
-        for (long long e = tid; e < nn; e += DY_THREADS) {
-            const int i = (int)(e / n), c = (int)(e % n);
-            if (i == j) continue;
-            const double2 fi = colj[i];
-            const double2 r = rowj[c];
-            double2 a = (c == j) ? make_double2(0.0, 0.0) : A[e];
-            a.x -= fi.x * r.x - fi.y * r.y;
-            a.y -= fi.x * r.y + fi.y * r.x;
-            A[e] = a;
+        for (int i = tid / n, c = tid % n; i < n;) {
+            if (i != j) {
+                const double2 fi = colj[i];
+                double2 a = (c == j) ? make_double2(0.0, 0.0) : A[(size_t)i * n + c];
+                A[(size_t)i * n + c] = cfms(a, fi, rowj[c]);
+            }
+            i += DY_THREADS / n;
+            c += DY_THREADS % n;
+            if (c >= n) { c -= n; ++i; }
         }
         __syncthreads();
     }
@@ -127,163 +154,216 @@ __global__ void __launch_bounds__(DY_THREADS) k_dyson(const double2* __restrict_
 }
 
 
-// Cooperative form: P CTAs per frequency (grid = frequencies of the launch * P, all resident; the
-// launcher groups frequencies so that a launch's matrices stay within L2), the columns of each
-// frequency's matrix split among its P CTAs.  Per pivot j every CTA finds the same pivot row
-// (identical scan of column j), copies column j and the pivot row into shared memory, then after a
-// grid-wide sync applies the interchange and the elimination to its own columns; a second sync
-// closes the step.  Row interchanges are undone afterwards as column interchanges, row by row.
-// The grid barriers are shared by all frequencies, so every CTA passes exactly 2 n + 1 of them
-// whatever the data: a frequency that meets a bad pivot keeps passing both barriers of each
-// remaining step and skips only the arithmetic.
+// Cooperative form: P CTAs per frequency (grid = frequencies of the launch * P, all resident), the
+// columns of each matrix split evenly among its P CTAs.  Pivot j is published through global scratch
+// by the CTA that owns column j: in step j - 1 it updates that column first, finds its pivot and
+// writes the column and the pivot row index, then updates the rest of its columns; one grid barrier
+// closes the step.  Every CTA then reads the column (coalesced), applies the interchange and the
+// scaled pivot row to its own columns and eliminates them.  A zero or non-finite pivot is published
+// as -1; the CTAs of that frequency keep passing the barriers (exactly n + 1 for every CTA, whatever
+// the data) and skip the arithmetic.  Afterwards each CTA undoes the interchanges on its own rows as
+// one column gather and scales by v^1/2.
 #define DC_THREADS 512
+#define DC_UNROLL 4
 
 __global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __restrict__ chi,
                                                            const double* __restrict__ vs, int n, int P,
-                                                           double2* __restrict__ Wout, int* err_flag) {
+                                                           double2* __restrict__ Wout,
+                                                           double2* __restrict__ colbuf, int* __restrict__ ibuf,
+                                                           int* err_flag) {
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
     extern __shared__ unsigned char smem[];
-    double2* colj = (double2*)smem;        // column j (rows 0..n-1), after the interchange
-    double2* rowj = colj + n;              // pivot row j (all columns), after the interchange
-    int* perm = (int*)(rowj + n);
+    double2* colj = (double2*)smem;        // column j after the interchange (all rows)
+    double2* rowj = colj + n;              // scaled pivot row on this CTA's columns; a row in the undo
+    int* idx = (int*)(rowj + n);           // column gather of the undo
     __shared__ double red_v[DC_THREADS / 32];
     __shared__ int red_i[DC_THREADS / 32];
-    __shared__ int s_piv, s_bad;
     const int f = blockIdx.x / P, pc = blockIdx.x % P;
     const int c0 = (int)((long long)n * pc / P), c1 = (int)((long long)n * (pc + 1) / P);
+    const int w = c1 - c0;
     const double2* X = chi + (size_t)f * n * n;
     double2* A = Wout + (size_t)f * n * n;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int w = c1 - c0;
+    double2* cb = colbuf + (size_t)f * 2 * n;      // [2][n]: the published column of even / odd steps
+    int* perm = ibuf + (size_t)f * (n + 2);        // [n] pivot rows, then [2] published pivots
+    int* pivb = perm + n;
+    const int tid = threadIdx.x;
+    // element walk over this CTA's n x w block, row-major, without divisions in the loop
+    const int di = DC_THREADS / w, dc = DC_THREADS % w;
     // eps = 1 - v^1/2 chi v^1/2 on this CTA's columns
-    for (long long e = tid; e < (long long)n * w; e += DC_THREADS) {
-        const int i = (int)(e / w), jj = c0 + (int)(e % w);
-        const double sc = vs[i] * vs[jj];
-        const double2 x = X[(size_t)i * n + jj];
-        A[(size_t)i * n + jj] = make_double2((i == jj ? 1.0 : 0.0) - sc * x.x, -sc * x.y);
+    for (int i = tid / w, cc = tid % w; i < n;) {
+        const int c = c0 + cc;
+        const double sc = vs[i] * vs[c];
+        const double2 x = X[(size_t)i * n + c];
+        A[(size_t)i * n + c] = make_double2((i == c ? 1.0 : 0.0) - sc * x.x, -sc * x.y);
+        i += di;
+        cc += dc;
+        if (cc >= w) { cc -= w; ++i; }
     }
-    if (tid == 0) s_bad = 0;
-    grid.sync();
-    for (int j = 0; j < n; ++j) {
-        if (s_bad) {          // read after a barrier: the same value in every thread of the CTA
-            grid.sync();
-            grid.sync();
-            continue;
-        }
+    __syncthreads();
+    if (c0 == 0) {       // owner of column 0 publishes it and its pivot
         double best = -1.0;
-        int bi = j;
-        for (int i = j + tid; i < n; i += DC_THREADS) {
-            const double v = cabs2(A[(size_t)i * n + j]);
+        int bi = 0;
+        for (int i = tid; i < n; i += DC_THREADS) {
+            const double2 a = A[(size_t)i * n];
+            cb[i] = a;
+            const double v = cabs2(a);
             if (v > best || (v == best && i < bi)) { best = v; bi = i; }
         }
-        for (int off = 16; off > 0; off >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, best, off);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
-        __syncthreads();
+        block_argmax<DC_THREADS>(best, bi, red_v, red_i);
         if (tid == 0) {
-            best = red_v[0];
-            bi = red_i[0];
-            for (int q = 1; q < DC_THREADS / 32; ++q)
-                if (red_v[q] > best || (red_v[q] == best && red_i[q] < bi)) { best = red_v[q]; bi = red_i[q]; }
-            s_piv = bi;
-            perm[j] = bi;
-            if (!(best > 0.0) || !isfinite(best)) s_bad = 1;
+            perm[0] = bi;
+            pivb[0] = (best > 0.0 && isfinite(best)) ? bi : -1;
         }
-        __syncthreads();
-        if (s_bad) {          // this frequency's CTAs all see the same pivot; the grid keeps going
-            grid.sync();
-            grid.sync();
-            continue;
-        }
-        const int p = s_piv;
-        for (int i = tid; i < n; i += DC_THREADS) {
-            const int src = (i == j) ? p : (i == p ? j : i);
-            colj[i] = A[(size_t)src * n + j];
-        }
-        for (int c = tid; c < n; c += DC_THREADS) rowj[c] = A[(size_t)p * n + c];
-        __syncthreads();
-        grid.sync();
-        const double2 piv = colj[j];
-        const double d = cabs2(piv);
-        const double2 inv = make_double2(piv.x / d, -piv.y / d);
-        // interchange rows j and p on this CTA's columns
-        if (p != j)
-            for (int c = c0 + tid; c < c1; c += DC_THREADS) A[(size_t)p * n + c] = A[(size_t)j * n + c];
-        __syncthreads();
-        // scaled pivot row on this CTA's columns (position j holds 1/pivot)
-        for (int c = c0 + tid; c < c1; c += DC_THREADS) {
-            const double2 v = (c == j) ? make_double2(1.0, 0.0) : rowj[c];
-            const double2 r = make_double2(v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x);
-            rowj[c] = r;
-            A[(size_t)j * n + c] = r;
-        }
-        __syncthreads();
-        for (long long e = tid; e < (long long)n * w; e += DC_THREADS) {
-            const int i = (int)(e / w), c = c0 + (int)(e % w);
-            if (i == j) continue;
-            const double2 fi = colj[i];
-            const double2 r = rowj[c];
-            double2 a = (c == j) ? make_double2(0.0, 0.0) : A[(size_t)i * n + c];
-            a.x -= fi.x * r.x - fi.y * r.y;
-            a.y -= fi.x * r.y + fi.y * r.x;
-            A[(size_t)i * n + c] = a;
+    }
+    grid.sync();
+    bool bad = false;                      // uniform over the CTA (read from the same published value)
+    for (int j = 0; j < n; ++j) {
+        const int cur = j & 1, nxt = cur ^ 1;
+        if (!bad) bad = __ldcg(&pivb[cur]) < 0;
+        if (!bad) {
+            const int p = __ldcg(&pivb[cur]);
+            for (int i = tid; i < n; i += DC_THREADS) {
+                const int src = (i == j) ? p : (i == p ? j : i);
+                colj[i] = __ldcg(&cb[(size_t)cur * n + src]);
+            }
+            for (int c = c0 + tid; c < c1; c += DC_THREADS) rowj[c] = A[(size_t)p * n + c];
+            __syncthreads();
+            const double2 piv = colj[j];
+            const double d = cabs2(piv);
+            const double2 inv = make_double2(piv.x / d, -piv.y / d);
+            // interchange rows j and p on this CTA's columns; row j becomes the scaled pivot row
+            // (position j holds 1 / pivot)
+            for (int c = c0 + tid; c < c1; c += DC_THREADS) {
+                const double2 v = (c == j) ? make_double2(1.0, 0.0) : rowj[c];
+                const double2 r = make_double2(v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x);
+                if (p != j) A[(size_t)p * n + c] = A[(size_t)j * n + c];
+                A[(size_t)j * n + c] = r;
+                rowj[c] = r;
+            }
+            __syncthreads();
+            const int jn = j + 1;
+            const bool owner = jn < n && jn >= c0 && jn < c1;
+            if (owner) {        // column j + 1 first: eliminate, publish, find its pivot
+                const double2 r = rowj[jn];
+                double best = -1.0;
+                int bi = jn;
+                for (int i = tid; i < n; i += DC_THREADS) {
+                    double2 a;
+                    if (i == j) {
+                        a = r;
+                    } else {
+                        a = cfms(A[(size_t)i * n + jn], colj[i], r);
+                        A[(size_t)i * n + jn] = a;
+                    }
+                    cb[(size_t)nxt * n + i] = a;
+                    if (i >= jn) {
+                        const double v = cabs2(a);
+                        if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+                    }
+                }
+                block_argmax<DC_THREADS>(best, bi, red_v, red_i);
+                if (tid == 0) {
+                    perm[jn] = bi;
+                    pivb[nxt] = (best > 0.0 && isfinite(best)) ? bi : -1;
+                }
+            }
+            // the rest of this CTA's block, DC_UNROLL elements per thread in flight (their loads
+            // issued before their arithmetic: the block streams from L2 or DRAM every step)
+            for (int i = tid / w, cc = tid % w; i < n;) {
+                int ei[DC_UNROLL], ec[DC_UNROLL];
+                double2 a[DC_UNROLL];
+#pragma unroll
+                for (int u = 0; u < DC_UNROLL; ++u) {
+                    const int c = c0 + cc;
+                    const bool act = i < n && i != j && c != jn;
+                    ei[u] = act ? i : -1;
+                    ec[u] = c;
+                    a[u] = (act && c != j) ? A[(size_t)i * n + c] : make_double2(0.0, 0.0);
+                    i += di;
+                    cc += dc;
+                    if (cc >= w) { cc -= w; ++i; }
+                }
+#pragma unroll
+                for (int u = 0; u < DC_UNROLL; ++u)
+                    if (ei[u] >= 0) A[(size_t)ei[u] * n + ec[u]] = cfms(a[u], colj[ei[u]], rowj[ec[u]]);
+            }
         }
         grid.sync();
     }
-    if (s_bad) {
+    if (bad) {
         if (tid == 0 && pc == 0) atomicOr(err_flag, 1);
         return;
     }
-    // undo the interchanges as column interchanges and scale by v^1/2, on this CTA's rows
+    // the row interchanges undone as column interchanges, last first, composed into one gather:
+    // out[c] = row[idx[c]]
+    int* pv = (int*)colj;
+    for (int i = tid; i < n; i += DC_THREADS) {
+        pv[i] = __ldcg(&perm[i]);
+        idx[i] = i;
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int jj = n - 1; jj >= 0; --jj) {
+            const int q = pv[jj];
+            const int t = idx[jj];
+            idx[jj] = idx[q];
+            idx[q] = t;
+        }
+    __syncthreads();
     const int r0 = (int)((long long)n * pc / P), r1 = (int)((long long)n * (pc + 1) / P);
-    for (int i = r0 + warp; i < r1; i += DC_THREADS / 32) {
+    for (int i = r0; i < r1; ++i) {
         double2* row = A + (size_t)i * n;
-        if (lane == 0)
-            for (int jj = n - 1; jj >= 0; --jj) {
-                const int q = perm[jj];
-                if (q != jj) { const double2 t = row[jj]; row[jj] = row[q]; row[q] = t; }
-            }
-        __syncwarp();
-        for (int c = lane; c < n; c += 32) {
-            const double sc = vs[i] * vs[c];
-            const double2 a = row[c];
+        for (int c = tid; c < n; c += DC_THREADS) rowj[c] = __ldcg(&row[c]);
+        __syncthreads();
+        const double vi = vs[i];
+        for (int c = tid; c < n; c += DC_THREADS) {
+            const double sc = vi * vs[c];
+            const double2 a = rowj[idx[c]];
             row[c] = make_double2(a.x * sc, a.y * sc);
         }
+        __syncthreads();
     }
 }
 
-cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W, int* err_flag,
-                         cudaStream_t st) {
+size_t dyson_scratch_bytes(int ng, int nf) {
+    const size_t cols = (size_t)nf * 2 * ng * sizeof(double2);
+    return ((cols + 255) / 256) * 256 + (size_t)nf * (ng + 2) * sizeof(int);
+}
+
+cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W, void* scratch,
+                         int* err_flag, cudaStream_t st) {
     const size_t smem = (size_t)ng * (2 * sizeof(double2) + sizeof(int));
     {   // cooperative form over the whole GPU when it fits
         int dev = 0, nsm = 0, per_sm = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
+        if (scratch && cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
             cudaFuncSetAttribute(k_dyson_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dyson_coop, DC_THREADS, smem) == cudaSuccess &&
             per_sm > 0) {
-            // frequencies per launch: as many as keep their matrices within ~96 MB of L2, since every
-            // pivot step updates the whole of each matrix (rank one); the columns of a matrix are
-            // split over P CTAs of at least 16 columns
-            const size_t mat = (size_t)ng * ng * sizeof(double2);
-            const int g = (int)std::max<size_t>(1, std::min<size_t>((size_t)nf, ((size_t)96 << 20) / mat));
-            const int P = std::min(std::max(1, ng / 16), (per_sm * nsm) / g);
-            if (P >= 2) {
+            // every frequency in one launch when each can have two CTAs; CTAs as many as are resident,
+            // so that every SM holds (nearly) the same number of equal column blocks (the FP64 pipe
+            // is the bound), and at least 8 columns per CTA
+            const int slots = per_sm * nsm;
+            const int g = std::max(1, std::min(nf, slots / 2));
+            const int pmax = ng / 8;
+            if (pmax >= 2) {
+                double2* cb_all = (double2*)scratch;
+                int* ib_all = (int*)((char*)scratch + (((size_t)nf * 2 * ng * sizeof(double2) + 255) / 256) * 256);
                 cudaError_t e = cudaSuccess;
                 for (int f0 = 0; f0 < nf && e == cudaSuccess; f0 += g) {
                     const int fg = std::min(g, nf - f0);
-                    int P_ = P, n_ = ng;
+                    int P_ = std::min(pmax, slots / fg), n_ = ng;
                     const double2* chi_ = chi + (size_t)f0 * ng * ng;
                     const double* vs_ = vs;
                     double2* W_ = W + (size_t)f0 * ng * ng;
+                    double2* cb_ = cb_all + (size_t)f0 * 2 * ng;
+                    int* ib_ = ib_all + (size_t)f0 * (ng + 2);
                     int* err_ = err_flag;
-                    void* args[] = {(void*)&chi_, (void*)&vs_, (void*)&n_, (void*)&P_, (void*)&W_, (void*)&err_};
-                    e = cudaLaunchCooperativeKernel((const void*)k_dyson_coop, dim3(fg * P), dim3(DC_THREADS), args, smem,
-                                                    st);
+                    void* args[] = {(void*)&chi_, (void*)&vs_, (void*)&n_, (void*)&P_, (void*)&W_,
+                                    (void*)&cb_, (void*)&ib_, (void*)&err_};
+                    e = cudaLaunchCooperativeKernel((const void*)k_dyson_coop, dim3(fg * P_), dim3(DC_THREADS), args,
+                                                    smem, st);
                     if (e != cudaSuccess && f0 > 0) return e;     // a group already ran: report, no fallback
                 }
                 if (e == cudaSuccess) return cudaSuccess;

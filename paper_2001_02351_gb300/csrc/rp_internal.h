@@ -84,6 +84,7 @@ struct rp_ctx {
 
     rp::DevBuf d_coef, d_miller, d_npw, d_energy, d_T, d_tets, d_tetk;
     rp::DevBuf d_err;                 // int error flags written by kernels
+    rp::DevBuf s_dy;                  // scratch of the cooperative Dyson solve
     // scratch (grow-only)
     rp::DevBuf s_box, s_u1, s_u2, s_u, s_p, s_t1, s_t2, s_m, s_w, s_chi, s_io1, s_io2, s_io3;
     rp::DevBuf s_hi, s_lo;            // bf16 hi/lo split of a block of pair densities
@@ -95,6 +96,7 @@ struct rp_ctx {
     rp::DevBuf d_wcoef, s_wm, s_wb, s_wy, s_wtab, s_wout;
     int num_sms = 0;
     unsigned long long wait_ns = 2000000000ULL;   // limit of a bounded device wait (rp_set_wait_limit)
+    size_t pair_budget = (size_t)16 << 30;        // plane-sum scratch of the pair stage (rp_set_pair_budget)
     std::map<int, int> tile_bn;                   // NG -> raw rows per tile of the BF16x3 contraction
                                                   // (rp_tune_contraction / rp_set_contraction_tile)
     std::vector<double> freq_stage;               // host copy of the frequencies of the last weight pass
@@ -170,8 +172,9 @@ cudaError_t launch_fill_tune_operands(void* hi, void* lo, long long n_bf16, void
 cudaError_t launch_contract_tf32x3(const void* M, bool m32, long long ldm, long long K, const double2* w,
                                    long long ldw, long long col0w, int nf, int ng, double2* chi, int accumulate,
                                    cudaStream_t st);
-// Dyson step
-cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W,
+// Dyson step; scratch: dyson_scratch_bytes(ng, nf) of device memory (NULL: one CTA per frequency)
+size_t dyson_scratch_bytes(int ng, int nf);
+cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W, void* scratch,
                          int* err_flag, cudaStream_t st);
 // head row at q -> 0: u_b = qhat.p_b / D_b of the pairs of k in [k0, k0 + nkb) into M[col0 + b] (complex
 // float when fp32, else complex double)

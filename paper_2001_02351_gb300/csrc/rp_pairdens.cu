@@ -394,8 +394,8 @@ struct ZyLayout {
 };
 
 template <typename C, int N3, int N2, int W>
-__global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const C* __restrict__ u, int nband, int nocc, int nemp, int N1,
-                                                 unsigned zmask, int nz_, unsigned ymask, int ny_,
+__global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const C* __restrict__ u, int nband, int nocc, int e0,
+                                                 int nemp, int N1, unsigned zmask, int nz_, unsigned ymask, int ny_,
                                                  C* __restrict__ T2) {
     static_assert(W == 0 || (2 * W + 1 <= N2 && 2 * W + 1 <= N3), "window wider than the plane");
     constexpr int NW = 2 * W + 1;
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(128, sizeof(C) == 16 ? 1 : 3) k_pair_zy(const 
     const size_t plane = (size_t)N2 * N3;
     const C* uk = u + (size_t)kl * nband * N1 * plane + x * plane;
     for (int q = 0; q < na; ++q) {
-        const C* ua = uk + (size_t)(nocc + a0 + q) * N1 * plane;
+        const C* ua = uk + (size_t)(nocc + e0 + a0 + q) * N1 * plane;
         for (int e = threadIdx.x; e < N2 * N3; e += 128) sa[(q * N2 + e / N3) * LD + e % N3] = ua[e];
     }
     // occupied plane 0
@@ -641,7 +641,7 @@ static bool launch_x_w_n(const float2* T2, long long npair, const int* colg, int
 }
 
 template <typename C, int N, int W>
-static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int N1, unsigned zmask, int nz,
+static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int e0, int nemp, int N1, unsigned zmask, int nz,
                         unsigned ymask, int ny, C* T2, cudaStream_t st) {
     constexpr int A = ZyLayout<C, N>::A;
     if (W > 0) nz = ny = 2 * W + 1;
@@ -651,16 +651,18 @@ static bool launch_zy_n(const C* u, int nkb, int nband, int nocc, int nemp, int 
         cudaSuccess)
         return false;
     dim3 grid(N1, (nemp + A - 1) / A, nkb);
-    k_pair_zy<C, N, N, W><<<grid, 128, smem, st>>>(u, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2);
+    k_pair_zy<C, N, N, W><<<grid, 128, smem, st>>>(u, nband, nocc, e0, nemp, N1, zmask, nz, ymask, ny, T2);
     return true;
 }
 
 // half-widths of the symmetric residue windows the FP32 plane kernel is built for, per plane
-// length 16, 24, 32 (ascending; the plan takes the narrowest that holds the sphere)
-static constexpr int kZyWin[3][5] = {{2, 3, 4, 5, 7}, {3, 5, 6, 7, 11}, {5, 7, 8, 11, 15}};
+// length 16, 24, 32, 48 (ascending; the plan takes the narrowest that holds the sphere)
+static constexpr int kZyWin[4][5] = {{2, 3, 4, 5, 7}, {3, 5, 6, 7, 11}, {5, 7, 8, 11, 15}, {7, 9, 11, 15, 23}};
+template <int N>
+static constexpr int zy_row() { return N == 16 ? 0 : N == 24 ? 1 : N == 32 ? 2 : 3; }
 
 int zy_window(int n, int m) {
-    const int i = n == 16 ? 0 : n == 24 ? 1 : n == 32 ? 2 : -1;
+    const int i = n == 16 ? 0 : n == 24 ? 1 : n == 32 ? 2 : n == 48 ? 3 : -1;
     if (i < 0) return 0;
     for (int w : kZyWin[i])
         if (w >= m) return w;
@@ -668,21 +670,21 @@ int zy_window(int n, int m) {
 }
 
 template <int N>
-static bool launch_zy_win(int w, const float2* u, int nkb, int nband, int nocc, int nemp, int N1, float2* T2,
+static bool launch_zy_win(int w, const float2* u, int nkb, int nband, int nocc, int e0, int nemp, int N1, float2* T2,
                           cudaStream_t st) {
-    constexpr int i = N == 16 ? 0 : N == 24 ? 1 : 2;
-    if (w == kZyWin[i][0]) return launch_zy_n<float2, N, kZyWin[i][0]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
-    if (w == kZyWin[i][1]) return launch_zy_n<float2, N, kZyWin[i][1]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
-    if (w == kZyWin[i][2]) return launch_zy_n<float2, N, kZyWin[i][2]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
-    if (w == kZyWin[i][3]) return launch_zy_n<float2, N, kZyWin[i][3]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
-    if (w == kZyWin[i][4]) return launch_zy_n<float2, N, kZyWin[i][4]>(u, nkb, nband, nocc, nemp, N1, 0, 0, 0, 0, T2, st);
+    constexpr int i = zy_row<N>();
+    if (w == kZyWin[i][0]) return launch_zy_n<float2, N, kZyWin[i][0]>(u, nkb, nband, nocc, e0, nemp, N1, 0, 0, 0, 0, T2, st);
+    if (w == kZyWin[i][1]) return launch_zy_n<float2, N, kZyWin[i][1]>(u, nkb, nband, nocc, e0, nemp, N1, 0, 0, 0, 0, T2, st);
+    if (w == kZyWin[i][2]) return launch_zy_n<float2, N, kZyWin[i][2]>(u, nkb, nband, nocc, e0, nemp, N1, 0, 0, 0, 0, T2, st);
+    if (w == kZyWin[i][3]) return launch_zy_n<float2, N, kZyWin[i][3]>(u, nkb, nband, nocc, e0, nemp, N1, 0, 0, 0, 0, T2, st);
+    if (w == kZyWin[i][4]) return launch_zy_n<float2, N, kZyWin[i][4]>(u, nkb, nband, nocc, e0, nemp, N1, 0, 0, 0, 0, T2, st);
     return false;
 }
 
 template <int N, typename CO>
 static bool launch_x_win_n(int w, const float2* T2, long long npair, const int* colg, int ng, float scale, CO* M,
                            long long ldm, long long col0, cudaStream_t st) {
-    constexpr int i = N == 16 ? 0 : N == 24 ? 1 : 2;
+    constexpr int i = zy_row<N>();
     if (w == kZyWin[i][0]) return launch_x_w_n<N, kZyWin[i][0], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
     if (w == kZyWin[i][1]) return launch_x_w_n<N, kZyWin[i][1], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
     if (w == kZyWin[i][2]) return launch_x_w_n<N, kZyWin[i][2], CO>(T2, npair, colg, ng, scale, M, ldm, col0, st);
@@ -700,22 +702,25 @@ static bool launch_x_win(int n, int w, const float2* T2, long long npair, const 
         case 16: return launch_x_win_n<16, CO>(w, T2, npair, colg, ng, scale, M, ldm, col0, st);
         case 24: return launch_x_win_n<24, CO>(w, T2, npair, colg, ng, scale, M, ldm, col0, st);
         case 32: return launch_x_win_n<32, CO>(w, T2, npair, colg, ng, scale, M, ldm, col0, st);
+        case 48: return launch_x_win_n<48, CO>(w, T2, npair, colg, ng, scale, M, ldm, col0, st);
         default: return false;
     }
 }
 
 // plane-wise path for square planes N2 == N3 of a supported length: the residue masks, or (FP32
 // lines, w > 0) the symmetric window of half-width w
+// (empty bands e0 .. e0 + nemp - 1 of each k; the masks are 32-bit, so the residue-set form stops at 32)
 template <typename C>
-static bool launch_zy(int n2, int n3, int w, const C* u, int nkb, int nband, int nocc, int nemp, int N1,
+static bool launch_zy(int n2, int n3, int w, const C* u, int nkb, int nband, int nocc, int e0, int nemp, int N1,
                       unsigned zmask, int nz, unsigned ymask, int ny, C* T2, cudaStream_t st) {
     if (n2 != n3) return false;
     if constexpr (sizeof(C) == 8) {
         if (w > 0) {
             switch (n3) {
-                case 16: return launch_zy_win<16>(w, u, nkb, nband, nocc, nemp, N1, T2, st);
-                case 24: return launch_zy_win<24>(w, u, nkb, nband, nocc, nemp, N1, T2, st);
-                case 32: return launch_zy_win<32>(w, u, nkb, nband, nocc, nemp, N1, T2, st);
+                case 16: return launch_zy_win<16>(w, u, nkb, nband, nocc, e0, nemp, N1, T2, st);
+                case 24: return launch_zy_win<24>(w, u, nkb, nband, nocc, e0, nemp, N1, T2, st);
+                case 32: return launch_zy_win<32>(w, u, nkb, nband, nocc, e0, nemp, N1, T2, st);
+                case 48: return launch_zy_win<48>(w, u, nkb, nband, nocc, e0, nemp, N1, T2, st);
                 default: return false;
             }
         }
@@ -723,9 +728,9 @@ static bool launch_zy(int n2, int n3, int w, const C* u, int nkb, int nband, int
         if (w > 0) return false;
     }
     switch (n3) {
-        case 16: return launch_zy_n<C, 16, 0>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
-        case 24: return launch_zy_n<C, 24, 0>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
-        case 32: return launch_zy_n<C, 32, 0>(u, nkb, nband, nocc, nemp, N1, zmask, nz, ymask, ny, T2, st);
+        case 16: return launch_zy_n<C, 16, 0>(u, nkb, nband, nocc, e0, nemp, N1, zmask, nz, ymask, ny, T2, st);
+        case 24: return launch_zy_n<C, 24, 0>(u, nkb, nband, nocc, e0, nemp, N1, zmask, nz, ymask, ny, T2, st);
+        case 32: return launch_zy_n<C, 32, 0>(u, nkb, nband, nocc, e0, nemp, N1, zmask, nz, ymask, ny, T2, st);
         default: return false;
     }
 }
@@ -867,23 +872,26 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
     {
         const int w = sizeof(C) == 8 ? P.zyw : 0;
         const int wy = w > 0 ? 2 * w + 1 : ny, wz = w > 0 ? 2 * w + 1 : nz;
-        const long long npair = (long long)nkb * c->nemp * c->nocc;
-        const size_t t2 = (size_t)npair * N1 * wy * wz * sizeof(C);
+        const size_t per_pair = (size_t)N1 * wy * wz * sizeof(C);
+        const size_t budget = c->pair_budget;
+        // empty bands per pass: all of them when the k block's plane sums fit the budget, else (a
+        // single k point, whose pairs are columns (a, o) in order) chunks of empty bands
+        int ne = c->nemp;
+        if ((size_t)nkb * c->nemp * c->nocc * per_pair > budget)
+            ne = nkb == 1 ? (int)std::min<size_t>((size_t)c->nemp,
+                                                  std::max<size_t>(1, budget / ((size_t)c->nocc * per_pair)))
+                          : 0;
         constexpr int PB = PairX<C>::PB;
         // shared memory of the x read-out that will run: k_pair_x_w holds only its pairs' outputs
         const size_t xsm = w > 0 ? (size_t)P.ng * PairXW<2>::PB * sizeof(C)
                                           : ((size_t)2 * PB * N1 * wy * wz + (size_t)P.nset[0] * N1 +
                                              (size_t)P.ng * PB) * sizeof(C);
-        if (P.fused && (w > 0 || P.masks) && xsm <= 200 * 1024 && t2 <= (size_t)16 << 30 &&
-            ensure(c, c->s_t2, t2) == RP_OK &&
-            launch_zy<C>(N2, N3, w, (const C*)c->s_u.p, nkb, c->nband, c->nocc, c->nemp, N1, P.zmask, nz, P.ymask,
-                         ny, (C*)c->s_t2.p, st)) {
+        // the x sum of npair pairs of T2 into columns col .. col + npair - 1
+        auto x_readout = [&](long long npair, long long col) -> cudaError_t {
             if constexpr (sizeof(C) == 8) {
                 if (w > 0 && launch_x_win<CO>(N1, w, (const float2*)c->s_t2.p, npair, (const int*)P.d_colg.p, P.ng,
-                                              (float)(1.0 / (double)nr), M, ldm, col0, st)) {
-                    *nlaunch += 2;
+                                              (float)(1.0 / (double)nr), M, ldm, col, st))
                     return cudaGetLastError();
-                }
             }
             cudaError_t e = cudaFuncSetAttribute(k_pair_x<C, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
             if (e != cudaSuccess) return e;
@@ -899,9 +907,23 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
             k_pair_x<C, CO><<<grid, PX_THREADS, xsm, st>>>(
                 (const C*)c->s_t2.p, npair, N1, wy * wz, wz, efwd[0], P.nset[0],
                 (const int*)(w > 0 ? P.d_gpos_w.p : P.d_gpos_r.p), P.ng,
-                (typename CT<C>::R)(1.0 / (double)nr), M, ldm, col0);
-            *nlaunch += 2;
+                (typename CT<C>::R)(1.0 / (double)nr), M, ldm, col);
             return cudaGetLastError();
+        };
+        if (ne > 0 && P.fused && (w > 0 || P.masks) && xsm <= 200 * 1024 &&
+            ensure(c, c->s_t2, (size_t)nkb * ne * c->nocc * per_pair) == RP_OK) {
+            for (int e0 = 0; e0 < c->nemp; e0 += ne) {
+                const int nab = std::min(ne, c->nemp - e0);
+                if (!launch_zy<C>(N2, N3, w, (const C*)c->s_u.p, nkb, c->nband, c->nocc, e0, nab, N1, P.zmask, nz,
+                                  P.ymask, ny, (C*)c->s_t2.p, st)) {
+                    if (e0 == 0) break;             // not built or refused: the paths below
+                    return cudaErrorLaunchFailure;  // (the same launch as the first chunk's)
+                }
+                cudaError_t e = x_readout((long long)nkb * nab * c->nocc, col0 + (long long)e0 * c->nocc);
+                if (e != cudaSuccess) return e;
+                *nlaunch += 2;
+                if (e0 + nab >= c->nemp) return cudaGetLastError();
+            }
         }
     }
     // fused path over the whole k block when its partial transforms fit the scratch budget
