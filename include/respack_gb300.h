@@ -305,6 +305,17 @@ int rp_set_contraction_tile(rp_ctx* ctx, int ng, int bn);
  *   the tcgen05 probe's bounded wait gave up. */
 int rp_probe_peaks(double* out);
 
+/* rp_set_fermi -- metals (Sec. 2.3; Eq. Xakqbk with the occupations of a metal): with a Fermi energy
+ *   set, the tetrahedron weights of a pair (a, o) integrate each tetrahedron only over its part where
+ *   band o (at k) lies below efermi_ha and band a (at k + q) above it, both interpolated linearly
+ *   (Fermi-surface clipping: the part is cut into sub-tetrahedra and the generalized tetrahedron
+ *   formula applied on each), evaluated in FP64 for every precision tier.  A metal's band list
+ *   (rp_load_bands) holds its partly filled bands in both ranges: the first nocc entries are the
+ *   bands that may be occupied, the next ones those that may be empty, so a partly filled band is
+ *   passed twice and (a, o) of one band with itself is an intraband term.  NaN turns the clipping
+ *   off (band-index occupations, the default).  RP_ERR_ARG for an infinite value. */
+int rp_set_fermi(rp_ctx* ctx, double efermi_ha);
+
 /* rp_set_pair_budget -- bytes of device scratch the pair-density stage may give to the plane sums of
  *   its pair kernels (default 16 GiB).  The k points are taken in sub-blocks whose plane sums fit;
  *   when one k point's do not, its empty bands are taken in chunks that fit (the pair densities are

@@ -189,6 +189,106 @@ def vertex_weights(e_occ, e_emp_kq, tets, z1, z2, delta_a, delta_r, k_list=None,
     return x[ks]
 
 
+def clip_negative(e):
+    """Sub-tetrahedra of the part of a tetrahedron where a function linear on it is negative.
+
+    e: [4] values at the vertices.  Returns a list of [4, 4] matrices B whose row i is sub-vertex i
+    in barycentric coordinates of the tetrahedron (so a sub-vertex is sum_j B[i, j] vertex_j, and
+    the sub-tetrahedron's volume is |det B| of the whole).  With n vertices below zero the region
+    is: nothing (n = 0); the corner at the lowest vertex cut off by the zero plane (n = 1); a
+    triangular prism between the two low vertices and the plane (n = 2); the whole minus the
+    corner at the highest vertex, again a prism (n = 3); the whole (n = 4).  A prism with
+    triangles A, B and lateral edges A_i B_i is cut into (A0 A1 A2 B0), (A1 A2 B0 B1), (A2 B0 B1 B2).
+    Zero counts as not negative (the boundary has no volume)."""
+    e = np.asarray(e, dtype=np.float64)
+    s = np.argsort(e, kind="stable")
+    n = int(np.sum(e < 0.0))
+    eye = np.eye(4)
+
+    def cut(u, v):
+        # the point of edge u-v where the function vanishes (e[u] < 0 <= e[v])
+        t = e[u] / (e[u] - e[v])
+        return (1.0 - t) * eye[u] + t * eye[v]
+
+    def prism(A, B):
+        return [np.array([A[0], A[1], A[2], B[0]]), np.array([A[1], A[2], B[0], B[1]]),
+                np.array([A[2], B[0], B[1], B[2]])]
+
+    if n == 0:
+        return []
+    if n == 4:
+        return [eye.copy()]
+    if n == 1:
+        return [np.array([eye[s[0]], cut(s[0], s[1]), cut(s[0], s[2]), cut(s[0], s[3])])]
+    if n == 2:
+        return prism([eye[s[0]], cut(s[0], s[2]), cut(s[0], s[3])],
+                     [eye[s[1]], cut(s[1], s[2]), cut(s[1], s[3])])
+    return prism([eye[s[0]], eye[s[1]], eye[s[2]]],
+                 [cut(s[0], s[3]), cut(s[1], s[3]), cut(s[2], s[3])])
+
+
+def occupied_pieces(eo, ea, fermi):
+    """Sub-tetrahedra (barycentric [4, 4] matrices of the whole) of the part of a tetrahedron where
+    the occupied band lies below the Fermi energy and the empty band at k+q above it: eo, ea [4]
+    vertex energies, each interpolated linearly (Fermi-surface clipping of the metallic
+    generalized tetrahedron method)."""
+    out = []
+    for B in clip_negative(np.asarray(eo) - fermi):
+        # the empty band's values at this piece's vertices; keep where it lies above the Fermi energy
+        g = B @ (fermi - np.asarray(ea))
+        for C in clip_negative(g):
+            out.append(C @ B)
+    return out
+
+
+def clipped_vertex_weights(d, pieces, sub_weight):
+    """(1/V_t) int over the pieces of lambda_j g(D) for the four vertices j of a tetrahedron, with
+    D linear (vertex values d [4]).  On a piece with barycentric matrix F (volume |det F| of the
+    whole), lambda_j = sum_i mu_i F[i, j] (mu_i the piece's own barycentric weights), so the
+    piece gives |det F| sum_i F[i, j] w_i, where w_i is the vertex-i weight of the piece (the
+    unclipped formula on the piece).  sub_weight(ds) takes D at the pieces' vertices [P, 4] and
+    returns their vertex weights [P, 4, ...].  Returns [4, ...], or None without pieces."""
+    if not pieces:
+        return None
+    F = np.stack(pieces)                                   # [P, 4 (i), 4 (j)]
+    vol = np.abs(np.linalg.det(F))                         # [P]
+    ds = F @ np.asarray(d, dtype=np.float64)               # [P, 4]
+    w = np.asarray(sub_weight(ds))                         # [P, 4, ...]
+    return np.tensordot(vol[:, None, None] * F, w, axes=([0, 1], [0, 1]))   # [4 (j), ...]
+
+
+def metal_vertex_weights(e_occ, e_emp_kq, tets, z1, z2, delta_a, delta_r, fermi, k_list=None):
+    """x[k, a, o, f] of the metallic generalized tetrahedron method: as vertex_weights, but each
+    tetrahedron contributes only over its part where band o (at k) is occupied and band a (at
+    k + q) is empty, with the Fermi energy `fermi` (both bands interpolated linearly)."""
+    nk, nocc = e_occ.shape
+    nemp = e_emp_kq.shape[1]
+    nf = len(z1)
+    ks = np.arange(nk) if k_list is None else np.asarray(k_list)
+    want = np.zeros(nk, dtype=bool)
+    want[ks] = True
+    sel = tets[np.any(want[tets], axis=1)]
+    x = np.zeros((nk, nemp, nocc, nf), dtype=np.complex128)
+    zz = [np.asarray(z1)[None, None, :], np.asarray(z2)[None, None, :]]
+
+    def sub_weight(ds):
+        # nodes of piece p, vertex i: its four D values and D_i again -> [P, 4, 1, 5]
+        nodes = np.concatenate([np.repeat(ds[:, None, :], 4, axis=1), ds[:, :, None]], axis=2)[:, :, None, :]
+        return sum(divided_difference(nodes, z, delta_a, delta_r) for z in zz)    # [P, 4, nf]
+
+    for tt in sel:
+        for a in range(nemp):
+            for o in range(nocc):
+                eo, ea = e_occ[tt, o], e_emp_kq[tt, a]
+                val = clipped_vertex_weights(ea - eo, occupied_pieces(eo, ea, fermi), sub_weight)
+                if val is None:
+                    continue
+                for j in range(4):
+                    if want[tt[j]]:
+                        x[tt[j], a, o] += val[j] / 6.0
+    return x[ks]
+
+
 def lorentz_x(e_occ, e_emp_kq, z1, z2):
     """X of Eq. Xakqbk at the mesh points themselves: [k, a, o, f]."""
     d = (e_emp_kq[:, :, None] - e_occ[:, None, :])[..., None]

@@ -849,6 +849,18 @@ int rp_tune_contraction(rp_ctx* c, int ng, long long K, int nfreq, int* bn_out, 
     return RP_OK;
 }
 
+int rp_set_fermi(rp_ctx* c, double efermi_ha) {
+    if (!c) return RP_ERR_ARG;
+    if (std::isnan(efermi_ha)) {
+        c->metal = false;
+        return RP_OK;
+    }
+    if (!std::isfinite(efermi_ha)) return fail(c, RP_ERR_ARG, "Fermi energy not finite");
+    c->metal = true;
+    c->efermi = efermi_ha;
+    return RP_OK;
+}
+
 int rp_set_pair_budget(rp_ctx* c, long long bytes) {
     if (!c) return RP_ERR_ARG;
     if (bytes < 1) return fail(c, RP_ERR_ARG, "pair budget must be positive");
@@ -1125,11 +1137,167 @@ int rp_build_chi0_batched(rp_ctx* c, int nq, const double* q_frac, const double*
     return RP_OK;
 }
 
+// Device buffers: every (q, w) matrix of the batch, sorted by NG (largest first), goes into
+// cooperative launches of k_dyson_list that each fill the GPU.  Consecutive matrices join a launch
+// while their summed per-pivot work (sum of NG^2) stays below about a large sphere's frequency set,
+// so small spheres share their grid barriers; each matrix gets CTAs in proportion to NG^2 (equal
+// work per CTA and step), at least 2 and at most one per 8 columns.
+static constexpr int kPerQ = -1;     // solve_w_list: use the per-q solves instead
+static int solve_w_list(rp_ctx* c, int nq, const double* q_frac, const double* cuts, int nfreq,
+                        const double* const* chi0, double* const* W_out, double* const* tail_out, cudaStream_t st) {
+    int s;
+    if (c->last_stream) {
+        // a bad pivot of an earlier asynchronous call is reported here
+        int flag = 0;
+        if (cudaMemcpy(&flag, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && flag) {
+            cudaMemset(c->d_err.p, 0, sizeof(int));
+            return fail(c, RP_ERR_NUMERIC, "zero or non-finite pivot in an earlier Dyson solve");
+        }
+    }
+    std::vector<int> ng(nq);
+    std::vector<size_t> vofs(nq);
+    c->dy_vs.clear();
+    for (int i = 0; i < nq; ++i) {
+        if ((s = check_ready_cut(c, q_frac + 3 * i, cuts ? cuts[i] : c->ecut_eps))) return s;
+        ng[i] = c->plan.ng;
+        if (ng[i] > 4096) return fail(c, RP_ERR_UNSUPPORTED, "NG above 4096");
+        vofs[i] = c->dy_vs.size();
+        c->dy_vs.insert(c->dy_vs.end(), c->plan.vs.begin(), c->plan.vs.end());
+        if (tail_out && tail_out[i] && c->plan.ntail > 0) {
+            // staged from the plan's pageable vector before the call returns
+            cudaError_t e = cudaMemcpyAsync(tail_out[i], c->plan.tailv.data(), c->plan.ntail * sizeof(double),
+                                            cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "tail");
+        }
+    }
+    // spheres below 16 points take the per-q solve (at least 8 columns for each of two CTAs)
+    if (*std::min_element(ng.begin(), ng.end()) < 16) return kPerQ;
+    // matrices, largest sphere first; scratch offsets
+    const int nm = nq * nfreq;
+    std::vector<int> order(nm);
+    for (int m = 0; m < nm; ++m) order[m] = m;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ng[a / nfreq] > ng[b / nfreq]; });
+    size_t cb_bytes = 0, ib_bytes = 0;
+    for (int i = 0; i < nq; ++i) {
+        cb_bytes += (size_t)nfreq * 2 * ng[i] * sizeof(double2);
+        ib_bytes += (size_t)nfreq * (ng[i] + 2) * sizeof(int);
+    }
+    const size_t vs_bytes = c->dy_vs.size() * sizeof(double);
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    // launches: [first, last) of the sorted list, with their CTA counts
+    std::vector<int> lb, lcount;
+    std::vector<DysonMat> mats(nm);
+    std::vector<int2> map;
+    {
+        const double target = 24.0 * 904.0 * 904.0;
+        int m0 = 0;
+        while (m0 < nm) {
+            const int nmax = ng[order[m0] / nfreq];
+            const int slots = dyson_list_slots(nmax);
+            if (slots < 2) return fail(c, RP_ERR_CUDA, "batched Dyson kernel cannot be resident");
+            double work = 0.0;
+            int m1 = m0;
+            while (m1 < nm && (m1 - m0 + 1) * 2 <= slots) {
+                const double n = ng[order[m1] / nfreq];
+                if (m1 > m0 && work + n * n > target) break;
+                work += n * n;
+                ++m1;
+            }
+            // two CTAs per matrix, then each further resident slot to the matrix whose CTAs have the
+            // most work per step (NG^2 / P), up to one CTA per 8 columns: every slot is used and the
+            // CTAs' work is as even as whole CTAs allow
+            std::vector<int> P(m1 - m0, 2);
+            int used = 2 * (m1 - m0);
+            {
+                std::vector<std::pair<double, int>> heap;
+                for (int t = m0; t < m1; ++t) {
+                    const double n = ng[order[t] / nfreq];
+                    heap.push_back({n * n / 2.0, t - m0});
+                }
+                std::make_heap(heap.begin(), heap.end());
+                while (used < slots && !heap.empty()) {
+                    std::pop_heap(heap.begin(), heap.end());
+                    const int i = heap.back().second;
+                    heap.pop_back();
+                    const int n = ng[order[m0 + i] / nfreq];
+                    if (P[i] >= std::max(2, n / 8)) continue;
+                    ++P[i];
+                    ++used;
+                    heap.push_back({(double)n * n / P[i], i});
+                    std::push_heap(heap.begin(), heap.end());
+                }
+            }
+            lb.push_back(m0);
+            lcount.push_back(used);
+            for (int t = m0; t < m1; ++t) {
+                mats[t].n = ng[order[t] / nfreq];
+                mats[t].P = P[t - m0];
+                for (int pc = 0; pc < P[t - m0]; ++pc) map.push_back(make_int2(t, pc));
+            }
+            m0 = m1;
+        }
+        lb.push_back(nm);
+    }
+    const size_t mats_bytes = (size_t)nm * sizeof(DysonMat), map_bytes = map.size() * sizeof(int2);
+    const size_t total = up(cb_bytes) + up(ib_bytes) + up(vs_bytes) + up(mats_bytes) + up(map_bytes);
+    if ((s = ensure(c, c->s_dy, total))) return s;
+    char* base = (char*)c->s_dy.p;
+    double2* cb = (double2*)base;
+    int* ib = (int*)(base + up(cb_bytes));
+    double* dvs = (double*)(base + up(cb_bytes) + up(ib_bytes));
+    DysonMat* dmats = (DysonMat*)(base + up(cb_bytes) + up(ib_bytes) + up(vs_bytes));
+    int2* dmap = (int2*)((char*)dmats + up(mats_bytes));
+    // per-matrix pointers: scratch in the order of q and w
+    {
+        std::vector<size_t> cbo(nq), ibo(nq);
+        size_t a = 0, b = 0;
+        for (int i = 0; i < nq; ++i) {
+            cbo[i] = a; ibo[i] = b;
+            a += (size_t)nfreq * 2 * ng[i];
+            b += (size_t)nfreq * (ng[i] + 2);
+        }
+        for (int t = 0; t < nm; ++t) {
+            const int i = order[t] / nfreq, f = order[t] % nfreq;
+            const size_t n = (size_t)ng[i];
+            mats[t].chi = (const double2*)chi0[i] + (size_t)f * n * n;
+            mats[t].W = (double2*)W_out[i] + (size_t)f * n * n;
+            mats[t].vs = dvs + vofs[i];
+            mats[t].cb = cb + cbo[i] + (size_t)f * 2 * n;
+            mats[t].ib = ib + ibo[i] + (size_t)f * (n + 2);
+        }
+    }
+    // the lists go through context-owned pageable copies (staged before each copy call returns)
+    c->dy_mats = mats;
+    c->dy_map = map;
+    cudaError_t e = cudaMemcpyAsync(dvs, c->dy_vs.data(), vs_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dmats, c->dy_mats.data(), mats_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dmap, c->dy_map.data(), map_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched Dyson lists");
+    prof_begin(c, 4, st);
+    int cta0 = 0;
+    for (size_t l = 0; l + 1 < lb.size(); ++l) {
+        const int nmax = ng[order[lb[l]] / nfreq];
+        e = launch_dyson_list(dmats, dmap + cta0, lcount[l], nmax, (int*)c->d_err.p, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "batched Dyson solve");
+        cta0 += lcount[l];
+    }
+    prof_end(c, 4, st, (int)lb.size() - 1);
+    return finish(c, st, 1);
+}
+
 int rp_solve_w_batched(rp_ctx* c, int nq, const double* q_frac, const double* ecut_eps_per_q, int nfreq,
                        const double* const* chi0, double* const* W_out, double* const* tail_out, int on_device,
                        void* stream) {
     if (!c) return RP_ERR_ARG;
     if (nq < 1 || !q_frac || !chi0 || !W_out) return fail(c, RP_ERR_ARG, "bad batch arguments");
+    if (nfreq < 1) return fail(c, RP_ERR_ARG, "bad Dyson arguments");
+    if (on_device && nq > 1) {
+        if (!c->loaded) return fail(c, RP_ERR_STATE, "bands not loaded");
+        for (int i = 0; i < nq; ++i)
+            if (!chi0[i] || !W_out[i]) return fail(c, RP_ERR_ARG, "bad Dyson arguments");
+        const int s = solve_w_list(c, nq, q_frac, ecut_eps_per_q, nfreq, chi0, W_out, tail_out, (cudaStream_t)stream);
+        if (s != kPerQ) return s;
+    }
     for (int i = 0; i < nq; ++i) {
         const double cut = ecut_eps_per_q ? ecut_eps_per_q[i] : c->ecut_eps;
         const int s = solve_w(c, q_frac + 3 * i, cut, nfreq, chi0[i], W_out[i], tail_out ? tail_out[i] : nullptr,

@@ -166,26 +166,21 @@ __global__ void __launch_bounds__(DY_THREADS) k_dyson(const double2* __restrict_
 #define DC_THREADS 512
 #define DC_UNROLL 4
 
-__global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __restrict__ chi,
-                                                           const double* __restrict__ vs, int n, int P,
-                                                           double2* __restrict__ Wout,
-                                                           double2* __restrict__ colbuf, int* __restrict__ ibuf,
-                                                           int* err_flag) {
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
-    extern __shared__ unsigned char smem[];
+// CTA pc of the P CTAs of one matrix: X = chi (n x n), A = W, cb = [2][n] published columns, perm =
+// [n] pivot rows then [2] published pivots.  nsteps >= n grid barriers after the first (a launch over
+// matrices of several sizes runs the largest count; a smaller matrix passes the extra barriers idle).
+__device__ __forceinline__ void dyson_coop_body(cooperative_groups::grid_group& grid, const double2* __restrict__ X,
+                                                const double* __restrict__ vs, int n, int P, int pc,
+                                                double2* __restrict__ A, double2* __restrict__ cb,
+                                                int* __restrict__ perm, int nsteps, int* err_flag,
+                                                unsigned char* smem) {
     double2* colj = (double2*)smem;        // column j after the interchange (all rows)
     double2* rowj = colj + n;              // scaled pivot row on this CTA's columns; a row in the undo
     int* idx = (int*)(rowj + n);           // column gather of the undo
     __shared__ double red_v[DC_THREADS / 32];
     __shared__ int red_i[DC_THREADS / 32];
-    const int f = blockIdx.x / P, pc = blockIdx.x % P;
     const int c0 = (int)((long long)n * pc / P), c1 = (int)((long long)n * (pc + 1) / P);
     const int w = c1 - c0;
-    const double2* X = chi + (size_t)f * n * n;
-    double2* A = Wout + (size_t)f * n * n;
-    double2* cb = colbuf + (size_t)f * 2 * n;      // [2][n]: the published column of even / odd steps
-    int* perm = ibuf + (size_t)f * (n + 2);        // [n] pivot rows, then [2] published pivots
     int* pivb = perm + n;
     const int tid = threadIdx.x;
     // element walk over this CTA's n x w block, row-major, without divisions in the loop
@@ -218,10 +213,10 @@ __global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __rest
     }
     grid.sync();
     bool bad = false;                      // uniform over the CTA (read from the same published value)
-    for (int j = 0; j < n; ++j) {
+    for (int j = 0; j < nsteps; ++j) {
         const int cur = j & 1, nxt = cur ^ 1;
-        if (!bad) bad = __ldcg(&pivb[cur]) < 0;
-        if (!bad) {
+        if (j < n && !bad) bad = __ldcg(&pivb[cur]) < 0;
+        if (j < n && !bad) {
             const int p = __ldcg(&pivb[cur]);
             for (int i = tid; i < n; i += DC_THREADS) {
                 const int src = (i == j) ? p : (i == p ? j : i);
@@ -324,6 +319,53 @@ __global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __rest
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __restrict__ chi,
+                                                           const double* __restrict__ vs, int n, int P,
+                                                           double2* __restrict__ Wout,
+                                                           double2* __restrict__ colbuf, int* __restrict__ ibuf,
+                                                           int* err_flag) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    extern __shared__ unsigned char smem[];
+    const int f = blockIdx.x / P, pc = blockIdx.x % P;
+    dyson_coop_body(grid, chi + (size_t)f * n * n, vs, n, P, pc, Wout + (size_t)f * n * n, colbuf + (size_t)f * 2 * n,
+                    ibuf + (size_t)f * (n + 2), n, err_flag, smem);
+}
+
+// matrices of several sizes in one cooperative launch (the (q, w) members of a batch): CTA b works
+// on matrix map[b].x as its CTA map[b].y; every CTA passes nsteps = the largest n barriers
+__global__ void __launch_bounds__(DC_THREADS) k_dyson_list(const DysonMat* __restrict__ mats,
+                                                           const int2* __restrict__ map, int nsteps,
+                                                           int* err_flag) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    extern __shared__ unsigned char smem[];
+    const int2 mp = map[blockIdx.x];
+    const DysonMat m = mats[mp.x];
+    dyson_coop_body(grid, m.chi, m.vs, m.n, m.P, mp.y, m.W, m.cb, m.ib, nsteps, err_flag, smem);
+}
+
+int dyson_list_slots(int nmax) {
+    const size_t smem = (size_t)nmax * (2 * sizeof(double2) + sizeof(int));
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k_dyson_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dyson_list, DC_THREADS, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * nsm;
+}
+
+cudaError_t launch_dyson_list(const DysonMat* d_mats, const int2* d_map, int nblocks, int nmax, int* err_flag,
+                              cudaStream_t st) {
+    const size_t smem = (size_t)nmax * (2 * sizeof(double2) + sizeof(int));
+    cudaError_t e = cudaFuncSetAttribute(k_dyson_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsteps = nmax;
+    void* args[] = {(void*)&d_mats, (void*)&d_map, (void*)&nsteps, (void*)&err_flag};
+    return cudaLaunchCooperativeKernel((const void*)k_dyson_list, dim3(nblocks), dim3(DC_THREADS), args, smem, st);
 }
 
 size_t dyson_scratch_bytes(int ng, int nf) {

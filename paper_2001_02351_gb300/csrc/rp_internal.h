@@ -62,6 +62,17 @@ struct QPlan {
     DevBuf d_einv[3], d_einv32[3];
 };
 
+// one matrix of a batched Dyson launch: chi and W (n x n), v^1/2, its scratch (cb [2][n], ib [n + 2])
+// and its CTA count P
+struct DysonMat {
+    const double2* chi;
+    double2* W;
+    const double* vs;
+    double2* cb;
+    int* ib;
+    int n, P;
+};
+
 }  // namespace rp
 
 struct rp_ctx {
@@ -85,6 +96,9 @@ struct rp_ctx {
     rp::DevBuf d_coef, d_miller, d_npw, d_energy, d_T, d_tets, d_tetk;
     rp::DevBuf d_err;                 // int error flags written by kernels
     rp::DevBuf s_dy;                  // scratch of the cooperative Dyson solve
+    std::vector<double> dy_vs;        // staging of the batched Dyson solve: v^1/2 of every q,
+    std::vector<rp::DysonMat> dy_mats; // the matrix list
+    std::vector<int2> dy_map;         // and the CTA map
     // scratch (grow-only)
     rp::DevBuf s_box, s_u1, s_u2, s_u, s_p, s_t1, s_t2, s_m, s_w, s_chi, s_io1, s_io2, s_io3;
     rp::DevBuf s_hi, s_lo;            // bf16 hi/lo split of a block of pair densities
@@ -97,6 +111,8 @@ struct rp_ctx {
     int num_sms = 0;
     unsigned long long wait_ns = 2000000000ULL;   // limit of a bounded device wait (rp_set_wait_limit)
     size_t pair_budget = (size_t)16 << 30;        // plane-sum scratch of the pair stage (rp_set_pair_budget)
+    bool metal = false;                           // Fermi-surface clipping of the weights (rp_set_fermi)
+    double efermi = 0.0;
     std::map<int, int> tile_bn;                   // NG -> raw rows per tile of the BF16x3 contraction
                                                   // (rp_tune_contraction / rp_set_contraction_tile)
     std::vector<double> freq_stage;               // host copy of the frequencies of the last weight pass
@@ -172,6 +188,11 @@ cudaError_t launch_fill_tune_operands(void* hi, void* lo, long long n_bf16, void
 cudaError_t launch_contract_tf32x3(const void* M, bool m32, long long ldm, long long K, const double2* w,
                                    long long ldw, long long col0w, int nf, int ng, double2* chi, int accumulate,
                                    cudaStream_t st);
+// resident CTAs of the list kernel for matrices of at most nmax rows (0: not available)
+int dyson_list_slots(int nmax);
+// one cooperative launch of nblocks CTAs over a list of matrices (d_map[b] = {matrix, CTA of it})
+cudaError_t launch_dyson_list(const DysonMat* d_mats, const int2* d_map, int nblocks, int nmax, int* err_flag,
+                              cudaStream_t st);
 // Dyson step; scratch: dyson_scratch_bytes(ng, nf) of device memory (NULL: one CTA per frequency)
 size_t dyson_scratch_bytes(int ng, int nf);
 cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W, void* scratch,

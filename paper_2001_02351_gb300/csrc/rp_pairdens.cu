@@ -883,7 +883,12 @@ static cudaError_t pair_forward_t(rp_ctx* c, int nkb, CO* M, long long ldm, long
                           : 0;
         constexpr int PB = PairX<C>::PB;
         // shared memory of the x read-out that will run: k_pair_x_w holds only its pairs' outputs
-        const size_t xsm = w > 0 ? (size_t)P.ng * PairXW<2>::PB * sizeof(C)
+        // (PB pairs per block for the window of half-width w, as PairXW<w>)
+        auto xw_pb = [](int hw) {
+            const int nc = (2 * hw + 1) * (2 * hw + 1);
+            return 256 / (nc >= 256 ? 256 : (nc + 31) / 32 * 32);
+        };
+        const size_t xsm = w > 0 ? (size_t)P.ng * xw_pb(w) * sizeof(C)
                                           : ((size_t)2 * PB * N1 * wy * wz + (size_t)P.nset[0] * N1 +
                                              (size_t)P.ng * PB) * sizeof(C);
         // the x sum of npair pairs of T2 into columns col .. col + npair - 1

@@ -243,18 +243,8 @@ __device__ __forceinline__ void cswap(double& a, double& b) {
     b = hi;
 }
 
-// nodes of tetrahedron-vertex entry `code` for pair (a, o): loaded, sorted, degenerate groups
-// merged into their mean (Eq. tetrahedron thresholds), all in FP64
-__device__ __forceinline__ void tetra_nodes(const double* __restrict__ E, int nband, int nocc, int a, int o,
-                                            const int* __restrict__ kp, const int* __restrict__ tets, int code,
-                                            double da, double dr, double (&x)[5]) {
-    const int tt = code >> 2, jv = code & 3;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const int kv = tets[4 * tt + v];
-        x[v] = E[(size_t)kp[kv] * nband + nocc + a] - E[(size_t)kv * nband + o];
-    }
-    x[4] = jv == 0 ? x[0] : jv == 1 ? x[1] : jv == 2 ? x[2] : x[3];
+// five nodes sorted, degenerate groups merged into their mean (Eq. tetrahedron thresholds), FP64
+__device__ __forceinline__ void sort_merge5(double (&x)[5], double da, double dr) {
     cswap(x[0], x[1]); cswap(x[3], x[4]); cswap(x[2], x[4]); cswap(x[2], x[3]); cswap(x[0], x[3]);
     cswap(x[0], x[2]); cswap(x[1], x[4]); cswap(x[1], x[3]); cswap(x[1], x[2]);
     bool brk[5];
@@ -284,6 +274,21 @@ __device__ __forceinline__ void tetra_nodes(const double* __restrict__ E, int nb
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i) x[i] = y[i];
+}
+
+// nodes of tetrahedron-vertex entry `code` for pair (a, o): loaded, sorted, degenerate groups
+// merged into their mean (Eq. tetrahedron thresholds), all in FP64
+__device__ __forceinline__ void tetra_nodes(const double* __restrict__ E, int nband, int nocc, int a, int o,
+                                            const int* __restrict__ kp, const int* __restrict__ tets, int code,
+                                            double da, double dr, double (&x)[5]) {
+    const int tt = code >> 2, jv = code & 3;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int kv = tets[4 * tt + v];
+        x[v] = E[(size_t)kp[kv] * nband + nocc + a] - E[(size_t)kv * nband + o];
+    }
+    x[4] = jv == 0 ? x[0] : jv == 1 ? x[1] : jv == 2 ? x[2] : x[3];
+    sort_merge5(x, da, dr);
 }
 
 // nodes of entry `code` for pair (a, o) relative to the pair's transition energy d0, in FP32:
@@ -675,6 +680,172 @@ __global__ void __launch_bounds__(64, sizeof(R) == 4 ? 6 : 1) k_tetra_weights(co
     }
 }
 
+// ---- metals: Fermi-surface clipping -------------------------------------------------------------
+// Pieces of a tetrahedron where the linear function with vertex values e is negative, as rows of
+// barycentric coordinates of the tetrahedron (out[p][i][j]: sub-vertex i of piece p = sum_j out
+// vertex j): none (no vertex below zero), the corner at the lowest vertex (one), a triangular
+// prism (two or three: three pieces, (A0 A1 A2 B0), (A1 A2 B0 B1), (A2 B0 B1 B2) for triangles A, B
+// with lateral edges A_i B_i), the whole (four).  Zero counts as not negative.
+__device__ int clip_negative4(const double (&e)[4], double (&out)[3][4][4]) {
+    int s[4] = {0, 1, 2, 3};
+    for (int i = 1; i < 4; ++i) {            // stable insertion sort of the vertices by e
+        const int v = s[i];
+        int j = i - 1;
+        while (j >= 0 && e[s[j]] > e[v]) { s[j + 1] = s[j]; --j; }
+        s[j + 1] = v;
+    }
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) n += e[i] < 0.0 ? 1 : 0;
+    auto unit = [](double (&r)[4], int u) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r[j] = j == u ? 1.0 : 0.0;
+    };
+    auto cut = [&](double (&r)[4], int u, int v) {   // zero of the edge u-v (e[u] < 0 <= e[v])
+        const double t = e[u] / (e[u] - e[v]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r[j] = 0.0;
+        r[u] = 1.0 - t;
+        r[v] = t;
+    };
+    auto prism = [&](double (&A)[3][4], double (&B)[3][4]) {
+        const double* rows[3][4] = {{A[0], A[1], A[2], B[0]}, {A[1], A[2], B[0], B[1]}, {A[2], B[0], B[1], B[2]}};
+        for (int p = 0; p < 3; ++p)
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) out[p][i][j] = rows[p][i][j];
+    };
+    if (n == 0) return 0;
+    if (n == 4) {
+        for (int i = 0; i < 4; ++i) unit(out[0][i], i);
+        return 1;
+    }
+    if (n == 1) {
+        unit(out[0][0], s[0]);
+        cut(out[0][1], s[0], s[1]);
+        cut(out[0][2], s[0], s[2]);
+        cut(out[0][3], s[0], s[3]);
+        return 1;
+    }
+    double A[3][4], B[3][4];
+    if (n == 2) {
+        unit(A[0], s[0]); cut(A[1], s[0], s[2]); cut(A[2], s[0], s[3]);
+        unit(B[0], s[1]); cut(B[1], s[1], s[2]); cut(B[2], s[1], s[3]);
+    } else {
+        unit(A[0], s[0]); unit(A[1], s[1]); unit(A[2], s[2]);
+        cut(B[0], s[0], s[3]); cut(B[1], s[1], s[3]); cut(B[2], s[2], s[3]);
+    }
+    prism(A, B);
+    return 3;
+}
+
+__device__ __forceinline__ double det4(const double (&m)[4][4]) {
+    const double a0 = m[2][2] * m[3][3] - m[2][3] * m[3][2], a1 = m[2][1] * m[3][3] - m[2][3] * m[3][1];
+    const double a2 = m[2][1] * m[3][2] - m[2][2] * m[3][1], a3 = m[2][0] * m[3][3] - m[2][3] * m[3][0];
+    const double a4 = m[2][0] * m[3][2] - m[2][2] * m[3][0], a5 = m[2][0] * m[3][1] - m[2][1] * m[3][0];
+    return m[0][0] * (m[1][1] * a0 - m[1][2] * a1 + m[1][3] * a2) -
+           m[0][1] * (m[1][0] * a0 - m[1][2] * a3 + m[1][3] * a4) +
+           m[0][2] * (m[1][0] * a1 - m[1][1] * a3 + m[1][3] * a5) -
+           m[0][3] * (m[1][0] * a2 - m[1][1] * a4 + m[1][2] * a5);
+}
+
+// f_z[x0..x4] in FP64 from five nodes (sorted and merged here; the series about the centre for a
+// narrow set, else the table)
+__device__ __noinline__ double2 dd_fp64_nodes(double (&x)[5], double da, double dr, double2 z) {
+    sort_merge5(x, da, dr);
+    const double c = 0.5 * (x[0] + x[4]);
+    const double2 y = make_double2(z.x - c, z.y);
+    const double spread = x[4] - x[0];
+    const double r2 = y.x * y.x + y.y * y.y;
+    if (spread * spread <= TT_TAU * TT_TAU * r2) {
+        const double t[5] = {-0.5 * spread, x[1] - c, x[2] - c, x[3] - c, 0.5 * spread};
+        double e[5];
+        esym5<double>(t, e);
+        return dd5_series<double>(e, spread, y, r2);
+    }
+    bool unused = false;
+    return dd5_table<double>(x, z, &unused);
+}
+
+// Metallic weights, FP64, one (k, a, o) per thread: for each of the 24 tetrahedra around k the part
+// where band o (at the vertex points) lies below the Fermi energy and band a (at their k + q) above
+// it, cut into pieces; a piece F (barycentric rows, volume |det F|) adds |det F| sum_i F[i][j] w_i
+// to vertex j, w_i its own vertex-i weight (the unclipped formula with D at its vertices).
+__global__ void __launch_bounds__(128) k_tetra_metal(const double* __restrict__ E, const double* __restrict__ Tw,
+                                                     int nband, int nocc, int nemp, int nk,
+                                                     const int* __restrict__ kp, const int* __restrict__ tets,
+                                                     const int* __restrict__ tetk, int nf,
+                                                     const double* __restrict__ freq, int axis, int ordering,
+                                                     double delta, double da, double dr, double fermi,
+                                                     double2* __restrict__ wout) {
+    const long long K = (long long)nk * nemp * nocc;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K) return;
+    const int o = (int)(t % nocc), a = (int)((t / nocc) % nemp), k = (int)(t / ((long long)nocc * nemp));
+    double pref = 2.0 / (double)nk;
+    if (Tw) pref *= 1.0 - Tw[(size_t)kp[k] * nband + nocc + a] * Tw[(size_t)k * nband + o];
+    const double ps = pref / 6.0;
+    for (int f = 0; f < nf; ++f) wout[(size_t)f * K + t] = make_double2(0.0, 0.0);
+    for (int s = 0; s < 24; ++s) {
+        const int code = tetk[24 * k + s];
+        const int tt = code >> 2, jv = code & 3;
+        double eo[4], ea[4], d[4], g1[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int kv = tets[4 * tt + v];
+            eo[v] = E[(size_t)kv * nband + o];
+            ea[v] = E[(size_t)kp[kv] * nband + nocc + a];
+            d[v] = ea[v] - eo[v];
+            g1[v] = eo[v] - fermi;
+        }
+        double P1[3][4][4];
+        const int n1 = clip_negative4(g1, P1);
+        for (int p1 = 0; p1 < n1; ++p1) {
+            double g2[4];
+            for (int i = 0; i < 4; ++i) {
+                g2[i] = 0.0;
+                for (int j = 0; j < 4; ++j) g2[i] += P1[p1][i][j] * (fermi - ea[j]);
+            }
+            double P2[3][4][4];
+            const int n2 = clip_negative4(g2, P2);
+            for (int p2 = 0; p2 < n2; ++p2) {
+                double F[4][4];
+                for (int i = 0; i < 4; ++i)
+                    for (int j = 0; j < 4; ++j) {
+                        double v = 0.0;
+                        for (int m = 0; m < 4; ++m) v += P2[p2][i][m] * P1[p1][m][j];
+                        F[i][j] = v;
+                    }
+                const double vol = fabs(det4(F));
+                if (vol == 0.0) continue;
+                double ds[4];
+                for (int i = 0; i < 4; ++i) {
+                    ds[i] = 0.0;
+                    for (int j = 0; j < 4; ++j) ds[i] += F[i][j] * d[j];
+                }
+                for (int f = 0; f < nf; ++f) {
+                    double2 acc = make_double2(0.0, 0.0);
+                    for (int side = 0; side < 2; ++side) {
+                        const double2 z = tetra_pole(freq, f, side, axis, ordering, delta);
+                        for (int i = 0; i < 4; ++i) {
+                            const double cf = F[i][jv];
+                            if (cf == 0.0) continue;
+                            double x[5] = {ds[0], ds[1], ds[2], ds[3], ds[i]};
+                            const double2 w = dd_fp64_nodes(x, da, dr, z);
+                            acc.x += cf * w.x;
+                            acc.y += cf * w.y;
+                        }
+                    }
+                    double2* dst = wout + (size_t)f * K + t;
+                    double2 v = *dst;
+                    v.x += vol * acc.x * ps;
+                    v.y += vol * acc.y * ps;
+                    *dst = v;
+                }
+            }
+        }
+    }
+}
+
 cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double* d_freq, double delta,
                          double da, double dr, bool fp32, double2* w, cudaStream_t st) {
     {   // series coefficients 6 / (m (m-1) (m-2) (m-3)) of the resonant path
@@ -687,6 +858,15 @@ cudaError_t launch_tetra(rp_ctx* c, int axis, int ordering, int nf, const double
         cudaError_t e = cudaMemcpyToSymbolAsync(c_bq, bq, sizeof(bq), 0, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_bqf, bqf, sizeof(bqf), 0, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
+    }
+    if (c->metal) {
+        // Fermi-surface clipping in FP64 for every tier (the split tiers convert the weights after)
+        const long long K = (long long)c->nk * c->nemp * c->nocc;
+        k_tetra_metal<<<(unsigned)((K + 127) / 128), 128, 0, st>>>(
+            (const double*)c->d_energy.p, c->T.empty() ? nullptr : (const double*)c->d_T.p, c->nband, c->nocc,
+            c->nemp, c->nk, (const int*)c->plan.d_kp.p, (const int*)c->d_tets.p, (const int*)c->d_tetk.p, nf,
+            d_freq, axis, ordering, delta, da, dr, c->efermi, w);
+        return cudaGetLastError();
     }
     // work list of the FP32 pass: up to a quarter of all (pair, frequency) (overflow is evaluated in
     // place); 16-byte items after a 16-byte counter

@@ -8,6 +8,8 @@ It holds no step of the polarization / screened-interaction method itself.
 from .epm import (HARTREE_EV, Cell, Bands, fcc_cell, sc_cell, kmesh_frac,
                   psi_sphere, make_bands)
 from .configs import CONFIGS, Workload, make_workload
+from .metal import metal_bands, metal_view
 
 __all__ = ["HARTREE_EV", "Cell", "Bands", "fcc_cell", "sc_cell", "kmesh_frac",
-           "psi_sphere", "make_bands", "CONFIGS", "Workload", "make_workload"]
+           "psi_sphere", "make_bands", "CONFIGS", "Workload", "make_workload",
+           "metal_bands", "metal_view"]

@@ -239,10 +239,12 @@ def make_bands(cell, kmesh, ecut_psi, nband, pot, seed, workers=None, symmetry=F
     if work > 2e10 and workers > 1:
         import concurrent.futures as cf
         import multiprocessing as mp
-        # one BLAS thread per worker process (spawned children read these at start-up)
+        # the cores shared out over the worker processes (one BLAS thread each when there are more
+        # jobs than cores; spawned children read these at start-up)
+        nthr = max(1, (os.cpu_count() or 1) // max(1, min(workers, len(jobs))))
         saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
         for v in saved:
-            os.environ[v] = "1"
+            os.environ[v] = str(nthr)
         # fork is safe (and needs no importable __main__) only while no CUDA context can exist in
         # this process: spawn once torch has initialised CUDA or any library has loaded the driver
         cuda_up = _cuda_in_process()

@@ -87,3 +87,9 @@ def test_batched_build_and_dyson_against_single_q(batched, picks):
         W1, t1 = one.rp_solve_w(qs[i], chi)
         assert np.all(_rel_fro(W, W1) < 1e-13) and np.array_equal(tail, t1)
         one.close()
+    # device buffers: the packed list-kernel solve over all six q against the host-buffer results
+    dev = [torch.from_numpy(c).cuda() for c in outs]
+    dW = ctx.rp_solve_w_batched(qs, dev, ecut_eps=cuts)
+    ctx.rp_check_numeric()
+    for (W, _), d in zip(Ws, dW):
+        assert np.all(_rel_fro(d.cpu().numpy(), W) < 1e-13)

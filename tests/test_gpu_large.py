@@ -28,7 +28,9 @@ FP64_TOL = 1e-11
 
 @pytest.fixture(scope="module")
 def large_sub():
-    return workload("large", nocc=4, nemp=8)
+    # the workload's own band set (the lowest 4 + 8 of its 256 + 1024 bands)
+    from dataclasses import replace
+    return replace(workload("large"), nocc=4, nemp=8)
 
 
 @pytest.fixture(scope="module")
@@ -62,8 +64,13 @@ def test_large_chi0_against_oracle(large_sub, large_ref, precision, tol):
     wl = large_sub
     G, chi_ref = large_ref
     ctx = rp.context_for(wl)
+    ctx.rp_profile_enable(True)
     got = ctx.rp_build_chi0(wl.q[0], rp.RP_AXIS_IMAG, rp.RP_TIME_ORDERED, wl.freq, wl.delta, precision)
+    _, launches = ctx.rp_profile_read()
     ctx.close()
+    if precision == rp.RP_BF16X3:
+        # the 48-point plane kernels ran: one block of all 8 k points, plane sums + x read-out
+        assert launches[1] == 2
     assert got.shape == chi_ref.shape
     assert np.all(_rel_fro(got, chi_ref) < tol)
 
@@ -76,7 +83,10 @@ def test_large_empty_band_chunks_bit_identical(large_sub):
     # one k point's plane sums: 4 x 8 pairs x 48 x 23 x 23 complex floats = 6.5 MB; a 2 MB budget
     # takes the empty bands two at a time (four chunks)
     ctx.rp_set_pair_budget(2 << 20)
+    ctx.rp_profile_enable(True)
     chunked = ctx.rp_build_chi0(q, rp.RP_AXIS_IMAG, rp.RP_TIME_ORDERED, wl.freq, wl.delta, rp.RP_BF16X3)
+    _, launches = ctx.rp_profile_read()
+    assert launches[1] == 2 * 4 * 8            # two launches per chunk, four chunks per k point, 8 k
     with pytest.raises(rp.RPError) as e:
         ctx.rp_set_pair_budget(0)
     assert e.value.code == rp.RP_ERR_ARG

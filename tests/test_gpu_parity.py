@@ -264,6 +264,35 @@ def test_bad_pivot_in_one_of_several_frequencies_cooperative():
     assert np.allclose(W.cpu().numpy()[1], np.diag(vs * vs), rtol=1e-14, atol=0)
 
 
+def test_bad_pivot_in_a_batched_device_solve():
+    """The batched Dyson solve on device buffers packs the (q, w) matrices of several q into
+    cooperative launches of the list kernel: one matrix with a non-finite chi0 is reported as
+    RP_ERR_NUMERIC, and every other matrix of the batch (of both q, sharing the launch and its
+    barriers) is still exact (chi0 = 0 gives W = v)."""
+    from synth.configs import _mid_gap_cutoff
+    wl = workload("tiny")
+    b = wl.bands
+    qs = np.array([wl.q[0], [0.25, 0.25, 0.0]])
+    cuts = np.array([_mid_gap_cutoff(wl.cell.recip, q, t, exclude_zero=True) for q, t in zip(qs, (150, 90))])
+    ctx = rp.Context(b.cell.lat, b.kmesh, wl.fft, b.ecut_psi, float(cuts[0]))
+    nb = wl.nocc + wl.nemp
+    ctx.load_bands(wl.nocc, b.npw, b.miller, b.coef[:, :nb], b.energy[:, :nb])
+    Gs = [OL.eps_sphere(wl.cell.lat, q, c) for q, c in zip(qs, cuts)]
+    chis = [torch.zeros((3, len(G), len(G)), dtype=torch.complex128, device="cuda") for G in Gs]
+    chis[1][2, :, 0] = float("nan")
+    Ws = ctx.rp_solve_w_batched(qs, chis, ecut_eps=cuts)
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_check_numeric()
+    assert e.value.code == rp.RP_ERR_NUMERIC
+    for i, (q, G, W) in enumerate(zip(qs, Gs, Ws)):
+        vs = OD.coulomb_sqrt(wl.cell.lat, q, G)
+        Wh = W.cpu().numpy()
+        for f in range(3):
+            if (i, f) != (1, 2):
+                assert np.allclose(Wh[f], np.diag(vs * vs), rtol=1e-14, atol=0)
+    ctx.close()
+
+
 def test_contraction_wait_that_gives_up_is_reported():
     """With the wait limit set to zero the BF16x3 contraction's pipeline waits give up at once:
     the kernel returns through its teardown (in-flight copies and MMAs drained with the fixed
@@ -462,6 +491,13 @@ def test_batched_q_with_uneven_spheres_tiny():
         assert np.all(_rel_fro(W, W_ref) < 1e-11)
         T = OL.tail_sphere(wl.cell.lat, q, cut, wl.bands.ecut_psi)
         assert np.allclose(tail, OD.tail(wl.cell.lat, q, T), rtol=1e-14, atol=0)
+    # the same batch on device buffers: the (q, w) matrices of all three q in one packed launch of
+    # the list kernel, the same W as the per-q host-buffer solves
+    dev = [torch.from_numpy(c).cuda() for c in chis]
+    dW = ctx.rp_solve_w_batched(qs, dev, ecut_eps=cuts)
+    ctx.rp_check_numeric()
+    for (W, _), d in zip(ws, dW):
+        assert np.all(_rel_fro(d.cpu().numpy(), W) < 1e-13)
     assert len(set(sizes)) == 3
 
 
