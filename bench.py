@@ -170,6 +170,12 @@ def subset_k(nk, n=4, seed=2001_02351):
     return sorted(int(k) for k in rng.choice(nk, size=min(n, nk), replace=False))
 
 
+def hermitian_eps(wl):
+    """eps = 1 - v^1/2 chi0 v^1/2 is Hermitian positive definite for the time-ordered chi0 of the
+    imaginary axis: the Dyson step may take the lower-triangle sweep."""
+    return wl.axis == "imag" and wl.ordering == "time"
+
+
 def sample_emp(wl, pairs=8192):
     """Empty bands of a bounded oracle sample: the lowest ones, about `pairs` pairs per k point on a
     48^3 grid (fewer on larger grids: the oracle's cost per pair grows with the grid)."""
@@ -329,6 +335,7 @@ def run_batched(args):
     prec = {"fp64": rp.RP_FP64_NATIVE, "bf16x3": rp.RP_BF16X3, "tf32x3": rp.RP_TF32X3}[args.precision]
     axis = rp.RP_AXIS_IMAG if wl.axis == "imag" else rp.RP_AXIS_REAL
     ctx = rp.context_for(wl)
+    ctx.rp_set_dyson_hermitian(hermitian_eps(wl))
     qs, cuts = wl.q, wl.ecut_eps
     nf = len(wl.freq)
     nk = wl.bands.kfrac.shape[0]
@@ -369,7 +376,8 @@ def run_batched(args):
            "data": "synthetic (seeded empirical-pseudopotential bands)",
            "config": {"workload": args.workload, "nq": len(qs), "ng_min": min(ngs), "ng_max": max(ngs),
                       "pairs_K": K, "nfreq": nf, "nk": nk, "nocc": wl.nocc, "nemp": wl.nemp, "axis": wl.axis,
-                      "precision": args.precision, "l2": "inputs larger than L2", "parallelism": "replicas x1"},
+                      "precision": args.precision, "l2": "inputs larger than L2", "parallelism": "replicas x1",
+                      "dyson": "hermitian sweep" if hermitian_eps(wl) else "pivoted Gauss-Jordan"},
            "stages_ms_per_step": {n: stage_ms[i] / args.steps for i, n in enumerate(STAGES)},
            "gpu_launches": int(launches.sum()),
            "roofline": {"bound": "tensor", "kernel": "chi0 contraction", "achieved": achieved, "peak": peak,
@@ -425,6 +433,7 @@ def main():
     axis = rp.RP_AXIS_IMAG if wl.axis == "imag" else rp.RP_AXIS_REAL
     ordering = rp.RP_TIME_ORDERED if wl.ordering == "time" else rp.RP_RETARDED
     ctx = rp.context_for(wl)
+    ctx.rp_set_dyson_hermitian(hermitian_eps(wl))
     G, tl = ctx.rp_sphere_size(q)
     ng, nf = len(G), len(wl.freq)
     nk = wl.bands.kfrac.shape[0]
@@ -537,6 +546,7 @@ def main():
                       "nocc": wl.nocc, "nemp": wl.nemp, "npw_max": int(wl.bands.npw.max()), "fft": list(wl.fft),
                       "axis": wl.axis, "precision": args.precision,
                       "l2": "inputs larger than L2 (bands and per-step scratch > 129 MB)",
+                      "dyson": "hermitian sweep" if hermitian_eps(wl) else "pivoted Gauss-Jordan",
                       "parallelism": f"k shards x{ws}" if shard_k else f"replicas x{ws}"},
            "stages_ms_per_step": {n: stage_ms[i] / args.steps for i, n in enumerate(STAGES)},
            "gpu_launches": int(launches.sum()), "roofline": roof, "clocks": clk}
@@ -597,6 +607,7 @@ def main():
         ectx = rp.Context(b.cell.lat, b.kmesh, wl.fft, b.ecut_psi, float(wl.ecut_eps[0]))
         if tile:
             ectx.rp_set_contraction_tile(ng, tile)
+        ectx.rp_set_dyson_hermitian(hermitian_eps(wl))
         del ctx                                            # one band set on the device at a time
 
         def e2e_step():

@@ -305,6 +305,15 @@ int rp_set_contraction_tile(rp_ctx* ctx, int ng, int bn);
  *   the tcgen05 probe's bounded wait gave up. */
 int rp_probe_peaks(double* out);
 
+/* rp_set_dyson_hermitian -- on != 0: the Dyson steps of the context (rp_solve_w, rp_solve_w_batched,
+ *   rp_solve_w_q0) take eps = 1 - v^1/2 chi0 v^1/2 as Hermitian positive definite, which it is on
+ *   the imaginary axis (chi0 Hermitian, negative semidefinite; Eq. epsGG), and invert it by the sweep
+ *   operator on its lower triangle without pivoting (half the FP64 work of the pivoted
+ *   Gauss-Jordan solve; the upper triangle of chi0 is not read).  A pivot that is not positive
+ *   (eps not positive definite, e.g. chi0 of the real axis) is reported like a bad pivot
+ *   (RP_ERR_NUMERIC, that frequency's W unspecified).  on = 0: pivoted Gauss-Jordan (the default). */
+int rp_set_dyson_hermitian(rp_ctx* ctx, int on);
+
 /* rp_set_fermi -- metals (Sec. 2.3; Eq. Xakqbk with the occupations of a metal): with a Fermi energy
  *   set, the tetrahedron weights of a pair (a, o) integrate each tetrahedron only over its part where
  *   band o (at k) lies below efermi_ha and band a (at k + q) above it, both interpolated linearly

@@ -29,7 +29,8 @@ EXPORTS = ["rp_setup_cell", "rp_load_bands", "rp_sphere_size", "rp_pair_density"
            "rp_build_chi0_batched", "rp_solve_w_batched", "rp_set_wait_limit", "rp_set_pair_budget", "rp_contract_chi0_static_status",
            "rp_build_chi0_kset", "rp_tune_contraction", "rp_set_contraction_tile",
            "rp_load_wannier", "rp_interaction", "rp_build_chi0_q0", "rp_solve_w_q0", "rp_optics",
-           "rp_rotate_q", "rp_probe_peaks", "rp_plasma", "rp_transform_grid", "rp_set_fermi"]
+           "rp_rotate_q", "rp_probe_peaks", "rp_plasma", "rp_transform_grid", "rp_set_fermi",
+           "rp_set_dyson_hermitian"]
 
 
 class RPError(RuntimeError):
@@ -72,6 +73,7 @@ def library():
         "rp_set_wait_limit": (I, [P, LL]),
         "rp_set_pair_budget": (I, [P, LL]),
         "rp_set_fermi": (I, [P, ctypes.c_double]),
+        "rp_set_dyson_hermitian": (I, [P, I]),
         "rp_build_chi0_kset": (I, [P, P, I, P, I, I, I, P, D, D, D, I, P, I, P]),
         "rp_tune_contraction": (I, [P, I, LL, I, ctypes.POINTER(I), P]),
         "rp_set_contraction_tile": (I, [P, I, I]),
@@ -464,6 +466,10 @@ class Context:
     def rp_set_fermi(self, efermi=float("nan")):
         """Fermi energy (Ha) of a metal: Fermi-surface clipping of the weights; NaN turns it off."""
         self._check(self._lib.rp_set_fermi(self._h, float(efermi)))
+
+    def rp_set_dyson_hermitian(self, on=True):
+        """Dyson steps by the Hermitian positive definite sweep (imaginary axis) or pivoted Gauss-Jordan."""
+        self._check(self._lib.rp_set_dyson_hermitian(self._h, 1 if on else 0))
 
     def rp_set_pair_budget(self, nbytes):
         self._check(self._lib.rp_set_pair_budget(self._h, int(nbytes)))

@@ -849,6 +849,12 @@ int rp_tune_contraction(rp_ctx* c, int ng, long long K, int nfreq, int* bn_out, 
     return RP_OK;
 }
 
+int rp_set_dyson_hermitian(rp_ctx* c, int on) {
+    if (!c) return RP_ERR_ARG;
+    c->dyson_herm = on != 0;
+    return RP_OK;
+}
+
 int rp_set_fermi(rp_ctx* c, double efermi_ha) {
     if (!c) return RP_ERR_ARG;
     if (std::isnan(efermi_ha)) {
@@ -904,7 +910,7 @@ static int solve_w(rp_ctx* c, const double q[3], double ecut_eps, int nfreq, con
     }
     if ((s = ensure(c, c->s_dy, dyson_scratch_bytes(ng, nfreq)))) return s;
     prof_begin(c, 4, st);
-    cudaError_t e = launch_dyson(dchi, (const double*)c->plan.d_vs.p, ng, nfreq, dW, c->s_dy.p, (int*)c->d_err.p, st);
+    cudaError_t e = launch_dyson(dchi, (const double*)c->plan.d_vs.p, ng, nfreq, dW, c->s_dy.p, c->dyson_herm, (int*)c->d_err.p, st);
     prof_end(c, 4, st, 1);
     if (e != cudaSuccess) return cuda_fail(c, e, "Dyson solve");
     if (tail_out && c->plan.ntail > 0) {
@@ -979,7 +985,7 @@ int rp_solve_w_q0(rp_ctx* c, int nfreq, const double* chi0, double* W_out, doubl
     }
     if ((s = ensure(c, c->s_dy, dyson_scratch_bytes(n, nfreq)))) return s;
     prof_begin(c, 4, st);
-    e = launch_dyson(dchi, (const double*)c->s_io3.p, n, nfreq, dW, c->s_dy.p, (int*)c->d_err.p, st);
+    e = launch_dyson(dchi, (const double*)c->s_io3.p, n, nfreq, dW, c->s_dy.p, c->dyson_herm, (int*)c->d_err.p, st);
     prof_end(c, 4, st, 1);
     if (e != cudaSuccess) return cuda_fail(c, e, "Dyson solve");
     if (tail_out && c->plan.ntail > 0) {
@@ -1277,7 +1283,7 @@ static int solve_w_list(rp_ctx* c, int nq, const double* q_frac, const double* c
     int cta0 = 0;
     for (size_t l = 0; l + 1 < lb.size(); ++l) {
         const int nmax = ng[order[lb[l]] / nfreq];
-        e = launch_dyson_list(dmats, dmap + cta0, lcount[l], nmax, (int*)c->d_err.p, st);
+        e = launch_dyson_list(dmats, dmap + cta0, lcount[l], nmax, c->dyson_herm, (int*)c->d_err.p, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "batched Dyson solve");
         cta0 += lcount[l];
     }

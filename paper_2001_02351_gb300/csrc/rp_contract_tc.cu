@@ -43,8 +43,10 @@ namespace rp {
 #define TC_GN 32                // G' per tile and frequency
 #define TC_BK 64                // reals per stage
 #define TC_FLUSH_STAGES 128     // stages per FP32 accumulation window (8192 reals)
-#define TC_THREADS 448
-#define TC_NBUILD 256           // builder threads (warps 2-9); epilogue = warps 10-13
+#define TC_BUILD_SPLIT 0        // 1: each tile has its own TC_NBUILD / 2 builder threads
+#define TC_NBUILD 256           // builder threads (warps 2 ..), one 16-B chunk of a stage's rows each
+#define TC_EPI_WARPS 4          // epilogue warps (4: one per TMEM lane quarter; 8: two, half the columns each)
+#define TC_THREADS (64 + TC_NBUILD + 32 * TC_EPI_WARPS)
 #define TC_TMEM_COLS 512        // the accumulators of the two tiles, BN columns each, 256 apart
 #define TC_NF 4                 // frequencies per job (two tiles of two)
 
@@ -243,10 +245,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(empty(s), TC_NBUILD + 1);
         }
         for (int t = 0; t < 2; ++t) {
-            mbar_init(bready(t), TC_NBUILD);
+            mbar_init(bready(t), TC_BUILD_SPLIT ? TC_NBUILD / 2 : TC_NBUILD);
             mbar_init(bfree(t), 1);
             mbar_init(accf(t), 1);
-            mbar_init(acce(t), 128);
+            mbar_init(acce(t), 32 * TC_EPI_WARPS);
         }
         mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -380,7 +382,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp < 2 + TC_NBUILD / 32) {
         // ---------------- builders of the weighted rows (TC_NBUILD threads, one 16-B chunk each) ----
-        const int tid = threadIdx.x - 64;
+        const int tid = (threadIdx.x - 64) % 256;
+        const int tsel = TC_BUILD_SPLIT ? (threadIdx.x - 64) / 256 : -1;   // the one tile built (split)
         const int r = tid >> 3, c = tid & 7;
         long long sg = 0, cs[2] = {0, 0};
         bool ok = true;
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mi[i] = hh.y + ll.y;
                 }
                 for (int t = 0; t < 2; ++t) {
-                    if (!lv[t]) continue;
+                    if (!lv[t] || (TC_BUILD_SPLIT && t != tsel)) continue;
                     if (!(ok = mbar_wait(bfree(t), (uint32_t)((cs[t] & 1) ^ 1), err, 122, lim))) break;
                     ++cs[t];
                     unsigned char* bhi = smem + L::B0 + t * 2 * TC_B_BYTES;
@@ -454,6 +457,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         constexpr bool REM = (BN % 32) == 16;
         static_assert(BN % 32 == 0 || REM, "BN is a multiple of 16");
         const int q4 = warp & 3;
+        // columns of this warp: chunks [c0e, c1e) (and the 16-column remainder with the second half)
+        const int half = TC_EPI_WARPS == 8 ? (warp - (2 + TC_NBUILD / 32)) / 4 : -1;
+        const int c0e = half == 1 ? NCH / 2 : 0, c1e = half == 0 ? NCH / 2 : NCH;
+        const bool rem_here = REM && half != 0;
         long long cj[2] = {0, 0};
         bool ok = true;
         double* chi = reinterpret_cast<double*>(args.chi);
@@ -474,10 +481,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t src = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(t * 256);
 #pragma unroll 1
-                for (int ch = 0; ch < NCH; ++ch) {
+                for (int ch = c0e; ch < c1e; ++ch) {
                     uint32_t v[32];
                     tmem_ld32(src + (uint32_t)(ch * 32), v);
-                    if (!REM && ch == NCH - 1) {
+                    if (!rem_here && ch == c1e - 1) {
                         // the accumulator is read: the MMA of the next job may overwrite it
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                         mbar_arrive(acce(t));
@@ -489,7 +496,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 atomicAdd(out + (size_t)(ch * 32 + j) * ldo, (double)__uint_as_float(v[j]));
                     }
                 }
-                if constexpr (REM) {
+                if (rem_here) {
                     constexpr int ch = NCH;
                     uint32_t v[16];
                     tmem_ld16(src + (uint32_t)(ch * 32), v);

@@ -321,14 +321,146 @@ __device__ __forceinline__ void dyson_coop_body(cooperative_groups::grid_group& 
     }
 }
 
+// Hermitian positive definite eps (chi0 Hermitian and negative semidefinite, as on the imaginary
+// axis): the sweep operator on the lower triangle, no pivoting.  Sweeping k maps d = A_kk,
+// c = column k (c_i = A_ik, Hermitian: A_kj = conj(c_j)) to
+//   A_kk = -1/d,   A_ik = c_i / d,   A_kj = conj(c_j) / d,   A_ij -= c_i conj(c_j) / d  (i, j != k),
+// which keeps the matrix Hermitian; after all n sweeps it holds -eps^-1, so W = -v^1/2 A v^1/2.
+// Half the flops of Gauss-Jordan (the lower triangle only).  The columns are split among the P CTAs
+// by equal element counts of the lower triangle.  Column k of step k is published by every CTA
+// (row k of its own columns, conjugated) and by the owner of column k (its part from the diagonal
+// down) after the CTA's update of step k - 1; one grid barrier closes each step (n + 1 in all,
+// whatever the data).  A pivot d that is not positive and finite (eps not positive definite) marks
+// the matrix bad: its CTAs skip the arithmetic and the flag is raised.
+__device__ __forceinline__ int herm_split(int n, int P, int p) {
+    // smallest c with (elements of columns 0 .. c-1 of the lower triangle) >= p / P of all
+    const long long total = (long long)n * (n + 1) / 2;
+    const long long target = total * p / P;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        const long long el = (long long)mid * n - (long long)mid * (mid - 1) / 2;
+        if (el >= target) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void dyson_herm_body(cooperative_groups::grid_group& grid, const double2* __restrict__ X,
+                                                const double* __restrict__ vs, int n, int P, int pc,
+                                                double2* __restrict__ A, double2* __restrict__ cb, int nsteps,
+                                                int* err_flag, unsigned char* smem) {
+    double2* cc = (double2*)smem;          // column k of the step (all rows)
+    double2* uu = cc + n;                  // c_i / d
+    const int c0 = herm_split(n, P, pc), c1 = herm_split(n, P, pc + 1);
+    const int w = c1 - c0;
+    const int tid = threadIdx.x;
+    // this CTA's block: rows c0 .. n-1 of its columns (entries above the diagonal skipped)
+    const int di = w > 0 ? DC_THREADS / w : 0, dc = w > 0 ? DC_THREADS % w : 0;
+    if (w > 0)
+        for (int i = c0 + tid / w, cq = tid % w; i < n;) {
+            const int j = c0 + cq;
+            if (j <= i) {
+                const double sc = vs[i] * vs[j];
+                const double2 x = X[(size_t)i * n + j];
+                A[(size_t)i * n + j] = make_double2((i == j ? 1.0 : 0.0) - sc * x.x, -sc * x.y);
+            }
+            i += di;
+            cq += dc;
+            if (cq >= w) { cq -= w; ++i; }
+        }
+    __syncthreads();
+    if (c0 == 0 && w > 0)                  // column 0 for step 0
+        for (int i = tid; i < n; i += DC_THREADS) cb[i] = A[(size_t)i * n];
+    grid.sync();
+    bool bad = false;
+    for (int k = 0; k < nsteps; ++k) {
+        const int cur = k & 1, nxt = cur ^ 1;
+        if (k < n && !bad) {
+            for (int i = tid; i < n; i += DC_THREADS) cc[i] = __ldcg(&cb[(size_t)cur * n + i]);
+            __syncthreads();
+            const double d = cc[k].x;
+            if (!(d > 0.0) || !isfinite(d)) bad = true;        // the same value in every CTA of the matrix
+        }
+        if (k < n && !bad) {
+            const double inv = 1.0 / cc[k].x;
+            for (int i = tid; i < n; i += DC_THREADS) uu[i] = make_double2(cc[i].x * inv, cc[i].y * inv);
+            __syncthreads();
+            if (w > 0)
+                for (int i = c0 + tid / w, cq = tid % w; i < n;) {
+                    int ei[DC_UNROLL], ej[DC_UNROLL];
+                    double2 a[DC_UNROLL];
+#pragma unroll
+                    for (int q = 0; q < DC_UNROLL; ++q) {
+                        const int j = c0 + cq;
+                        const bool act = i < n && j <= i;
+                        ei[q] = act ? i : -1;
+                        ej[q] = j;
+                        a[q] = (act && i != k && j != k) ? A[(size_t)i * n + j] : make_double2(0.0, 0.0);
+                        i += di;
+                        cq += dc;
+                        if (cq >= w) { cq -= w; ++i; }
+                    }
+#pragma unroll
+                    for (int q = 0; q < DC_UNROLL; ++q) {
+                        const int ii = ei[q], jj = ej[q];
+                        if (ii < 0) continue;
+                        double2 v;
+                        if (ii == k && jj == k) v = make_double2(-inv, 0.0);
+                        else if (ii == k) v = make_double2(uu[jj].x, -uu[jj].y);          // conj(c_j) / d
+                        else if (jj == k) v = uu[ii];                                      // c_i / d
+                        else v = cfms(a[q], uu[ii], make_double2(cc[jj].x, -cc[jj].y));    // - c_i conj(c_j) / d
+                        A[(size_t)ii * n + jj] = v;
+                    }
+                }
+            __syncthreads();
+            // publish column k + 1: row k + 1 of this CTA's columns left of it (conjugated), and the
+            // owner of column k + 1 its entries from the diagonal down
+            const int kn = k + 1;
+            if (kn < n) {
+                for (int j = c0 + tid; j < c1 && j < kn; j += DC_THREADS) {
+                    const double2 v = A[(size_t)kn * n + j];
+                    cb[(size_t)nxt * n + j] = make_double2(v.x, -v.y);
+                }
+                if (kn >= c0 && kn < c1)
+                    for (int i = kn + tid; i < n; i += DC_THREADS) cb[(size_t)nxt * n + i] = A[(size_t)i * n + kn];
+            }
+        }
+        grid.sync();
+    }
+    if (bad) {
+        if (tid == 0 && pc == 0) atomicOr(err_flag, 1);
+        return;
+    }
+    // W = -v^1/2 A v^1/2 on this CTA's columns, both triangles (the upper one from the lower)
+    if (w > 0)
+        for (int i = c0 + tid / w, cq = tid % w; i < n;) {
+            const int j = c0 + cq;
+            if (j <= i) {
+                const double sc = -vs[i] * vs[j];
+                const double2 a = A[(size_t)i * n + j];
+                const double2 v = make_double2(a.x * sc, a.y * sc);
+                A[(size_t)i * n + j] = v;
+                if (i != j) A[(size_t)j * n + i] = make_double2(v.x, -v.y);
+            }
+            i += di;
+            cq += dc;
+            if (cq >= w) { cq -= w; ++i; }
+        }
+}
+
 __global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __restrict__ chi,
                                                            const double* __restrict__ vs, int n, int P,
                                                            double2* __restrict__ Wout,
                                                            double2* __restrict__ colbuf, int* __restrict__ ibuf,
-                                                           int* err_flag) {
+                                                           int herm, int* err_flag) {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     extern __shared__ unsigned char smem[];
     const int f = blockIdx.x / P, pc = blockIdx.x % P;
+    if (herm) {
+        dyson_herm_body(grid, chi + (size_t)f * n * n, vs, n, P, pc, Wout + (size_t)f * n * n,
+                        colbuf + (size_t)f * 2 * n, n, err_flag, smem);
+        return;
+    }
     dyson_coop_body(grid, chi + (size_t)f * n * n, vs, n, P, pc, Wout + (size_t)f * n * n, colbuf + (size_t)f * 2 * n,
                     ibuf + (size_t)f * (n + 2), n, err_flag, smem);
 }
@@ -336,12 +468,16 @@ __global__ void __launch_bounds__(DC_THREADS) k_dyson_coop(const double2* __rest
 // matrices of several sizes in one cooperative launch (the (q, w) members of a batch): CTA b works
 // on matrix map[b].x as its CTA map[b].y; every CTA passes nsteps = the largest n barriers
 __global__ void __launch_bounds__(DC_THREADS) k_dyson_list(const DysonMat* __restrict__ mats,
-                                                           const int2* __restrict__ map, int nsteps,
+                                                           const int2* __restrict__ map, int nsteps, int herm,
                                                            int* err_flag) {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     extern __shared__ unsigned char smem[];
     const int2 mp = map[blockIdx.x];
     const DysonMat m = mats[mp.x];
+    if (herm) {
+        dyson_herm_body(grid, m.chi, m.vs, m.n, m.P, mp.y, m.W, m.cb, nsteps, err_flag, smem);
+        return;
+    }
     dyson_coop_body(grid, m.chi, m.vs, m.n, m.P, mp.y, m.W, m.cb, m.ib, nsteps, err_flag, smem);
 }
 
@@ -358,13 +494,13 @@ int dyson_list_slots(int nmax) {
     return per_sm * nsm;
 }
 
-cudaError_t launch_dyson_list(const DysonMat* d_mats, const int2* d_map, int nblocks, int nmax, int* err_flag,
-                              cudaStream_t st) {
+cudaError_t launch_dyson_list(const DysonMat* d_mats, const int2* d_map, int nblocks, int nmax, bool herm,
+                              int* err_flag, cudaStream_t st) {
     const size_t smem = (size_t)nmax * (2 * sizeof(double2) + sizeof(int));
     cudaError_t e = cudaFuncSetAttribute(k_dyson_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int nsteps = nmax;
-    void* args[] = {(void*)&d_mats, (void*)&d_map, (void*)&nsteps, (void*)&err_flag};
+    int nsteps = nmax, hm = herm ? 1 : 0;
+    void* args[] = {(void*)&d_mats, (void*)&d_map, (void*)&nsteps, (void*)&hm, (void*)&err_flag};
     return cudaLaunchCooperativeKernel((const void*)k_dyson_list, dim3(nblocks), dim3(DC_THREADS), args, smem, st);
 }
 
@@ -374,7 +510,7 @@ size_t dyson_scratch_bytes(int ng, int nf) {
 }
 
 cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W, void* scratch,
-                         int* err_flag, cudaStream_t st) {
+                         bool herm, int* err_flag, cudaStream_t st) {
     const size_t smem = (size_t)ng * (2 * sizeof(double2) + sizeof(int));
     {   // cooperative form over the whole GPU when it fits
         int dev = 0, nsm = 0, per_sm = 0;
@@ -402,8 +538,9 @@ cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, d
                     double2* cb_ = cb_all + (size_t)f0 * 2 * ng;
                     int* ib_ = ib_all + (size_t)f0 * (ng + 2);
                     int* err_ = err_flag;
+                    int hm = herm ? 1 : 0;
                     void* args[] = {(void*)&chi_, (void*)&vs_, (void*)&n_, (void*)&P_, (void*)&W_,
-                                    (void*)&cb_, (void*)&ib_, (void*)&err_};
+                                    (void*)&cb_, (void*)&ib_, (void*)&hm, (void*)&err_};
                     e = cudaLaunchCooperativeKernel((const void*)k_dyson_coop, dim3(fg * P_), dim3(DC_THREADS), args,
                                                     smem, st);
                     if (e != cudaSuccess && f0 > 0) return e;     // a group already ran: report, no fallback

@@ -112,6 +112,7 @@ struct rp_ctx {
     unsigned long long wait_ns = 2000000000ULL;   // limit of a bounded device wait (rp_set_wait_limit)
     size_t pair_budget = (size_t)16 << 30;        // plane-sum scratch of the pair stage (rp_set_pair_budget)
     bool metal = false;                           // Fermi-surface clipping of the weights (rp_set_fermi)
+    bool dyson_herm = false;                      // Hermitian positive definite Dyson sweep (rp_set_dyson_hermitian)
     double efermi = 0.0;
     std::map<int, int> tile_bn;                   // NG -> raw rows per tile of the BF16x3 contraction
                                                   // (rp_tune_contraction / rp_set_contraction_tile)
@@ -191,12 +192,13 @@ cudaError_t launch_contract_tf32x3(const void* M, bool m32, long long ldm, long 
 // resident CTAs of the list kernel for matrices of at most nmax rows (0: not available)
 int dyson_list_slots(int nmax);
 // one cooperative launch of nblocks CTAs over a list of matrices (d_map[b] = {matrix, CTA of it})
-cudaError_t launch_dyson_list(const DysonMat* d_mats, const int2* d_map, int nblocks, int nmax, int* err_flag,
-                              cudaStream_t st);
+// (herm: eps Hermitian positive definite, the lower-triangle sweep without pivoting)
+cudaError_t launch_dyson_list(const DysonMat* d_mats, const int2* d_map, int nblocks, int nmax, bool herm,
+                              int* err_flag, cudaStream_t st);
 // Dyson step; scratch: dyson_scratch_bytes(ng, nf) of device memory (NULL: one CTA per frequency)
 size_t dyson_scratch_bytes(int ng, int nf);
 cudaError_t launch_dyson(const double2* chi, const double* vs, int ng, int nf, double2* W, void* scratch,
-                         int* err_flag, cudaStream_t st);
+                         bool herm, int* err_flag, cudaStream_t st);
 // head row at q -> 0: u_b = qhat.p_b / D_b of the pairs of k in [k0, k0 + nkb) into M[col0 + b] (complex
 // float when fp32, else complex double)
 cudaError_t launch_head_row(rp_ctx* c, int k0, int nkb, const double qhat[3], bool fp32, void* M, long long col0,

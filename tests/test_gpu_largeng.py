@@ -72,3 +72,8 @@ def test_dyson_ng_about_4000(big_cell):
     W_ref = OD.screened(chi, vs)
     assert np.all(_rel_fro(W, W_ref) < 1e-11)
     assert np.allclose(tail, OD.tail(cell.lat, q, T), rtol=1e-14, atol=0)
+    # the Hermitian positive definite sweep (eps >= 1 here) at the same size
+    ctx.rp_set_dyson_hermitian(True)
+    Wh, _ = ctx.rp_solve_w(q, chi)
+    ctx.rp_set_dyson_hermitian(False)
+    assert np.all(_rel_fro(Wh, W_ref) < 1e-11)

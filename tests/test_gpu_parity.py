@@ -264,6 +264,60 @@ def test_bad_pivot_in_one_of_several_frequencies_cooperative():
     assert np.allclose(W.cpu().numpy()[1], np.diag(vs * vs), rtol=1e-14, atol=0)
 
 
+def test_dyson_hermitian_sweep():
+    """rp_set_dyson_hermitian: the lower-triangle sweep without pivoting (eps Hermitian positive
+    definite on the imaginary axis) against the oracle and the pivoted solve, on host buffers, on
+    device buffers and in a packed batched launch over three q; a frequency whose eps is not positive
+    definite is reported as RP_ERR_NUMERIC while the others stay exact."""
+    from synth.configs import _mid_gap_cutoff
+    wl = workload("tiny")
+    b = wl.bands
+    q = wl.q[0]
+    cut = _mid_gap_cutoff(wl.cell.recip, q, 150, exclude_zero=True)
+    ctx = rp.Context(b.cell.lat, b.kmesh, wl.fft, b.ecut_psi, cut)
+    nb = wl.nocc + wl.nemp
+    ctx.load_bands(wl.nocc, b.npw, b.miller, b.coef[:, :nb], b.energy[:, :nb])
+    G = OL.eps_sphere(wl.cell.lat, q, cut)
+    vs = OD.coulomb_sqrt(wl.cell.lat, q, G)
+    chi = ctx.rp_build_chi0(q, _axis(wl), _ordering(wl), wl.freq, wl.delta, rp.RP_FP64_NATIVE)
+    W_gj, _ = ctx.rp_solve_w(q, chi)
+    W_ref = OD.screened(chi, vs)
+    ctx.rp_set_dyson_hermitian(True)
+    W_h, _ = ctx.rp_solve_w(q, chi)
+    assert np.all(_rel_fro(W_h, W_ref) < 1e-11)
+    assert np.all(_rel_fro(W_h, W_gj) < 1e-12)
+    dW, _ = ctx.rp_solve_w(q, torch.from_numpy(chi).cuda())
+    ctx.rp_check_numeric()
+    assert np.all(_rel_fro(dW.cpu().numpy(), W_ref) < 1e-11)
+    # eps = 1 - 2 at G = 0 for the second frequency: not positive definite
+    bad = np.zeros((3, len(G), len(G)), dtype=np.complex128)
+    bad[1, 0, 0] = 2.0 / vs[0] ** 2
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_solve_w(q, bad)
+    assert e.value.code == rp.RP_ERR_NUMERIC
+    dB, _ = ctx.rp_solve_w(q, torch.from_numpy(bad).cuda())
+    with pytest.raises(rp.RPError) as e:
+        ctx.rp_check_numeric()
+    assert e.value.code == rp.RP_ERR_NUMERIC
+    dB = dB.cpu().numpy()
+    for f in (0, 2):
+        assert np.allclose(dB[f], np.diag(vs * vs), rtol=1e-14, atol=0)
+    ctx.close()
+    # three q in one packed launch of the list kernel, device buffers, against the pivoted host solves
+    ctx = _ctx(wl)
+    qs = np.array([wl.q[0], [0.25, 0.25, 0.0], [0.5, 0.0, 0.25]])
+    cuts = np.array([_mid_gap_cutoff(wl.cell.recip, qq, t, exclude_zero=True) for qq, t in zip(qs, (40, 60, 90))])
+    chis = ctx.rp_build_chi0_batched(qs, _axis(wl), _ordering(wl), wl.freq, wl.delta, rp.RP_FP64_NATIVE,
+                                     ecut_eps=cuts)
+    ref = ctx.rp_solve_w_batched(qs, chis, ecut_eps=cuts)
+    ctx.rp_set_dyson_hermitian(True)
+    dW = ctx.rp_solve_w_batched(qs, [torch.from_numpy(c).cuda() for c in chis], ecut_eps=cuts)
+    ctx.rp_check_numeric()
+    for (W, _), d in zip(ref, dW):
+        assert np.all(_rel_fro(d.cpu().numpy(), W) < 1e-12)
+    ctx.close()
+
+
 def test_bad_pivot_in_a_batched_device_solve():
     """The batched Dyson solve on device buffers packs the (q, w) matrices of several q into
     cooperative launches of the list kernel: one matrix with a non-finite chi0 is reported as
