@@ -37,7 +37,7 @@ CONTRACT_SRC = os.path.join(ROOT, "paper_2001_02351_gb300", "csrc", "rp_contract
 # contraction kernel at each workload's launch shape, from one ncu capture of
 # `python bench.py --kernel contraction --workload <w>`, valid for the kernel source whose
 # sha256 starts with the given prefix (null traffic otherwise).
-TRAFFIC = {("precision", "bf16x3"): (43_461_647_000, "27be8a6ecd3bb6e2")}
+TRAFFIC = {("precision", "bf16x3"): (44_598_248_192, "bd172516418fe28f")}
 
 
 def measured_traffic(workload, precision):
