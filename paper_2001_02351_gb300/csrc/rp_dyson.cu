@@ -385,33 +385,61 @@ __device__ __forceinline__ void dyson_herm_body(cooperative_groups::grid_group& 
             const double inv = 1.0 / cc[k].x;
             for (int i = tid; i < n; i += DC_THREADS) uu[i] = make_double2(cc[i].x * inv, cc[i].y * inv);
             __syncthreads();
-            if (w > 0)
-                for (int i = c0 + tid / w, cq = tid % w; i < n;) {
+            // the update of one lower-triangle entry (old value a where it is read)
+            auto upd = [&](int ii, int jj, double2 a) {
+                double2 v;
+                if (ii == k && jj == k) v = make_double2(-inv, 0.0);
+                else if (ii == k) v = make_double2(uu[jj].x, -uu[jj].y);          // conj(c_j) / d
+                else if (jj == k) v = uu[ii];                                      // c_i / d
+                else v = cfms(a, uu[ii], make_double2(cc[jj].x, -cc[jj].y));       // - c_i conj(c_j) / d
+                A[(size_t)ii * n + jj] = v;
+            };
+            // rows c1 .. n-1: the full width of this CTA's columns
+            if (w > 0 && c1 < n)
+                for (int i = c1 + tid / w, cq = tid % w; i < n;) {
                     int ei[DC_UNROLL], ej[DC_UNROLL];
                     double2 a[DC_UNROLL];
 #pragma unroll
                     for (int q = 0; q < DC_UNROLL; ++q) {
                         const int j = c0 + cq;
-                        const bool act = i < n && j <= i;
-                        ei[q] = act ? i : -1;
+                        ei[q] = i < n ? i : -1;
                         ej[q] = j;
-                        a[q] = (act && i != k && j != k) ? A[(size_t)i * n + j] : make_double2(0.0, 0.0);
+                        a[q] = (i < n && i != k && j != k) ? A[(size_t)i * n + j] : make_double2(0.0, 0.0);
                         i += di;
                         cq += dc;
                         if (cq >= w) { cq -= w; ++i; }
                     }
 #pragma unroll
-                    for (int q = 0; q < DC_UNROLL; ++q) {
-                        const int ii = ei[q], jj = ej[q];
-                        if (ii < 0) continue;
-                        double2 v;
-                        if (ii == k && jj == k) v = make_double2(-inv, 0.0);
-                        else if (ii == k) v = make_double2(uu[jj].x, -uu[jj].y);          // conj(c_j) / d
-                        else if (jj == k) v = uu[ii];                                      // c_i / d
-                        else v = cfms(a[q], uu[ii], make_double2(cc[jj].x, -cc[jj].y));    // - c_i conj(c_j) / d
-                        A[(size_t)ii * n + jj] = v;
-                    }
+                    for (int q = 0; q < DC_UNROLL; ++q)
+                        if (ei[q] >= 0) upd(ei[q], ej[q], a[q]);
                 }
+            // rows c0 .. c1-1: the triangle j <= i, entry e = r (r + 1) / 2 + (j - c0) for row c0 + r
+            {
+                const int T = w * (w + 1) / 2;
+                for (int e0 = tid; e0 < T; e0 += DC_UNROLL * DC_THREADS) {
+                    int ei[DC_UNROLL], ej[DC_UNROLL];
+                    double2 a[DC_UNROLL];
+#pragma unroll
+                    for (int q = 0; q < DC_UNROLL; ++q) {
+                        const int e = e0 + q * DC_THREADS;
+                        ei[q] = -1;
+                        ej[q] = 0;
+                        a[q] = make_double2(0.0, 0.0);
+                        if (e < T) {
+                            int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                            while (r > 0 && r * (r + 1) / 2 > e) --r;
+                            while ((r + 1) * (r + 2) / 2 <= e) ++r;
+                            const int i = c0 + r, j = c0 + (e - r * (r + 1) / 2);
+                            ei[q] = i;
+                            ej[q] = j;
+                            if (i != k && j != k) a[q] = A[(size_t)i * n + j];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < DC_UNROLL; ++q)
+                        if (ei[q] >= 0) upd(ei[q], ej[q], a[q]);
+                }
+            }
             __syncthreads();
             // publish column k + 1: row k + 1 of this CTA's columns left of it (conjugated), and the
             // owner of column k + 1 its entries from the diagonal down
