@@ -197,8 +197,13 @@ int rp_build_chi0_batched(rp_ctx* ctx, int nq, const double* q_frac, const doubl
 
 /* rp_solve_w_batched -- rp_solve_w for the members of a batch: chi0[i], W_out[i] [io] c128
  *   [nfreq][NG_i][NG_i]; tail_out NULL or [nq] pointers (each NULL or double [N_tail,i]);
- *   q_frac and ecut_eps_per_q as in rp_build_chi0_batched.  FP64, errors as rp_solve_w; the
- *   first failure stops the batch. */
+ *   q_frac and ecut_eps_per_q as in rp_build_chi0_batched.  FP64, errors as rp_solve_w.  Host
+ *   buffers: the members are solved one after another and the first failure stops the batch.
+ *   Device buffers (on_device = 1, nq > 1, every NG_i >= 16): all (q, w) matrices, largest sphere
+ *   first, are packed into a few cooperative launches (consecutive matrices share a launch while
+ *   their summed NG^2 stays below about 24 x 904^2; CTAs per matrix in proportion to NG^2); a bad
+ *   pivot is reported by rp_check_numeric, the other matrices are still solved.  The Dyson form
+ *   (pivoted or Hermitian sweep) follows rp_set_dyson_hermitian. */
 int rp_solve_w_batched(rp_ctx* ctx, int nq, const double* q_frac, const double* ecut_eps_per_q, int nfreq,
                        const double* const* chi0, double* const* W_out, double* const* tail_out,
                        int on_device, void* cuda_stream);
