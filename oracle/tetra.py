@@ -241,26 +241,35 @@ def occupied_pieces(eo, ea, fermi):
     return out
 
 
+def piece_vertex_weights(F, d, sub_weight):
+    """Contributions of pieces of a tetrahedron to its four vertices: for a piece with barycentric
+    matrix F (volume |det F| of the whole) and D linear with vertex values d, lambda_j = sum_i mu_i
+    F[i, j] (mu_i the piece's own barycentric weights), so the piece adds |det F| sum_i F[i, j] w_i
+    to vertex j, w_i its vertex-i weight (the unclipped formula on the piece).
+    F [P, 4, 4], d [P, 4] (D at the tetrahedron's vertices, per piece); sub_weight(ds) takes D at
+    the pieces' vertices [P, 4] and returns their vertex weights [P, 4, ...].  Returns [P, 4, ...]."""
+    vol = np.abs(np.linalg.det(F))                          # [P]
+    ds = np.einsum("pij,pj->pi", F, d)                      # [P, 4]
+    w = np.asarray(sub_weight(ds))                          # [P, 4 (i), ...]
+    return np.einsum("p,pij,pi...->pj...", vol, F, w)
+
+
 def clipped_vertex_weights(d, pieces, sub_weight):
-    """(1/V_t) int over the pieces of lambda_j g(D) for the four vertices j of a tetrahedron, with
-    D linear (vertex values d [4]).  On a piece with barycentric matrix F (volume |det F| of the
-    whole), lambda_j = sum_i mu_i F[i, j] (mu_i the piece's own barycentric weights), so the
-    piece gives |det F| sum_i F[i, j] w_i, where w_i is the vertex-i weight of the piece (the
-    unclipped formula on the piece).  sub_weight(ds) takes D at the pieces' vertices [P, 4] and
-    returns their vertex weights [P, 4, ...].  Returns [4, ...], or None without pieces."""
+    """(1/V_t) int over the pieces of lambda_j g(D) for the four vertices j of a tetrahedron (D
+    linear, vertex values d [4]): the sum of piece_vertex_weights.  Returns [4, ...], or None
+    without pieces."""
     if not pieces:
         return None
-    F = np.stack(pieces)                                   # [P, 4 (i), 4 (j)]
-    vol = np.abs(np.linalg.det(F))                         # [P]
-    ds = F @ np.asarray(d, dtype=np.float64)               # [P, 4]
-    w = np.asarray(sub_weight(ds))                         # [P, 4, ...]
-    return np.tensordot(vol[:, None, None] * F, w, axes=([0, 1], [0, 1]))   # [4 (j), ...]
+    F = np.stack(pieces)
+    d = np.broadcast_to(np.asarray(d, dtype=np.float64), (len(pieces), 4))
+    return piece_vertex_weights(F, d, sub_weight).sum(axis=0)
 
 
 def metal_vertex_weights(e_occ, e_emp_kq, tets, z1, z2, delta_a, delta_r, fermi, k_list=None):
     """x[k, a, o, f] of the metallic generalized tetrahedron method: as vertex_weights, but each
     tetrahedron contributes only over its part where band o (at k) is occupied and band a (at
-    k + q) is empty, with the Fermi energy `fermi` (both bands interpolated linearly)."""
+    k + q) is empty, with the Fermi energy `fermi` (both bands interpolated linearly).  The pieces
+    of all pairs of one tetrahedron are evaluated together."""
     nk, nocc = e_occ.shape
     nemp = e_emp_kq.shape[1]
     nf = len(z1)
@@ -277,15 +286,23 @@ def metal_vertex_weights(e_occ, e_emp_kq, tets, z1, z2, delta_a, delta_r, fermi,
         return sum(divided_difference(nodes, z, delta_a, delta_r) for z in zz)    # [P, 4, nf]
 
     for tt in sel:
+        F, d, owner = [], [], []
         for a in range(nemp):
             for o in range(nocc):
                 eo, ea = e_occ[tt, o], e_emp_kq[tt, a]
-                val = clipped_vertex_weights(ea - eo, occupied_pieces(eo, ea, fermi), sub_weight)
-                if val is None:
-                    continue
-                for j in range(4):
-                    if want[tt[j]]:
-                        x[tt[j], a, o] += val[j] / 6.0
+                for B in occupied_pieces(eo, ea, fermi):
+                    F.append(B)
+                    d.append(ea - eo)
+                    owner.append((a, o))
+        if not F:
+            continue
+        contrib = piece_vertex_weights(np.stack(F), np.stack(d), sub_weight)     # [P, 4, nf]
+        val = np.zeros((nemp, nocc, 4, nf), dtype=np.complex128)
+        own = np.array(owner)
+        np.add.at(val, (own[:, 0], own[:, 1]), contrib)
+        for j in range(4):
+            if want[tt[j]]:
+                x[tt[j]] += val[:, :, j] / 6.0
     return x[ks]
 
 

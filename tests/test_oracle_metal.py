@@ -12,7 +12,9 @@ which the unclipped vertex formula is applied.  Pinned here by:
 - nothing occupied (Fermi energy below the bands) gives zero;
 - a metal (Fermi energy inside two bands of the tiny set, a band window with its partly filled
   bands in both ranges): chi0 on the imaginary axis is Hermitian and negative semidefinite (every
-  clipped piece has D = E_a - E_o > 0), and the intraband pairs (a band with itself) contribute.
+  clipped piece has D = E_a - E_o > 0), and the intraband pairs (a band with itself) contribute;
+- the free-electron gas: chi_00(q, i nu) per volume from the clipped tetrahedra approaches the
+  Lindhard function as the mesh grows (4^3 -> 6^3: relative error 0.13 -> 0.05 at nu = 0.5 Ha).
 """
 from dataclasses import replace
 
@@ -132,3 +134,27 @@ def test_metal_chi0_hermitian_negative_semidefinite(tiny_metal):
     nk = wl.bands.kfrac.shape[0]
     wk = w.reshape(len(wl.freq), nk, wl.nemp, wl.nocc)
     assert np.abs(wk[:, :, 0, 2]).max() > 0 and np.abs(wk[:, :, 1, 3]).max() > 0
+
+
+def test_free_electron_lindhard_metallic_tetrahedron():
+    """Plane-wave bands of an empty simple-cubic cell (a = 4 bohr), Fermi wave number 0.8, the lowest
+    12 bands of each range, |q| = 2 pi / 8 bohr^-1 (Q / 2 k_F ~ 0.49): chi_00 from the metallic
+    tetrahedron weights against the Lindhard function, on 4^3 and 6^3 meshes."""
+    from test_oracle_chi0 import _pw_bands, lindhard_imag
+    from synth import Workload
+    nu = np.array([0.5])
+    kf, nwin = 0.8, 12
+    errs = []
+    for n in (4, 6):
+        bands, nb = _pw_bands(4.0, (n, n, n), ecut=0.5 * (kf + 2.6) ** 2)
+        rows = np.concatenate([np.arange(nwin), nb + np.arange(nwin)])
+        b2 = replace(bands, coef=bands.coef[:, rows], energy=bands.energy[:, rows])
+        q = np.array([0.5, 0.0, 0.0])
+        M = pd.pair_density(b2, nwin, nwin, q, np.zeros((1, 3), dtype=np.int64), fft=(16, 16, 16))
+        wl = Workload(name="free", bands=b2, fft=(16, 16, 16), nocc=nwin, nemp=nwin, q=q[None, :],
+                      ecut_eps=np.array([1.0]), axis="imag", freq=nu, delta=0.0)
+        chi = C.chi0(M, C.pair_weights(wl, q, kind="tetra", fermi=0.5 * kf * kf))[:, 0, 0] / bands.cell.omega
+        Q = np.linalg.norm(q @ bands.cell.recip)
+        ref = lindhard_imag(Q, nu[0], kf)
+        errs.append(abs(chi[0] - ref) / abs(ref))
+    assert errs[1] < 0.08 and errs[1] < 0.5 * errs[0], errs
